@@ -1,0 +1,199 @@
+"""Pins for oracle/cross_deim.py: published generator values, brute force,
+exact cross-approximation identities, closed-form solutions."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import lrp_inputs as li
+from oracle import cross_deim as cd
+from oracle import poisson as po
+
+
+def test_splitmix64_published_first_outputs():
+    # SplitMix64 seeded with 0: the first output of the reference generator is
+    # 0xe220a8397b1dcdaf; with state += golden gamma each call the second is
+    # 0x6e789e6aa1b965f4.
+    assert cd.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert cd.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+def test_growth_index_probes_to_complement():
+    n = 10
+    i0 = cd.splitmix64(7 + 2 * 3 + 1) % n
+    present = [(i0 + d) % n for d in range(4)]
+    g = cd.growth_index(7, 3, 1, n, present)
+    assert g == (i0 + 4) % n and g not in present
+    assert cd.growth_index(7, 3, 1, 3, [0, 1, 2]) == -1
+
+
+def test_leverage_scores_sum_to_one_and_topc_bruteforce():
+    rng = np.random.default_rng(0)
+    U, _ = np.linalg.qr(rng.standard_normal((50, 6)))
+    pi = cd.leverage_scores(U)
+    assert abs(pi.sum() - 1.0) < 1e-14
+    # brute force: repeatedly take the max, lowest index first on ties
+    U[7] = U[3]  # planted tie between rows 3 and 7
+    pi = cd.leverage_scores(U)
+    left = list(range(50))
+    ref = []
+    for _ in range(6):
+        best = max(left, key=lambda i: (pi[i], -i))
+        ref.append(best)
+        left.remove(best)
+    assert list(cd.select_leverage(U)) == ref
+    assert ref.index(3) < ref.index(7) if 7 in ref else True
+
+
+def _greedy_column_pivots(A, c):
+    """Businger-Golub pivoting by explicit Gram-Schmidt downdates (brute force)."""
+    A = A.copy()
+    piv = []
+    for _ in range(c):
+        norms = np.sum(A * A, axis=0)
+        norms[piv] = -1
+        j = int(np.argmax(norms))
+        piv.append(j)
+        q = A[:, j] / np.linalg.norm(A[:, j])
+        A = A - np.outer(q, q @ A)
+    return piv
+
+
+def test_qdeim_matches_greedy_pivoting():
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((40, 5)) * np.array([5, 3, 2, 1, 0.5]))
+    assert list(cd.select_qdeim(U)) == _greedy_column_pivots(U.T, 5)
+
+
+def test_deim_selects_independent_rows():
+    rng = np.random.default_rng(4)
+    U, _ = np.linalg.qr(rng.standard_normal((30, 4)))
+    idx = cd.select_deim(U)
+    assert len(set(idx.tolist())) == 4
+    assert np.linalg.matrix_rank(U[idx]) == 4
+
+
+class DenseG:
+    def __init__(self, A):
+        self.A = A
+        self.shape = A.shape
+
+    def cols(self, J):
+        return self.A[:, np.asarray(J)]
+
+    def rows(self, I):
+        return self.A[np.asarray(I), :]
+
+
+def test_scross_exact_for_low_rank_both_branches():
+    # Cross approximation theorem: rank(G(I,J)) = rank(G) => C G(I,J)^+ R = G.
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((60, 5)) @ rng.standard_normal((5, 45))
+    G = DenseG(A)
+    I = rng.choice(60, 9, replace=False)
+    J = rng.choice(45, 7, replace=False)
+    for (II, JJ) in [(I, J), (I[:6], J)]:   # |J| <= |I| and |J| > |I|
+        r = cd.scross(G, II, JJ, None)
+        approx = (r.U * r.S) @ r.V.T
+        assert np.abs(approx - A).max() < 1e-12 * np.abs(A).max()
+        assert r.S.shape[0] == 5
+    # both branches give the same approximation on a full-rank matrix
+    B = rng.standard_normal((30, 30))
+    GB = DenseG(B)
+    I, J = np.arange(12), np.arange(12)
+    r1 = cd.scross(GB, I, J[:11], None)
+    r2 = cd.scross(GB, I[:11], J, None)
+    C = B[:, J[:11]]
+    ref = C @ np.linalg.pinv(B[np.ix_(I, J[:11])]) @ B[I, :]
+    assert np.abs((r1.U * r1.S) @ r1.V.T - ref).max() < 1e-10 * np.abs(ref).max()
+    C = B[:, J]
+    ref2 = C @ np.linalg.pinv(B[np.ix_(I[:11], J)]) @ B[I[:11], :]
+    assert np.abs((r2.U * r2.S) @ r2.V.T - ref2).max() < 1e-10 * np.abs(ref2).max()
+
+
+def test_scross_all_indices_is_truncated_svd():
+    # I = J = all rows/cols: the cross approximation is G itself and scross
+    # returns its SVD (numpy.linalg.svd on the dense matrix).
+    n = 47
+    rhs = li.gaussian_eigen_rhs(n, 2, 3)
+    G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+    r = cd.scross(G, np.arange(n), np.arange(n), None)
+    s_ref = np.linalg.svd(G.dense(), compute_uv=False)
+    k = r.S.shape[0]
+    assert np.abs(r.S - s_ref[:k]).max() < 1e-12 * s_ref[0]
+    assert np.abs((r.U * r.S) @ r.V.T - G.dense()).max() < 1e-12 * s_ref[0]
+
+
+def test_scross_redundancy_diagonal_flags_duplicate_column():
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((40, 4)) @ rng.standard_normal((4, 40))
+    G = DenseG(A)
+    I = np.array([0, 1, 2, 3, 4])
+    J = np.array([5, 6, 7, 8, 5])   # column 5 twice: the repeat is dependent
+    r = cd.scross(G, I, J, None)
+    aC = np.abs(r.rC)
+    assert aC[4] < 1e-12 * aC.max()
+    assert np.all(aC[:4] > 1e-6 * aC.max())
+
+
+def test_tail_rank_bruteforce():
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        s = np.sort(np.abs(rng.standard_normal(12)) * 10.0 ** rng.uniform(-12, 0, 12))[::-1]
+        tol = 10.0 ** rng.uniform(-10, -1)
+        total = np.sum(s ** 2)
+        ref = next(r for r in range(13) if np.sum(s[r:] ** 2) < tol * tol * total)
+        assert cd.tail_rank(s, tol) == max(ref, 1)
+
+
+def test_cross_deim_eigenfunction_rhs_rank_one():
+    n, p, q = 255, 9, 40
+    rhs = li.eigenfunction_rhs(n, p, q, 2.5)
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-12, 8)
+    assert S.shape[0] == 1
+    assert po.rel_error_vs_exact(U, S, V, G) < 1e-12
+    assert p - 1 in info.I and q - 1 in info.J
+
+
+@pytest.mark.parametrize("selector", ["ls", "qdeim"])
+def test_cross_deim_small_grid_within_tolerance(selector):
+    # Brute force on a small grid: the full-grid DST solve is the exact answer.
+    n = 63
+    rhs = li.gaussian_eigen_rhs(n, 11, 3)
+    tol = 1e-8
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, 40, selector=selector)
+    W = po.full_grid_solve(rhs.dense())
+    err = np.linalg.norm((U * S) @ V.T - W) / np.linalg.norm(W)
+    assert err < 10 * tol
+    s_ex = np.linalg.svd(W, compute_uv=False)
+    # the returned rank is no larger than the exact tail-rule rank plus the safeguard slack
+    assert S.shape[0] <= cd.tail_rank(s_ex, tol / 10)
+
+
+def test_cross_deim_workload_n255_reaches_tolerance():
+    rhs = li.workload_single_small(0)
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-10, 32, m_cap=2 * 32 + 4)
+    assert info.converged
+    assert po.rel_error_vs_exact(U, S, V, G) < 1e-9
+    assert np.all(np.diff(S) <= 0)
+    # orthonormal factors
+    assert np.abs(U.T @ U - np.eye(S.shape[0])).max() < 1e-12
+
+
+def test_rank_cap_and_floor():
+    rhs = li.workload_single_small(1)
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-10, 5)
+    assert S.shape[0] == 5 and info.rank_capped
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 10.0, 5)
+    assert S.shape[0] == 1
+
+
+def test_planted_sign_error_is_caught():
+    # A plausible mistake (a sign flip in the Cauchy denominator) must break the
+    # exactness check on the eigenfunction right-hand side.
+    n, p, q = 63, 3, 5
+    rhs = li.eigenfunction_rhs(n, p, q)
+    G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+    good = G.cols([q - 1])
+    G.lam = -G.lam[::-1].copy()
+    bad = G.cols([q - 1])
+    assert np.abs(good - bad).max() > 1e-3 * np.abs(good).max()
