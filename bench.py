@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Batched low-rank Poisson solves on GB300: solves/s and p50/p99 step latency.
+
+Workload (one "step" = one batch of independent solves through the whole hot
+path: forward DST, Cross-DEIM iterations, back DST): n = 4095 interior points
+(h = 1/4096), right-hand side of rank 20 (16 seeded separable Gaussians + 4
+discrete eigenfunctions with p, q in 1..64), tol 1e-8, max rank 64, seeds
+distinct per problem and rank.  Both precisions run side by side; the headline
+`value` is the mixed-precision path when it is built, else FP64.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank solves its own batch on its own GPU (replicas, weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 4095
+TOL = 1e-8
+RMAX = 64
+RF = 20
+M_CAP = 2 * RMAX + RF
+WORKLOAD = ("n=4095 (h=1/4096), RHS rank 20 = 16 seeded Gaussians + 4 eigenfunctions "
+            "(p,q in 1..64), tol 1e-8, max rank 64")
+METRIC = "Poisson solves/s & p50/p99 latency at rel err<=1e-6, mixed vs plain FP64"
+FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA throughput of this GB300 pool ("Peaks")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lrp", choices=["lrp", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "both"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback (profiling recipe)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+class Batch:
+    """Device-resident inputs and outputs of one batch, packed for single H2D / D2H copies."""
+
+    def __init__(self, rhss, torch, device):
+        import numpy as np
+        self.B = len(rhss)
+        per_in = 2 * N * RF + RF
+        per_out = 2 * N * RMAX + RMAX + 8
+        host_in = np.zeros(self.B * per_in)
+        for b, r in enumerate(rhss):
+            o = b * per_in
+            host_in[o:o + N * RF] = r.U.reshape(-1, order="F")
+            host_in[o + N * RF:o + 2 * N * RF] = r.V.reshape(-1, order="F")
+            host_in[o + 2 * N * RF:o + per_in] = r.s
+        self.host_in = torch.from_numpy(host_in).pin_memory()
+        self.dev_in = self.host_in.to(device)
+        self.dev_out = torch.zeros(self.B * per_out, dtype=torch.float64, device=device)
+        self.host_out = torch.zeros(self.B * per_out, dtype=torch.float64).pin_memory()
+        self.inputs, self.outputs = [], []
+        for b in range(self.B):
+            o = b * per_in
+            U = self.dev_in[o:o + N * RF].view(RF, N).t()
+            V = self.dev_in[o + N * RF:o + 2 * N * RF].view(RF, N).t()
+            s = self.dev_in[o + 2 * N * RF:o + per_in]
+            self.inputs.append((U, s, V))
+            q = b * per_out
+            Uo = self.dev_out[q:q + N * RMAX].view(RMAX, N).t()
+            Vo = self.dev_out[q + N * RMAX:q + 2 * N * RMAX].view(RMAX, N).t()
+            So = self.dev_out[q + 2 * N * RMAX:q + 2 * N * RMAX + RMAX]
+            info = self.dev_out[q + 2 * N * RMAX + RMAX:q + per_out].view(torch.uint8)
+            self.outputs.append((Uo, So, Vo, info))
+        self.h2d_bytes = self.host_in.numel() * 8
+        self.d2h_bytes = self.host_out.numel() * 8
+
+
+def time_steps(fn, K, stream, torch, flush):
+    evs = []
+    for _ in range(K):
+        flush.zero_()  # L2 flush: 256 MiB write between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def gpu_arm(args, rank, world, local_rank, precisions):
+    import torch
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    B = args.batch
+    rhss = [li.workload_n4095(seed=1000 * rank + i) for i in range(B)]
+    batch = Batch(rhss, torch, device)
+    stream = torch.cuda.Stream(device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    hbm_peak, peak_src = load_peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec in precisions:
+        plan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP)
+
+        def step():
+            with torch.cuda.stream(stream):
+                plan.solve_batch_into(batch.inputs, batch.outputs, stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+        torch.cuda.synchronize()
+        plan.reset_stats()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            ms = time_steps(step, args.steps, stream, torch, flush)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        torch.cuda.synchronize()
+        barrier()
+        launches = plan.kernel_stats()["all"][0]
+        total_ms = max_over_ranks(sum(ms))
+        res = {"ms": ms, "total_ms": total_ms, "wall_s": wall, "clocks": clk, "launches": launches,
+               "value": B * world * args.steps / (total_ms / 1e3)}
+        # Per-kernel-class event timing and algorithmic work (separate pass, same inputs).
+        plan.set_timing(True)
+        plan.reset_stats()
+        with torch.cuda.stream(stream):
+            time_steps(step, 2, stream, torch, flush)
+        stats = plan.kernel_stats()
+        plan.set_timing(False)
+        res["kernels"] = stats
+        # End to end through the public call with host buffers (pinned), copies inside the timed region.
+        if not args.no_e2e:
+            def e2e_step():
+                batch.dev_in.copy_(batch.host_in, non_blocking=True)
+                plan.solve_batch_into(batch.inputs, batch.outputs, stream)
+                batch.host_out.copy_(batch.dev_out, non_blocking=True)
+
+            barrier()
+            with torch.cuda.stream(stream):
+                e2e_ms = time_steps(e2e_step, args.steps, stream, torch, flush)
+            e2e_total = max_over_ranks(sum(e2e_ms))
+            res["e2e"] = {"value": B * world * args.steps / (e2e_total / 1e3), "unit": "solves/s",
+                          "h2d_bytes_per_step": batch.h2d_bytes, "d2h_bytes_per_step": batch.d2h_bytes}
+        # Per-problem reports of the last step.
+        torch.cuda.synchronize()
+        infos = [lrp.parse_info(o[3]) for o in batch.outputs]
+        res["infos"] = infos
+        res["results"] = [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy()) for o in batch.outputs]
+        plan.close()
+        results[prec] = res
+    return results, rhss, hbm_peak, peak_src
+
+
+def roofline(res, prec, hbm_peak, peak_src):
+    """Dominant kernel class (most event-timed time) against its bound."""
+    ks = {k: v for k, v in res["kernels"].items() if k != "all"}
+    name = max(ks, key=lambda k: ks[k][1])
+    launches, ms, flops, nbytes = ks[name]
+    if ms <= 0 or launches <= 0:
+        return None
+    alu_classes = {"gram", "gemm", "cross", "chol", "core", "select", "stop"}
+    if prec == "fp64" and name in alu_classes:
+        achieved = flops / (ms / 1e3) / 1e12
+        out = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "measured FP64 FMA probe"}
+    else:
+        achieved = nbytes / (ms / 1e3) / 1e9
+        out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+               "frac": achieved / hbm_peak, "peak_source": peak_src}
+    out.update({"kernel": name, "launches": launches, "avg_launch_us": 1e3 * ms / launches,
+                "algorithmic_per_launch": (flops if out["bound"] == "alu" else nbytes) / launches,
+                "traffic": None})
+    return out
+
+
+def cpu_baseline(rhss, seconds, gpu_results=None):
+    """The CPU oracle as it stands, on a bounded sample of the same workload."""
+    import numpy as np
+
+    from oracle import cross_deim as cd
+    from oracle import poisson as po
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    r = rhss[0]
+    cd.poisson_solve(r.U, r.s, r.V, TOL, RMAX, m_cap=M_CAP)  # warm-up (as the paper does)
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < seconds and done < len(rhss):
+        r = rhss[done]
+        cd.poisson_solve(r.U, r.s, r.V, TOL, RMAX, seed=0, m_cap=M_CAP)
+        done += 1
+    dt = time.perf_counter() - t0
+    out = {"value": done / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{done} of the batch's problems, solved one after another ({dt:.1f} s)"}
+    errs = {}
+    if gpu_results:
+        for prec, res in gpu_results.items():
+            e = []
+            for b in range(min(4, len(rhss))):
+                G = po.SpectralSolution(rhss[b].U, rhss[b].s, rhss[b].V)
+                inf = res["infos"][b]
+                U, S, V = res["results"][b]
+                rk = inf["rank"]
+                e.append(po.rel_error_vs_exact(U[:, :rk], S[:rk], V[:, :rk], G))
+            errs[prec] = max(e)
+    return out, errs
+
+
+def reference_arm(args, rank):
+    """The oracle on the host cores, on the same workload: K steps of a bounded sample."""
+    if rank != 0:
+        return
+    import lrp_inputs as li
+    from oracle import cross_deim as cd
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    per_step = 2
+    rhss = [li.workload_n4095(seed=i) for i in range(per_step * (args.steps + args.warmup))]
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for r in rhss[k * per_step:(k + 1) * per_step]:
+            cd.poisson_solve(r.U, r.s, r.V, TOL, RMAX, m_cap=M_CAP)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "batch": per_step, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} solves per step on the host cores"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import paper_2607_06021_gb300 as lrp  # noqa: F401  (fails loudly without the library)
+    if args.precision == "auto":
+        precisions = ["fp64", "mixed"] if os.environ.get("LRP_BENCH_MIXED", "0") == "1" else ["fp64"]
+    elif args.precision == "both":
+        precisions = ["fp64", "mixed"]
+    else:
+        precisions = [args.precision]
+    results, rhss, hbm_peak, peak_src = gpu_arm(args, rank, world, local_rank, precisions)
+    if rank != 0:
+        return
+    head = "mixed" if "mixed" in results else "fp64"
+    res = results[head]
+    ms = res["ms"]
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_gpu": args.batch, "precision": head,
+                   "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"},
+        "latency_ms": {"p50": statistics.median(ms), "p99": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
+                       "note": "per step; every solve of a batch completes at the end of its step"},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    for prec, r in results.items():
+        line[f"{prec}_solves_per_s"] = r["value"]
+        line[f"{prec}_iterations_mean"] = statistics.mean(i["iterations"] for i in r["infos"])
+        line[f"{prec}_rank_mean"] = statistics.mean(i["rank"] for i in r["infos"])
+    if "mixed" in results and "fp64" in results:
+        line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    line["roofline"] = roofline(res, head, hbm_peak, peak_src)
+    line["kernel_ms"] = {k: round(v[1], 3) for k, v in res["kernels"].items()}
+    if not args.no_cpu and world == 1:
+        cb, errs = cpu_baseline(rhss, args.cpu_seconds, results)
+        line["cpu_baseline"] = cb
+        line["rel_err_max_vs_exact"] = errs
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * lrp.h -- C ABI of the GB300 low-rank Poisson solver (Cross-DEIM on the
+ * sine-transformed 5-point Poisson equation).
+ *
+ * Problem (paper Sec. 3, Eq. matrix_poisson): on the n x n interior grid of
+ * the unit square with zero Dirichlet data, h = 1/(n+1), solve
+ *
+ *     T W + W T = h^2 F,      T = tridiag(-1, 2, -1)  (n x n),
+ *
+ * for a right-hand side given by factors F = U_f diag(s_f) V_f^T (Sec. 3.2).
+ * The solver transforms the factors with the orthonormal DST-I Z (Sec. 3),
+ * runs Cross-DEIM (Algorithm "Cross-DEIM", Sec. 2.2.3) on the transformed
+ * solution What(i,j) = h^2 Fhat(i,j) / (lambda_i + lambda_j) (Eq. g_for_p)
+ * and transforms the result back: W = (Z Uhat) diag(S) (Z Vhat)^T.
+ * The n x n grid is never formed.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major FP64 with a leading dimension ld >= n.
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device; the
+ *     caller allocates and owns them.  h_* pointers are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Every call returns an lrp_status; no call aborts, throws or exits.  On an
+ *     error the thread-local message lrp_last_error() says what failed.
+ *   - Results: W ~= U diag(S) V^T, U and V with orthonormal columns, S >= 0
+ *     descending, the sign of each singular pair unspecified.
+ */
+#ifndef LRP_H_
+#define LRP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lrp_status {
+  LRP_OK = 0,
+  LRP_EINVAL = 1,          /* bad argument (size, pointer, leading dimension, option) */
+  LRP_ENOMEM = 2,          /* device or host allocation failed */
+  LRP_ECUDA = 3,           /* a CUDA runtime call failed (see lrp_last_error) */
+  LRP_ETIMEDOUT = 4,       /* a bounded wait gave up (server drain, device flag) */
+  LRP_NOT_CONVERGED = 5,   /* max_iter reached; a valid result was still written */
+  LRP_RANK_CAPPED = 6,     /* tolerance needs rank > max_rank; result truncated */
+  LRP_EAGAIN = 7,          /* lrp_poll: the request has not finished yet */
+  LRP_ECAPACITY = 8        /* server admission: request larger than the memory cap */
+} lrp_status;
+
+typedef enum lrp_precision {
+  LRP_FP64 = 0,   /* every step in FP64 */
+  LRP_MIXED = 1   /* FP32 transforms/contractions, FP64 Gram/Cholesky/core, one
+                     FP64-residual refinement step (not in the paper) */
+} lrp_precision;
+
+typedef enum lrp_selector {
+  LRP_SEL_LEVERAGE = 0,  /* Algorithm LeverageScores, deterministic top-c (Sec. 2.2.2) */
+  LRP_SEL_QDEIM = 1      /* Algorithm (Q)DEIM: pivoted QR of U^T (Sec. 2.2.1) */
+} lrp_selector;
+
+/* Solver options.  lrp_default_opts fills the defaults noted here. */
+typedef struct lrp_opts {
+  int32_t precision;     /* lrp_precision, default LRP_FP64 */
+  int32_t selector;      /* lrp_selector, default LRP_SEL_LEVERAGE */
+  int32_t max_iter;      /* Cross-DEIM iterations, default 30 */
+  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps, default 1 */
+  int32_t max_rhs_rank;  /* capacity for r_f, default 64 (<= 256) */
+  int32_t batch;         /* max problems per lrp_solve_batch call, default 1 */
+  int32_t m_cap;         /* index-set capacity, default min(2*max_rank + max_rhs_rank, 256) */
+  int32_t check_every;   /* host reads the active-solve count every this many
+                            iterations, default 1 */
+  uint64_t seed;         /* key of the growth-index generator (SplitMix64), default 0 */
+} lrp_opts;
+
+/* Per-problem report, written by the device into caller memory. */
+typedef struct lrp_info {
+  int32_t rank;          /* r = max(min(r*, max_rank), 1) columns written to U, V, S */
+  int32_t iterations;    /* Cross-DEIM iterations taken (last solve of a refinement) */
+  int32_t status;        /* LRP_OK, LRP_NOT_CONVERGED or LRP_RANK_CAPPED */
+  int32_t r_star;        /* tail-rule rank before the max_rank cap */
+  int32_t size_I;        /* |I| at exit */
+  int32_t size_J;        /* |J| at exit */
+  int32_t total_iterations; /* summed over the initial solve and refinement solves */
+  int32_t reserved0;
+  double rho;            /* last relative change ||A_k - A_{k-1}||_F / ||A_k||_F */
+  double eta_smin;       /* last min(eta1(1+eta2), eta2(1+eta1)) * S_min / ||S||_F */
+  double sigma_max;      /* largest singular value of the result */
+  double reserved1;
+} lrp_info;
+
+/* One problem of a batch (all problems of a plan share n). */
+typedef struct lrp_problem {
+  int32_t r_f;           /* right-hand-side rank, 1 <= r_f <= max_rhs_rank */
+  int32_t reserved;
+  const double* d_U_f;   /* n x r_f, ld ldu_f */
+  int64_t ldu_f;
+  const double* d_s_f;   /* r_f weights of F = U_f diag(s_f) V_f^T */
+  const double* d_V_f;   /* n x r_f, ld ldv_f */
+  int64_t ldv_f;
+  double* d_U;           /* out: n x max_rank, ld ldu (first rank columns written) */
+  int64_t ldu;
+  double* d_S;           /* out: max_rank singular values (first rank written) */
+  double* d_V;           /* out: n x max_rank, ld ldv */
+  int64_t ldv;
+  lrp_info* d_info;      /* out: device memory for one lrp_info (may be NULL) */
+} lrp_problem;
+
+typedef struct lrp_plan_s* lrp_plan_t;
+
+/* Fill *opts with the defaults.  Returns LRP_EINVAL for NULL. */
+lrp_status lrp_default_opts(lrp_opts* opts);
+
+/*
+ * Create a plan for grids with n interior points per dimension, relative
+ * tolerance tol (Algorithm Cross-DEIM's epsilon: stop test and final
+ * truncation sum_{l>r} S_l^2 < tol^2 ||S||^2) and output rank cap max_rank
+ * (the paper's r_max).  opts may be NULL (defaults).  The plan allocates and
+ * owns all device workspace on the current device; its size grows with
+ * batch * n * m_cap.  Supported: 1 <= n <= 8191 with n+1 a power of two is
+ * the shared-memory DST path; other n (n+1 a power of two up to 2^20) use the
+ * multi-pass DST.  Errors: LRP_EINVAL (n+1 not a power of two, tol <= 0,
+ * max_rank < 1, options out of range), LRP_ENOMEM, LRP_ECUDA.
+ */
+lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank,
+                    const lrp_opts* opts);
+
+/* Release a plan and its workspace (synchronises the device first). */
+lrp_status lrp_plan_destroy(lrp_plan_t plan);
+
+/* Bytes of device workspace the plan holds. */
+lrp_status lrp_plan_workspace_bytes(lrp_plan_t plan, size_t* bytes);
+
+/*
+ * Solve one problem (Sec. 3.2: DST of the factors, Cross-DEIM on Eq. g_for_p,
+ * back DST).  Inputs and outputs are device pointers as in lrp_problem.  Work
+ * is enqueued on `stream`; the call returns once the iteration loop has ended
+ * (it reads a device counter of active solves between iterations) with the
+ * output writes enqueued on `stream`.  Errors: LRP_EINVAL, LRP_ECUDA.  The
+ * per-problem outcome (LRP_NOT_CONVERGED, LRP_RANK_CAPPED) is in d_info.
+ */
+lrp_status lrp_solve(lrp_plan_t plan, int32_t r_f,
+                     const double* d_U_f, int64_t ldu_f, const double* d_s_f,
+                     const double* d_V_f, int64_t ldv_f,
+                     double* d_U, int64_t ldu, double* d_S, double* d_V, int64_t ldv,
+                     lrp_info* d_info, void* stream);
+
+/*
+ * Solve `count` independent problems of the plan's n in one set of launches
+ * (every kernel covers all problems).  h_problems is a HOST array of count
+ * descriptors; count <= opts.batch.  Same completion rule as lrp_solve.
+ */
+lrp_status lrp_solve_batch(lrp_plan_t plan, int32_t count, const lrp_problem* h_problems,
+                           void* stream);
+
+/*
+ * Orthonormal DST-I of ncols columns (Sec. 3: Y = Z X, Z_{ik} =
+ * sqrt(2/(n+1)) sin(i k pi/(n+1))), FP64, n+1 a power of two up to 2^20.
+ * X and Y are device, column-major, may not overlap.  Enqueued on stream.
+ */
+lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* d_X, int64_t ldx,
+                    double* d_Y, int64_t ldy, void* stream);
+
+/*
+ * Measurement hooks (not part of the paper's method).  Kernel classes of the
+ * solve, for per-class launch counts and CUDA-event timings.
+ */
+typedef enum lrp_kernel_class {
+  LRP_K_DST = 0,       /* forward and back DST-I */
+  LRP_K_CROSS = 1,     /* sampled columns/rows of the transformed solution */
+  LRP_K_GRAM = 2,      /* per-block FP64 partial Gram / cross-Gram products */
+  LRP_K_REDUCE = 3,    /* reduction of the Gram partials */
+  LRP_K_GEMM = 4,      /* tall-skinny n x m times m x m' products */
+  LRP_K_LEVERAGE = 5,  /* leverage scores and block top-c */
+  LRP_K_CHOL = 6,      /* small Cholesky / triangular inverse per problem */
+  LRP_K_CORE = 7,      /* small pseudoinverse / SVD core per problem */
+  LRP_K_SELECT = 8,    /* index-set enrichment per problem */
+  LRP_K_STOP = 9,      /* convergence test per problem */
+  LRP_K_OTHER = 10,    /* setup, finalize, counters */
+  LRP_K_COUNT = 11
+} lrp_kernel_class;
+
+/*
+ * enable != 0: every kernel launch of later solves on this plan is bracketed
+ * by a CUDA event pair recorded on the solve's stream (no host synchronisation
+ * is added); enable == 0 stops recording.  Launch counting is always on.
+ */
+lrp_status lrp_plan_set_timing(lrp_plan_t plan, int32_t enable);
+
+/*
+ * Launches and summed event-timed milliseconds of kernel class kclass
+ * (0 <= kclass < LRP_K_COUNT, or -1 for all classes) since the last reset.
+ * Synchronises the device first.  *total_ms is 0 when timing was off.
+ */
+lrp_status lrp_plan_kernel_stats(lrp_plan_t plan, int32_t kclass, int64_t* launches, double* total_ms);
+
+/*
+ * Algorithmic work of kernel class kclass (or -1 for all) since the last reset,
+ * summed over problems: the minimal flops and HBM bytes of the method's steps
+ * at the sizes each iteration actually had (|I|, |J|, ranks), independent of
+ * the kernels' tiling.  Synchronises the device first.
+ */
+lrp_status lrp_plan_kernel_work(lrp_plan_t plan, int32_t kclass, double* flops, double* bytes);
+
+/* Clear the launch counts, timings and work totals of a plan. */
+lrp_status lrp_plan_reset_stats(lrp_plan_t plan);
+
+/* Thread-local text of the last error (empty string if none). */
+const char* lrp_last_error(void);
+
+/* Static name of a status code. */
+const char* lrp_status_string(lrp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRP_H_ */

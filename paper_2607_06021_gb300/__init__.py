@@ -1,0 +1,169 @@
+"""Python binding of liblrp.so (include/lrp.h): argument marshalling only.
+
+Every computation runs in the library's sm_103a kernels.  PyTorch provides
+device memory and streams.  Factor matrices are column-major: an n x r matrix
+is a CUDA float64 tensor of shape (n, r) with strides (1, ld), ld >= n (for
+example ``torch.empty(r, n).T``).  If the shared library is missing the import
+of this package fails; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrp.so")
+
+LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ECUDA, LRP_ETIMEDOUT = 0, 1, 2, 3, 4
+LRP_NOT_CONVERGED, LRP_RANK_CAPPED, LRP_EAGAIN, LRP_ECAPACITY = 5, 6, 7, 8
+LRP_FP64, LRP_MIXED = 0, 1
+LRP_SEL_LEVERAGE, LRP_SEL_QDEIM = 0, 1
+KERNEL_CLASSES = ["dst", "cross", "gram", "reduce", "gemm", "leverage", "chol", "core", "select", "stop",
+                  "other"]
+
+
+class LrpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}: {last_error()}")
+
+
+class lrp_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("selector", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("max_rhs_rank", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("m_cap", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class lrp_info(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("r_star", ctypes.c_int32),
+                ("size_I", ctypes.c_int32), ("size_J", ctypes.c_int32),
+                ("total_iterations", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("rho", ctypes.c_double), ("eta_smin", ctypes.c_double),
+                ("sigma_max", ctypes.c_double), ("reserved1", ctypes.c_double)]
+
+
+class lrp_problem(ctypes.Structure):
+    _fields_ = [("r_f", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("d_U_f", ctypes.c_void_p), ("ldu_f", ctypes.c_int64),
+                ("d_s_f", ctypes.c_void_p), ("d_V_f", ctypes.c_void_p),
+                ("ldv_f", ctypes.c_int64), ("d_U", ctypes.c_void_p), ("ldu", ctypes.c_int64),
+                ("d_S", ctypes.c_void_p), ("d_V", ctypes.c_void_p), ("ldv", ctypes.c_int64),
+                ("d_info", ctypes.c_void_p)]
+
+
+INFO_BYTES = ctypes.sizeof(lrp_info)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python paper_2607_06021_gb300/build.py` (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, VP = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "lrp_default_opts": ([ctypes.POINTER(lrp_opts)], I32),
+        "lrp_plan": ([ctypes.POINTER(P), I64, D, I32, ctypes.POINTER(lrp_opts)], I32),
+        "lrp_plan_destroy": ([P], I32),
+        "lrp_plan_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I32),
+        "lrp_solve": ([P, I32, VP, I64, VP, VP, I64, VP, I64, VP, VP, I64, VP, VP], I32),
+        "lrp_solve_batch": ([P, I32, ctypes.POINTER(lrp_problem), VP], I32),
+        "lrp_dst1": ([I64, I32, VP, I64, VP, I64, VP], I32),
+        "lrp_plan_set_timing": ([P, I32], I32),
+        "lrp_plan_kernel_stats": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], I32),
+        "lrp_plan_reset_stats": ([P], I32),
+        "lrp_plan_kernel_work": ([P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+        "lrp_last_error": ([], ctypes.c_char_p),
+        "lrp_status_string": ([I32], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def last_error() -> str:
+    return _lib.lrp_last_error().decode()
+
+
+def status_string(s: int) -> str:
+    return _lib.lrp_status_string(int(s)).decode()
+
+
+def _check(s: int, where: str, ok=(LRP_OK,)):
+    if s not in ok:
+        raise LrpError(s, where)
+    return s
+
+
+def lrp_default_opts() -> lrp_opts:
+    o = lrp_opts()
+    _check(_lib.lrp_default_opts(ctypes.byref(o)), "lrp_default_opts")
+    return o
+
+
+def lrp_plan(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_plan(ctypes.byref(h), int(n), float(tol), int(max_rank),
+                         ctypes.byref(opts) if opts is not None else None), "lrp_plan")
+    return h
+
+
+def lrp_plan_destroy(plan) -> None:
+    _check(_lib.lrp_plan_destroy(plan), "lrp_plan_destroy")
+
+
+def lrp_plan_workspace_bytes(plan) -> int:
+    v = ctypes.c_size_t()
+    _check(_lib.lrp_plan_workspace_bytes(plan, ctypes.byref(v)), "lrp_plan_workspace_bytes")
+    return int(v.value)
+
+
+def lrp_solve(plan, r_f, d_U_f, ldu_f, d_s_f, d_V_f, ldv_f, d_U, ldu, d_S, d_V, ldv, d_info, stream) -> int:
+    return _check(_lib.lrp_solve(plan, int(r_f), d_U_f, int(ldu_f), d_s_f, d_V_f, int(ldv_f), d_U, int(ldu),
+                                 d_S, d_V, int(ldv), d_info, stream), "lrp_solve")
+
+
+def lrp_solve_batch(plan, problems, stream) -> int:
+    arr = (lrp_problem * len(problems))(*problems)
+    return _check(_lib.lrp_solve_batch(plan, len(problems), arr, stream), "lrp_solve_batch")
+
+
+def lrp_dst1(n, ncols, d_X, ldx, d_Y, ldy, stream) -> int:
+    return _check(_lib.lrp_dst1(int(n), int(ncols), d_X, int(ldx), d_Y, int(ldy), stream), "lrp_dst1")
+
+
+def lrp_plan_set_timing(plan, enable: bool) -> None:
+    _check(_lib.lrp_plan_set_timing(plan, 1 if enable else 0), "lrp_plan_set_timing")
+
+
+def lrp_plan_kernel_stats(plan, kclass: int):
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(_lib.lrp_plan_kernel_stats(plan, int(kclass), ctypes.byref(n), ctypes.byref(ms)),
+           "lrp_plan_kernel_stats")
+    return int(n.value), float(ms.value)
+
+
+def lrp_plan_kernel_work(plan, kclass: int):
+    f = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(_lib.lrp_plan_kernel_work(plan, int(kclass), ctypes.byref(f), ctypes.byref(b)), "lrp_plan_kernel_work")
+    return float(f.value), float(b.value)
+
+
+def lrp_plan_reset_stats(plan) -> None:
+    _check(_lib.lrp_plan_reset_stats(plan), "lrp_plan_reset_stats")
+
+
+from .api import Plan, dst1, colmajor, parse_info, solve  # noqa: E402,F401

@@ -1,0 +1,144 @@
+"""PyTorch-tensor convenience layer over the C ABI (allocation and marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK,
+               LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
+               lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
+               lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch)
+
+
+def colmajor(x: torch.Tensor) -> torch.Tensor:
+    """Column-major copy of a 2-D tensor (strides (1, rows))."""
+    return x.t().contiguous().t()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.dtype != torch.float64 or not t.is_cuda:
+        raise ValueError("expected a 2-D CUDA float64 tensor")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError("expected a column-major tensor (stride(0) == 1)")
+    return int(t.stride(1)) if t.shape[1] > 1 else int(t.shape[0])
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def parse_info(raw: torch.Tensor) -> dict:
+    b = bytes(raw.cpu().numpy().tobytes())
+    inf = lrp_info.from_buffer_copy(b)
+    return {f: getattr(inf, f) for f, _ in lrp_info._fields_}
+
+
+class Plan:
+    """A solver plan for grids with n interior points per dimension."""
+
+    def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
+                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
+                 check_every: int = 1, refine_steps: int = 1):
+        o = lrp_default_opts()
+        o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
+        o.batch = batch
+        o.max_rhs_rank = max_rhs_rank
+        o.max_iter = max_iter
+        o.m_cap = m_cap
+        o.seed = seed
+        o.check_every = check_every
+        o.refine_steps = refine_steps
+        self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
+        self.handle = lrp_plan(n, tol, max_rank, o)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return lrp_plan_workspace_bytes(self.handle)
+
+    def set_timing(self, enable: bool) -> None:
+        lrp_plan_set_timing(self.handle, enable)
+
+    def reset_stats(self) -> None:
+        lrp_plan_reset_stats(self.handle)
+
+    def kernel_stats(self) -> dict:
+        """{class: (launches, total_ms, algorithmic_flops, algorithmic_bytes)} since the last reset."""
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            out[name] = lrp_plan_kernel_stats(self.handle, i) + lrp_plan_kernel_work(self.handle, i)
+        out["all"] = lrp_plan_kernel_stats(self.handle, -1) + lrp_plan_kernel_work(self.handle, -1)
+        return out
+
+    def close(self):
+        if self.handle is not None:
+            lrp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_outputs(self, device="cuda"):
+        n, r = self.n, self.max_rank
+        U = torch.zeros((r, n), dtype=torch.float64, device=device).t()
+        V = torch.zeros((r, n), dtype=torch.float64, device=device).t()
+        S = torch.zeros(r, dtype=torch.float64, device=device)
+        info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=device)
+        return U, S, V, info
+
+    def problem(self, U_f, s_f, V_f, outs) -> lrp_problem:
+        U, S, V, info = outs
+        p = lrp_problem()
+        p.r_f = int(U_f.shape[1])
+        p.d_U_f, p.ldu_f = U_f.data_ptr(), _ld(U_f)
+        p.d_s_f = s_f.data_ptr()
+        p.d_V_f, p.ldv_f = V_f.data_ptr(), _ld(V_f)
+        p.d_U, p.ldu = U.data_ptr(), _ld(U)
+        p.d_S = S.data_ptr()
+        p.d_V, p.ldv = V.data_ptr(), _ld(V)
+        p.d_info = info.data_ptr()
+        return p
+
+    def solve_batch_into(self, inputs, outputs, stream=None) -> None:
+        """Enqueue a batch; inputs/outputs are lists of (U_f, s_f, V_f) / alloc_outputs()."""
+        probs = [self.problem(*i, o) for i, o in zip(inputs, outputs)]
+        lrp_solve_batch(self.handle, probs, _stream(stream))
+
+    def solve_batch(self, inputs, stream=None):
+        outs = [self.alloc_outputs() for _ in inputs]
+        self.solve_batch_into(inputs, outs, stream)
+        torch.cuda.synchronize()
+        res = []
+        for U, S, V, info in outs:
+            inf = parse_info(info)
+            r = inf["rank"]
+            res.append((U[:, :r], S[:r], V[:, :r], inf))
+        return res
+
+    def solve(self, U_f, s_f, V_f, stream=None):
+        return self.solve_batch([(U_f, s_f, V_f)], stream)[0]
+
+
+def solve(U_f, s_f, V_f, tol: float, max_rank: int, **kw):
+    """One-off solve: W ~= U diag(S) V^T for T W + W T = h^2 U_f diag(s_f) V_f^T."""
+    n = U_f.shape[0]
+    p = Plan(n, tol, max_rank, max_rhs_rank=max(int(U_f.shape[1]), 1), **kw)
+    try:
+        return p.solve(U_f, s_f, V_f)
+    finally:
+        p.close()
+
+
+def dst1(X: torch.Tensor, stream=None) -> torch.Tensor:
+    """Orthonormal DST-I of the columns of a column-major float64 CUDA tensor."""
+    n, c = X.shape
+    Y = torch.empty((c, n), dtype=torch.float64, device=X.device).t()
+    lrp_dst1(n, c, X.data_ptr(), _ld(X), Y.data_ptr(), _ld(Y) if c > 1 else n, _stream(stream))
+    return Y
+
+
+__all__ = ["Plan", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]

@@ -1,0 +1,145 @@
+// Shared definitions of the sm_103a kernels and the host driver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lrp.h"
+
+#ifndef LRP_MAX_M
+#define LRP_MAX_M 256  // hard cap on index-set sizes and ranks (m_cap)
+#endif
+
+namespace lrp {
+
+constexpr int kMaxM = LRP_MAX_M;
+constexpr int kMaxRF = 256;
+
+// Per-problem iteration state, one per batch slot, in device memory.
+// Side 0 is the row space (cross matrix C = What(:,J), factor U_k, index set
+// I); side 1 is the column space (R^T = What(I,:)^T, factor V_k, index set J).
+struct SolveState {
+  int32_t active;        // 1 while the Cross-DEIM loop runs for this slot
+  int32_t k;             // next iteration number
+  int32_t cnt[2];        // |I|, |J|
+  int32_t r;             // rank of the current iterate
+  int32_t r_prev;        // rank of the previous iterate (0 = none)
+  int32_t rf;            // right-hand-side rank
+  int32_t flags;         // kFlag* bits
+  int32_t iters;         // iterations done in this solve
+  int32_t r_out;         // final rank
+  int32_t r_star;        // tail-rule rank before the cap
+  int32_t total_iters;   // across initial and refinement solves
+  int32_t branch;        // scross branch taken (0: |J|<=|I|, 1: mirror)
+  int32_t cnt_next[2];   // |I|, |J| after the redundancy removal (applied by k_stop,
+                         // after the factor update has used the pre-removal sizes)
+  int32_t mx[2];         // generic column counts of the refinement's tall matrices
+  int32_t r0;            // rank of the trial solution being refined
+  int32_t valid;         // slot holds a problem of this call
+  int32_t rf0;           // rank of the caller's right-hand side
+  int32_t upar;          // ping-pong parity of the FP32 iterate being stacked
+  int32_t rd;            // rank of the correction
+  int32_t first_converged;  // the first (FP32) solve met its stop test
+  double rho;
+  double eta_smin;
+  double snorm;          // ||S_k||_F
+  double snorm_prev;
+  double gram_trace[2];  // trace of the pass-1 Gram (shift scale)
+};
+
+enum : int32_t {
+  kFlagConverged = 1,
+  kFlagRankCapped = 2,
+  kFlagCapacity = 4,   // index set hit m_cap
+  kFlagBadInput = 8,
+};
+
+// Size selectors for the generic tall kernels: which per-side dimension of
+// the state a kernel's column count comes from.
+enum DimSel : int32_t {
+  kDimOther = 0,  // cnt[1-s]: columns of side s's cross matrix
+  kDimR = 1,      // r
+  kDimRPrev = 2,  // r_prev
+  kDimRF = 3,     // rf
+  kDimX = 4,      // mx[s]
+};
+
+__host__ __device__ inline int dim_of(const SolveState& st, int side, int sel) {
+  switch (sel) {
+    case kDimOther: return st.cnt[1 - side];
+    case kDimR: return st.r;
+    case kDimRPrev: return st.r_prev;
+    case kDimX: return st.mx[side];
+    default: return st.rf;
+  }
+}
+
+// Strided batch addressing: element (slot, side) of an array of equal blocks.
+template <typename T>
+struct Strided {
+  T* base;
+  int64_t side_stride;  // elements between side 0 and side 1
+  int64_t slot_stride;  // elements between consecutive slots
+  __host__ __device__ T* at(int slot, int side) const {
+    return base + (int64_t)slot * slot_stride + (int64_t)side * side_stride;
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024); `scratch` >= 32 doubles.
+__device__ inline double block_sum(double v, double* scratch) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline double block_max(double v, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : -1.0e308;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  }
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): add the golden
+// gamma, then two xor-shift-multiply rounds and a final xor-shift.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace lrp

@@ -1,0 +1,794 @@
+// Per-problem kernels of the Cross-DEIM iteration: one CTA per problem (or per
+// problem and side), FP64 small dense linear algebra on m x m matrices
+// (m = |I|, |J| <= m_cap) held in an L2-resident per-problem scratch area.
+//
+//  k_chol      one pass of shifted CholeskyQR: Cholesky of the reduced Gram
+//              with pivot dropping, R^{-1}, and the accumulated R = R_k ... R_1
+//              whose diagonal is Algorithm scross's r_C / r_R.
+//  k_core      the small part of Algorithm scross: Q(I,:), the pseudoinverse
+//              solve (branch |J| <= |I| or its mirror), the SVD of the core,
+//              the in-loop truncation, the redundancy removal of Algorithm
+//              Cross-DEIM and the DEIM constants eta_1, eta_2.
+//  k_select    index enrichment of Algorithm Cross-DEIM: top-c leverage
+//              candidates, ordered union with the previous set and the growth
+//              safeguard (one index from the complement).
+//  k_stop      rho = ||A_k - A_{k-1}||_F / ||S_k||_F from small Gram terms and
+//              the stop test max(rho, min(eta1(1+eta2), eta2(1+eta1)) S_min) < eps.
+//  k_finalize  final truncation sum_{l>r} S_l^2 < eps^2 ||S||^2, r = max(min(r*, r_max), 1).
+//
+// Singular value decompositions use one-sided (Hestenes) Jacobi with the
+// round-robin pair ordering; each warp rotates one column pair at a time.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "core.cuh"
+#include "dense.cuh"
+#include "dst.cuh"
+
+namespace lrp {
+
+namespace {
+constexpr int CT = 256;  // threads of the core CTAs
+}  // namespace
+
+// ------------------------------------------------------- work accounting
+
+__device__ inline void acct_add(double* row, int cls, double flops, double bytes) {
+  row[2 * cls] += flops;
+  row[2 * cls + 1] += bytes;
+}
+
+__device__ inline double dst_col_flops(int n) {
+  const double N = (double)(n + 1);
+  return 5.0 * N * log2(N);  // one complex FFT of length N per column
+}
+
+// Three symmetric Gram passes, two triangular applies, on side sizes m0, m1.
+__device__ inline void acct_cholqr3(double* row, double n, double m0, double m1, int NB, double w) {
+  for (double m : {m0, m1}) {
+    acct_add(row, LRP_K_GRAM, 3.0 * n * m * (m + 1.0), 3.0 * (n * m * w + NB * m * (m + 1.0) / 2.0 * 8.0));
+    acct_add(row, LRP_K_REDUCE, 3.0 * NB * m * (m + 1.0) / 2.0, 3.0 * (NB + 1.0) * m * (m + 1.0) / 2.0 * 8.0);
+    acct_add(row, LRP_K_GEMM, 2.0 * n * m * (m + 1.0), 2.0 * 2.0 * n * m * w);
+  }
+}
+
+__device__ void acct_setup(double* row, int n_, int rf_, int NB, int w_) {
+  const double n = n_, rf = rf_, w = w_;
+  acct_add(row, LRP_K_DST, 2.0 * rf * dst_col_flops(n_), 2.0 * rf * n * (8.0 + w));
+  acct_cholqr3(row, n, rf, rf, NB, w);
+  acct_add(row, LRP_K_GEMM, 2.0 * n * rf * (rf + 1.0), 2.0 * 2.0 * n * rf * w);  // U_{-1} = Q2 P3
+  acct_add(row, LRP_K_LEVERAGE, 2.0 * 2.0 * n * rf, 2.0 * n * rf * w);
+}
+
+__device__ void acct_iteration(double* row, int n_, int p_, int q_, int r_, int rp_, int rf_, int NB, int w_) {
+  const double n = n_, p = p_, q = q_, r = r_, rp = rp_, rf = rf_, w = w_;
+  // side 0 columns: p = |J|; side 1 columns: q = |I|
+  acct_add(row, LRP_K_CROSS, 2.0 * n * rf * (p + q), w * (2.0 * n * rf + n * (p + q) + n));
+  acct_cholqr3(row, n, p, q, NB, w);
+  acct_add(row, LRP_K_GEMM, 2.0 * n * r * (p + q), w * n * (p + q + 2.0 * r));  // U_k = Q2 Bf
+  acct_add(row, LRP_K_LEVERAGE, 2.0 * 2.0 * n * r, 2.0 * n * r * w);
+  if (rp_ > 0) {
+    acct_add(row, LRP_K_GRAM, 2.0 * 2.0 * n * r * rp, 2.0 * (n * (r + rp) * w + NB * r * rp * 8.0));
+    acct_add(row, LRP_K_REDUCE, 2.0 * NB * r * rp, 2.0 * (NB + 1.0) * r * rp * 8.0);
+    acct_add(row, LRP_K_GEMM, 2.0 * 2.0 * n * r * rp, 2.0 * n * (r + 2.0 * rp) * w);
+    acct_add(row, LRP_K_GRAM, 2.0 * n * rp * (rp + 1.0), 2.0 * (n * rp * w + NB * rp * (rp + 1.0) / 2.0 * 8.0));
+    acct_add(row, LRP_K_REDUCE, 2.0 * NB * rp * (rp + 1.0) / 2.0, 2.0 * (NB + 1.0) * rp * (rp + 1.0) / 2.0 * 8.0);
+  }
+}
+
+__device__ void acct_back(double* row, int n_, int r_out, int w_) {
+  const double n = n_, w = w_;
+  acct_add(row, LRP_K_DST, 2.0 * r_out * dst_col_flops(n_), 2.0 * r_out * n * (8.0 + w));
+}
+
+// ------------------------------------------------------------------- kernels
+
+template <typename T>
+__global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int sel, int pass) {
+  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  SolveState* stp = p.st + slot;
+  if (!stp->active) return;
+  const int M = p.g.M;
+  const int m = dim_of(*stp, side, sel);
+  const double* G = b.G.at(slot, side);
+  double* base = b.scratch + (int64_t)slot * b.scratch_stride;
+  double* W = base + (int64_t)(8 + side) * M * M;     // working triangle
+  double* Tm = base + (int64_t)(10 + side) * M * M;   // R^{-1} (FP64), then R * Racc
+  double* P = b.P.at(slot, side);
+  double* Racc = b.Racc.at(slot, side);
+  __shared__ double red[32];
+  __shared__ int dropped[kMaxM];
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // Pass 0 equilibrates: W = D G D with D = diag(G_jj^{-1/2}) (zero columns are
+  // dropped), so R = R' D^{-1} and R^{-1} = D R'^{-1}; the relative diagonal test
+  // on R is unchanged and the shift acts on unit-diagonal data.
+  __shared__ double dsc[kMaxM];
+  for (int j = tid; j < m; j += nt) {
+    const double gjj = G[(int64_t)j * M + j];
+    dsc[j] = (pass == 0) ? ((gjj > 0.0) ? 1.0 / sqrt(gjj) : 0.0) : 1.0;
+  }
+  __syncthreads();
+  double tr = 0.0, mx = 0.0;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    const double v = G[(int64_t)j * M + i] * dsc[i] * dsc[j];
+    W[(int64_t)j * M + i] = (i <= j) ? v : 0.0;
+    if (i == j) {
+      tr += v;
+      mx = fmax(mx, v);
+    }
+  }
+  tr = block_sum(tr, red);
+  mx = block_max(mx, red);
+  const double shift = (pass == 0) ? p.shift_rel * tr : 0.0;
+  if (pass == 0 && tid == 0) stp->gram_trace[side] = tr;
+  for (int j = tid; j < m; j += nt) W[(int64_t)j * M + j] += (dsc[j] > 0.0) ? shift : 0.0;
+  const double thr = (pass == 0) ? 0.0 : p.drop_rel * mx;
+  __syncthreads();
+
+  for (int j = 0; j < m; ++j) {
+    const double d = W[(int64_t)j * M + j];
+    const bool drop = !(d > thr);
+    const double rjj = drop ? 0.0 : sqrt(d);
+    __syncthreads();
+    for (int l = j + 1 + tid; l < m; l += nt) {
+      double* wl = W + (int64_t)l * M + j;
+      *wl = drop ? 0.0 : (*wl / rjj);
+    }
+    if (tid == 0) {
+      W[(int64_t)j * M + j] = rjj;
+      dropped[j] = drop ? 1 : 0;
+    }
+    __syncthreads();
+    if (!drop) {
+      const int t = m - j - 1;
+      for (int e = tid; e < t * t; e += nt) {
+        const int kk = e % t, ll = e / t;
+        if (kk > ll) continue;
+        const int k = j + 1 + kk, l = j + 1 + ll;
+        W[(int64_t)l * M + k] -= W[(int64_t)k * M + j] * W[(int64_t)l * M + j];
+      }
+    }
+    __syncthreads();
+  }
+
+  // P = R^{-1}: column l by back substitution (dropped rows give zeros).
+  for (int l = tid; l < m; l += nt) {
+    double* x = Tm + (int64_t)l * M;
+    for (int i = m - 1; i > l; --i) x[i] = 0.0;
+    for (int i = l; i >= 0; --i) {
+      if (dropped[i]) {
+        x[i] = 0.0;
+        continue;
+      }
+      double s = (i == l) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= l; ++k) s -= W[(int64_t)k * M + i] * x[k];
+      x[i] = s / W[(int64_t)i * M + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * M + i];
+  }
+  __syncthreads();
+  // Racc <- R (pass 0, undoing the equilibration) or R * Racc.
+  if (pass == 0) {
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e % m, j = e / m;
+      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? W[(int64_t)j * M + i] / dsc[j] : 0.0;
+    }
+  } else {
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e % m, l = e / m;
+      double s = 0.0;
+      if (i <= l)
+        for (int k = i; k <= l; ++k) s += W[(int64_t)k * M + i] * Racc[(int64_t)l * M + k];
+      Tm[(int64_t)l * M + i] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e % m, j = e / m;
+      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * M + i];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int parity) {
+  const int slot = blockIdx.x;
+  SolveState* stp = p.st + slot;
+  if (!stp->active) return;
+  const int M = p.g.M;
+  const int64_t MM = (int64_t)M * M;
+  const int q = stp->cnt[0];   // |I|
+  const int pc = stp->cnt[1];  // |J|
+  if (q < 1 || pc < 1) {
+    if (threadIdx.x == 0) {
+      stp->active = 0;
+      stp->flags |= kFlagBadInput;
+    }
+    return;
+  }
+  double* base = b.scratch + (int64_t)slot * b.scratch_stride;
+  double* QI = base + 0 * MM;  // q x pc
+  double* ZJ = base + 1 * MM;  // pc x q
+  double* W1 = base + 2 * MM;
+  double* V1 = base + 3 * MM;
+  double* Mt = base + 4 * MM;
+  double* V2 = base + 5 * MM;
+  double* T1 = base + 6 * MM;
+  double* UI = base + 7 * MM;  // U_k(I,:)  q x r
+  double* VJ = base + 8 * MM;  // V_k(J,:)  pc x r
+  double* WK = base + 9 * MM;  // eta work
+  const T* Q20 = b.Q2.at(slot, 0);
+  const T* Q21 = b.Q2.at(slot, 1);
+  const double* P0 = b.P.at(slot, 0);
+  const double* P1 = b.P.at(slot, 1);
+  const double* RC = b.Racc.at(slot, 0);
+  const double* RR = b.Racc.at(slot, 1);
+  int32_t* I = b.idx.at(slot, 0);
+  int32_t* J = b.idx.at(slot, 1);
+  const int64_t ld = p.g.ld;
+  __shared__ double sig1[kMaxM];
+  __shared__ double sig2[kMaxM];
+  __shared__ int perm[kMaxM];
+  __shared__ int keep[kMaxM];
+  __shared__ int flag;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // Q(I,:) = Q2_0(I,:) P3_0 and Z(J,:) = Q2_1(J,:) P3_1 (P3 upper triangular).
+  for (int e = tid; e < q * pc; e += nt) {
+    const int a = e % q, c = e / q;
+    const int64_t row = I[a];
+    double s = 0.0;
+    for (int d = 0; d <= c; ++d) s += (double)Q20[(int64_t)d * ld + row] * P0[(int64_t)c * M + d];
+    QI[(int64_t)c * M + a] = s;
+  }
+  for (int e = tid; e < pc * q; e += nt) {
+    const int a = e % pc, c = e / pc;
+    const int64_t row = J[a];
+    double s = 0.0;
+    for (int d = 0; d <= c; ++d) s += (double)Q21[(int64_t)d * ld + row] * P1[(int64_t)c * M + d];
+    ZJ[(int64_t)c * M + a] = s;
+  }
+  __syncthreads();
+  const double eps64 = 2.220446049250313e-16;
+  const int mx = max(pc, q);
+  const int branch = (pc <= q) ? 0 : 1;
+  int nsv;
+  if (branch == 0) {
+    // pinv(Q(I,:)) R_R^T: Q(I,:) = U1 S1 V1^T (q x pc), then M = V1 S1^+ U1^T R_R^T (pc x q).
+    for (int e = tid; e < q * pc; e += nt) {
+      const int i = e % q, j = e / q;
+      W1[(int64_t)j * M + i] = QI[(int64_t)j * M + i];
+    }
+    __syncthreads();
+    blk_jacobi(W1, M, q, pc, V1, M, sig1, &flag);
+    double smax = 0.0;
+    for (int j = tid; j < pc; j += nt) smax = fmax(smax, sig1[j]);
+    smax = block_max(smax, red);
+    const double cut = mx * eps64 * smax;
+    // T1(a, c) = sum_{d >= c} W1(d, a) R_R(c, d) / sig1[a]^2   (pc x q)
+    for (int e = tid; e < pc * q; e += nt) {
+      const int a = e % pc, c = e / pc;
+      double s = 0.0;
+      if (sig1[a] > cut) {
+        for (int d = c; d < q; ++d) s += W1[(int64_t)a * M + d] * RR[(int64_t)d * M + c];
+        s /= sig1[a] * sig1[a];
+      }
+      T1[(int64_t)c * M + a] = s;
+    }
+    __syncthreads();
+    // Mt = M^T (q x pc): Mt(c, i) = sum_a V1(i, a) T1(a, c)
+    for (int e = tid; e < q * pc; e += nt) {
+      const int c = e % q, i = e / q;
+      double s = 0.0;
+      for (int a = 0; a < pc; ++a) s += V1[(int64_t)a * M + i] * T1[(int64_t)c * M + a];
+      Mt[(int64_t)i * M + c] = s;
+    }
+    __syncthreads();
+    blk_jacobi(Mt, M, q, pc, V2, M, sig2, &flag);
+    nsv = pc;
+  } else {
+    // Mirror: M = R_C pinv(Z(J,:))^T with Z(J,:) = U2 S2 V2^T (pc x q).
+    for (int e = tid; e < pc * q; e += nt) {
+      const int i = e % pc, j = e / pc;
+      W1[(int64_t)j * M + i] = ZJ[(int64_t)j * M + i];
+    }
+    __syncthreads();
+    blk_jacobi(W1, M, pc, q, V1, M, sig1, &flag);
+    double smax = 0.0;
+    for (int j = tid; j < q; j += nt) smax = fmax(smax, sig1[j]);
+    smax = block_max(smax, red);
+    const double cut = mx * eps64 * smax;
+    // T1(i, a) = sum_{c >= i} R_C(i, c) W1(c, a) / sig1[a]^2  (pc x q)
+    for (int e = tid; e < pc * q; e += nt) {
+      const int i = e % pc, a = e / pc;
+      double s = 0.0;
+      if (sig1[a] > cut) {
+        for (int c = i; c < pc; ++c) s += RC[(int64_t)c * M + i] * W1[(int64_t)a * M + c];
+        s /= sig1[a] * sig1[a];
+      }
+      T1[(int64_t)a * M + i] = s;
+    }
+    __syncthreads();
+    // Mt = M (pc x q): M(i, bb) = sum_a T1(i, a) V1(bb, a)
+    for (int e = tid; e < pc * q; e += nt) {
+      const int i = e % pc, bb = e / pc;
+      double s = 0.0;
+      for (int a = 0; a < q; ++a) s += T1[(int64_t)a * M + i] * V1[(int64_t)a * M + bb];
+      Mt[(int64_t)bb * M + i] = s;
+    }
+    __syncthreads();
+    blk_jacobi(Mt, M, pc, q, V2, M, sig2, &flag);
+    nsv = q;
+  }
+  blk_sort_desc(sig2, nsv, perm);
+  const double s1 = sig2[perm[0]];
+  int r = 0;
+  {
+    const double cut = (double)mx * p.eps_data * s1;
+    for (int t = 0; t < nsv; ++t) r += (sig2[perm[t]] >= cut && sig2[perm[t]] > 0.0) ? 1 : 0;
+    if (r < 1) r = 1;
+  }
+  // U~ (pc x r) and V~ (q x r): branch 0: U~ = V2, V~ = Mt/sig; branch 1: U~ = Mt/sig, V~ = V2.
+  // Reuse W1 for U~ and V1 for V~ (their previous contents are no longer needed).
+  double* Ut = W1;
+  double* Vt = V1;
+  for (int e = tid; e < pc * r; e += nt) {
+    const int i = e % pc, t = e / pc;
+    const int j = perm[t];
+    const double sv = sig2[j];
+    Ut[(int64_t)t * M + i] = (branch == 0) ? V2[(int64_t)j * M + i] : (sv > 0 ? Mt[(int64_t)j * M + i] / sv : 0.0);
+  }
+  for (int e = tid; e < q * r; e += nt) {
+    const int i = e % q, t = e / q;
+    const int j = perm[t];
+    const double sv = sig2[j];
+    Vt[(int64_t)t * M + i] = (branch == 0) ? (sv > 0 ? Mt[(int64_t)j * M + i] / sv : 0.0) : V2[(int64_t)j * M + i];
+  }
+  double* sig_out = b.sig + (int64_t)slot * 2 * M + (int64_t)parity * M;
+  for (int t = tid; t < r; t += nt) sig_out[t] = sig2[perm[t]];
+  __syncthreads();
+  // Bf0 = P3_0 U~ (pc x r), Bf1 = P3_1 V~ (q x r)
+  double* B0 = b.Bf.at(slot, 0);
+  double* B1 = b.Bf.at(slot, 1);
+  for (int e = tid; e < pc * r; e += nt) {
+    const int i = e % pc, t = e / pc;
+    double s = 0.0;
+    for (int d = i; d < pc; ++d) s += P0[(int64_t)d * M + i] * Ut[(int64_t)t * M + d];
+    B0[(int64_t)t * M + i] = s;
+  }
+  for (int e = tid; e < q * r; e += nt) {
+    const int i = e % q, t = e / q;
+    double s = 0.0;
+    for (int d = i; d < q; ++d) s += P1[(int64_t)d * M + i] * Vt[(int64_t)t * M + d];
+    B1[(int64_t)t * M + i] = s;
+  }
+  // U_k(I,:) = Q(I,:) U~ (q x r), V_k(J,:) = Z(J,:) V~ (pc x r)
+  for (int e = tid; e < q * r; e += nt) {
+    const int a = e % q, t = e / q;
+    double s = 0.0;
+    for (int c = 0; c < pc; ++c) s += QI[(int64_t)c * M + a] * Ut[(int64_t)t * M + c];
+    UI[(int64_t)t * M + a] = s;
+  }
+  for (int e = tid; e < pc * r; e += nt) {
+    const int a = e % pc, t = e / pc;
+    double s = 0.0;
+    for (int c = 0; c < q; ++c) s += ZJ[(int64_t)c * M + a] * Vt[(int64_t)t * M + c];
+    VJ[(int64_t)t * M + a] = s;
+  }
+  __syncthreads();
+
+  // Redundancy removal: keep I_l iff |R_R(l,l)| >= tau max|diag R_R|, J_l likewise with R_C.
+  double mR = 0.0, mC = 0.0;
+  for (int l = tid; l < q; l += nt) mR = fmax(mR, fabs(RR[(int64_t)l * M + l]));
+  for (int l = tid; l < pc; l += nt) mC = fmax(mC, fabs(RC[(int64_t)l * M + l]));
+  mR = block_max(mR, red);
+  mC = block_max(mC, red);
+  int qn = 0, pn = 0;
+  for (int l = tid; l < q; l += nt) keep[l] = (mR > 0.0 && fabs(RR[(int64_t)l * M + l]) >= p.redundancy * mR) ? 1 : 0;
+  __syncthreads();
+  if (tid == 0) {
+    int w = 0;
+    for (int l = 0; l < q; ++l) {
+      if (keep[l]) {
+        I[w] = I[l];
+        perm[w] = l;  // source row of U_k(I,:)
+        ++w;
+      }
+    }
+    flag = w;
+  }
+  __syncthreads();
+  qn = flag;
+  // compact rows of UI into WK (qn x r), then back
+  for (int e = tid; e < qn * r; e += nt) {
+    const int a = e % qn, t = e / qn;
+    WK[(int64_t)t * M + a] = UI[(int64_t)t * M + perm[a]];
+  }
+  __syncthreads();
+  for (int e = tid; e < qn * r; e += nt) {
+    const int a = e % qn, t = e / qn;
+    UI[(int64_t)t * M + a] = WK[(int64_t)t * M + a];
+  }
+  for (int l = tid; l < pc; l += nt) keep[l] = (mC > 0.0 && fabs(RC[(int64_t)l * M + l]) >= p.redundancy * mC) ? 1 : 0;
+  __syncthreads();
+  if (tid == 0) {
+    int w = 0;
+    for (int l = 0; l < pc; ++l) {
+      if (keep[l]) {
+        J[w] = J[l];
+        perm[w] = l;
+        ++w;
+      }
+    }
+    flag = w;
+  }
+  __syncthreads();
+  pn = flag;
+  for (int e = tid; e < pn * r; e += nt) {
+    const int a = e % pn, t = e / pn;
+    WK[(int64_t)t * M + a] = VJ[(int64_t)t * M + perm[a]];
+  }
+  __syncthreads();
+  for (int e = tid; e < pn * r; e += nt) {
+    const int a = e % pn, t = e / pn;
+    VJ[(int64_t)t * M + a] = WK[(int64_t)t * M + a];
+  }
+  __syncthreads();
+  // eta_1 = 1/sigma_min(U_k(I,:)), eta_2 = 1/sigma_min(V_k(J,:)), with the reduced sets.
+  const double sm1 = blk_smin(UI, M, qn, r, WK, M, sig1, &flag);
+  const double sm2 = blk_smin(VJ, M, pn, r, WK, M, sig1, &flag);
+  double snorm2 = 0.0;
+  for (int t = tid; t < r; t += nt) snorm2 += sig_out[t] * sig_out[t];
+  snorm2 = block_sum(snorm2, red);
+  if (tid == 0) {
+    const double snorm = sqrt(snorm2);
+    const double e1 = (sm1 > 0.0) ? 1.0 / sm1 : INFINITY;
+    const double e2 = (sm2 > 0.0) ? 1.0 / sm2 : INFINITY;
+    const double smin = snorm > 0.0 ? sig_out[r - 1] / snorm : 0.0;
+    const double f = fmin(e1 * (1.0 + e2), e2 * (1.0 + e1));
+    stp->eta_smin = snorm > 0.0 ? f * smin : 0.0;
+    stp->snorm = snorm;
+    if (b.acct)
+      acct_iteration(b.acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, pc, q, r, stp->r_prev, stp->rf, p.g.NB,
+                     (int)sizeof(T));
+    stp->r = r;
+    stp->cnt_next[0] = qn;
+    stp->cnt_next[1] = pn;
+    stp->branch = branch;
+  }
+}
+
+// Index enrichment (Algorithm Cross-DEIM): side s merges its leverage candidates.
+template <typename T>
+__global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
+  extern __shared__ unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int* id = reinterpret_cast<int*>(key + sort_len);
+  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  SolveState* stp = p.st + slot;
+  if (!stp->active) return;
+  const int M = p.g.M;
+  const int n = p.g.n;
+  const int c = dim_of(*stp, side, sel_c);
+  const int total = p.cand_blocks * p.cand_per_block;
+  const int64_t base = (int64_t)(slot * 2 + side) * total;
+  for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+    key[t] = (t < total) ? b.cand_score[base + t] : -1.0;
+    id[t] = (t < total) ? b.cand_idx[base + t] : -1;
+    if (id[t] < 0) {
+      key[t] = -1.0;
+      id[t] = 0x7fffffff;
+    }
+  }
+  __syncthreads();
+  // bitonic sort (score desc, index asc)
+  for (int size = 2; size <= sort_len; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+        const int pp = t ^ stride;
+        if (pp > t) {
+          const bool up = ((t & size) == 0);
+          const bool tf = (key[t] > key[pp]) || (key[t] == key[pp] && id[t] < id[pp]);
+          if (up != tf) {
+            const double kk = key[t];
+            key[t] = key[pp];
+            key[pp] = kk;
+            const int ii = id[t];
+            id[t] = id[pp];
+            id[pp] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  int32_t* set = b.idx.at(slot, side);
+  __shared__ int isnew[kMaxM];
+  const int cnt0 = stp->cnt[side];
+  const int cc = min(c, min(sort_len, kMaxM));
+  for (int t = threadIdx.x; t < cc; t += blockDim.x) {
+    int nw = (key[t] >= 0.0) ? 1 : 0;
+    if (nw) {
+      const int v = id[t];
+      for (int l = 0; l < cnt0; ++l)
+        if (set[l] == v) {
+          nw = 0;
+          break;
+        }
+    }
+    isnew[t] = nw;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cnt = cnt0;
+    for (int t = 0; t < cc && cnt < M; ++t)
+      if (isnew[t]) set[cnt++] = id[t];
+    if ((cnt == cnt0 || stp->k == 0) && cnt < M && cnt < n) {
+      // growth safeguard: SplitMix64 keyed by (seed, k, side), probed to the complement
+      uint64_t g = splitmix64(p.seed + 2ull * (uint64_t)stp->k + (uint64_t)side) % (uint64_t)n;
+      for (int probe = 0; probe < n; ++probe) {
+        bool present = false;
+        for (int l = 0; l < cnt; ++l)
+          if (set[l] == (int32_t)g) {
+            present = true;
+            break;
+          }
+        if (!present) break;
+        g = (g + 1) % (uint64_t)n;
+      }
+      set[cnt++] = (int32_t)g;
+    }
+    if (cnt >= M) stp->flags |= kFlagCapacity;
+    stp->cnt[side] = cnt;
+  }
+}
+
+template <typename T>
+__global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
+  const int slot = blockIdx.x;
+  SolveState* stp = p.st + slot;
+  if (!stp->active) return;
+  const int M = p.g.M;
+  const int r = stp->r, rp = stp->r_prev;
+  const double* sc = b.sig + (int64_t)slot * 2 * M + (int64_t)parity * M;
+  const double* sp = b.sig + (int64_t)slot * 2 * M + (int64_t)(1 - parity) * M;
+  __shared__ double red[32];
+  double rho = 1.0;
+  if (rp > 0) {
+    const double* X0 = b.X.at(slot, 0);
+    const double* X1 = b.X.at(slot, 1);
+    const double* GU = b.GE.at(slot, 0);
+    const double* GV = b.GE.at(slot, 1);
+    double acc = 0.0;
+    // ||S_k - X0 S' X1^T||^2
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int a = e % r, bb = e / r;
+      double v = (a == bb) ? sc[a] : 0.0;
+      for (int cc = 0; cc < rp; ++cc) v -= X0[(int64_t)cc * M + a] * sp[cc] * X1[(int64_t)cc * M + bb];
+      acc += v * v;
+    }
+    // tr(X0 S' GV S' X0^T) and tr(X1 S' GU S' X1^T)
+    for (int e = threadIdx.x; e < r * rp; e += blockDim.x) {
+      const int a = e % r, cc = e / r;
+      double s0 = 0.0, s1 = 0.0;
+      for (int d = 0; d < rp; ++d) {
+        s0 += GV[(int64_t)d * M + cc] * sp[d] * X0[(int64_t)d * M + a];
+        s1 += GU[(int64_t)d * M + cc] * sp[d] * X1[(int64_t)d * M + a];
+      }
+      acc += X0[(int64_t)cc * M + a] * sp[cc] * s0 + X1[(int64_t)cc * M + a] * sp[cc] * s1;
+    }
+    // tr(S' GU S' GV)
+    for (int e = threadIdx.x; e < rp * rp; e += blockDim.x) {
+      const int cc = e % rp, d = e / rp;
+      acc += sp[cc] * GU[(int64_t)d * M + cc] * sp[d] * GV[(int64_t)cc * M + d];
+    }
+    acc = block_sum(acc, red);
+    rho = stp->snorm > 0.0 ? sqrt(fmax(acc, 0.0)) / stp->snorm : 0.0;
+  }
+  if (stp->snorm == 0.0) rho = 0.0;  // zero right-hand side: W = 0 is exact
+  if (threadIdx.x == 0) {
+    stp->rho = rho;
+    stp->iters += 1;
+    stp->total_iters += 1;
+    stp->k += 1;
+    const bool conv = fmax(rho, stp->eta_smin) < p.tol;
+    if (conv) {
+      stp->flags |= kFlagConverged;
+      stp->active = 0;
+    } else if (stp->k >= p.max_iter) {
+      stp->active = 0;
+    }
+    stp->r_prev = r;
+    stp->snorm_prev = stp->snorm;
+    stp->cnt[0] = stp->cnt_next[0];
+    stp->cnt[1] = stp->cnt_next[1];
+  }
+}
+
+template <typename T>
+__global__ void k_finalize(CoreParams p, CoreBufs<T> b, DstBatch<T, double> back, T* const* ubufs,
+                           int64_t ubuf_side_stride, int64_t ubuf_slot_stride) {
+  const int slot = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  SolveState* stp = p.st + slot;
+  const ProblemDev& pr = b.prob[slot];
+  T** in = const_cast<T**>(reinterpret_cast<const T* const*>(back.in));
+  double** out = const_cast<double**>(back.out);
+  int64_t* ldi = const_cast<int64_t*>(back.ld_in);
+  int64_t* ldo = const_cast<int64_t*>(back.ld_out);
+  if (pr.rf <= 0 || stp->iters == 0) {
+    stp->r_out = 0;
+    in[slot] = nullptr;
+    in[back.nslots + slot] = nullptr;
+    out[slot] = nullptr;
+    out[back.nslots + slot] = nullptr;
+    return;
+  }
+  const int M = p.g.M;
+  const int parity = (stp->k - 1) & 1;
+  const double* s = b.sig + (int64_t)slot * 2 * M + (int64_t)parity * M;
+  const int r = stp->r;
+  double tot = 0.0;
+  for (int t = 0; t < r; ++t) tot += s[t] * s[t];
+  int rstar = r;
+  double tail = 0.0;  // sum_{l >= t} s_l^2, scanning from the end
+  for (int t = r; t >= 0; --t) {
+    if (t < r) tail += s[t] * s[t];
+    if (tail < p.tol * p.tol * tot) rstar = t;
+    else break;
+  }
+  if (rstar < 1) rstar = 1;
+  int rout = rstar < p.r_max ? rstar : p.r_max;
+  if (rout < 1) rout = 1;
+  stp->r_star = rstar;
+  stp->r_out = rout;
+  if (b.acct) acct_back(b.acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rout, (int)sizeof(T));
+  if (rstar > p.r_max) stp->flags |= kFlagRankCapped;
+  for (int t = 0; t < rout; ++t) pr.S[t] = s[t];
+  T* ub = ubufs[parity];
+  in[slot] = ub + (int64_t)slot * ubuf_slot_stride;
+  in[back.nslots + slot] = ub + (int64_t)slot * ubuf_slot_stride + ubuf_side_stride;
+  out[slot] = pr.U;
+  out[back.nslots + slot] = pr.V;
+  ldi[slot] = p.g.ld;
+  ldi[back.nslots + slot] = p.g.ld;
+  ldo[slot] = pr.ldu;
+  ldo[back.nslots + slot] = pr.ldv;
+  if (pr.info) {
+    lrp_info inf;
+    inf.rank = rout;
+    inf.iterations = stp->iters;
+    const bool conv = (stp->flags & kFlagConverged) != 0;
+    inf.status = !conv ? LRP_NOT_CONVERGED : ((rstar > p.r_max) ? LRP_RANK_CAPPED : LRP_OK);
+    inf.r_star = rstar;
+    inf.size_I = stp->cnt[0];
+    inf.size_J = stp->cnt[1];
+    inf.total_iterations = stp->total_iters;
+    inf.reserved0 = stp->flags;
+    inf.rho = stp->rho;
+    inf.eta_smin = stp->eta_smin;
+    inf.sigma_max = s[0];
+    inf.reserved1 = 0.0;
+    *pr.info = inf;
+  }
+}
+
+template <typename T>
+__global__ void k_setup(CoreParams p, const ProblemDev* prob, T* w, int wstride, int nactive, double* acct) {
+  const int slot = blockIdx.x;
+  SolveState* stp = p.st + slot;
+  const bool act = slot < nactive && prob[slot].rf > 0;
+  const int rf = act ? prob[slot].rf : 0;
+  const double h = 1.0 / (double)(p.g.n + 1);
+  for (int k = threadIdx.x; k < rf; k += blockDim.x) w[(int64_t)slot * wstride + k] = (T)(h * h * prob[slot].s_f[k]);
+  if (threadIdx.x == 0) {
+    SolveState st;
+    memset(&st, 0, sizeof(st));
+    st.active = act ? 1 : 0;
+    st.valid = act ? 1 : 0;
+    st.rf = rf;
+    st.rf0 = rf;
+    *stp = st;
+    if (act && acct) acct_setup(acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rf, p.g.NB, (int)sizeof(T));
+  }
+}
+
+__global__ void k_eigenvalues(int n, double* lam64, float* lam32) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  // lambda_{k+1} = 4 sin^2(pi (k+1) / (2(n+1)))
+  const double s = sinpi((double)(k + 1) / (2.0 * (double)(n + 1)));
+  const double l = 4.0 * s * s;
+  if (lam64) lam64[k] = l;
+  if (lam32) lam32[k] = (float)l;
+}
+
+__global__ void k_count_active(const SolveState* st, int nslots, int32_t* out) {
+  __shared__ int c;
+  if (threadIdx.x == 0) c = 0;
+  __syncthreads();
+  int local = 0;
+  for (int s = threadIdx.x; s < nslots; s += blockDim.x) local += st[s].active ? 1 : 0;
+  atomicAdd(&c, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = c;
+}
+
+// ------------------------------------------------------------------ launches
+
+template <typename T>
+cudaError_t launch_chol(const CoreParams& p, const CoreBufs<T>& b, int sel, int pass, cudaStream_t s) {
+  k_chol<T><<<p.g.nslots * 2, CT, 0, s>>>(p, b, sel, pass);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_core(const CoreParams& p, const CoreBufs<T>& b, int parity, cudaStream_t s) {
+  k_core<T><<<p.g.nslots, CT, 0, s>>>(p, b, parity);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_select(const CoreParams& p, const CoreBufs<T>& b, int sel_c, cudaStream_t s) {
+  const int total = p.cand_blocks * p.cand_per_block;
+  int len = 1;
+  while (len < total) len <<= 1;
+  const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
+  auto kern = k_select<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<p.g.nslots * 2, 512, smem, s>>>(p, b, sel_c, len);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stop(const CoreParams& p, const CoreBufs<T>& b, int parity, cudaStream_t s) {
+  k_stop<T><<<p.g.nslots, CT, 0, s>>>(p, b, parity);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize_impl(const CoreParams& p, const CoreBufs<T>& b, const DstBatch<T, double>& back,
+                                 T* const* ubufs, int64_t side_stride, int64_t slot_stride, cudaStream_t s) {
+  k_finalize<T><<<p.g.nslots, 32, 0, s>>>(p, b, back, ubufs, side_stride, slot_stride);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_setup(const CoreParams& p, const ProblemDev* prob, T* w, int wstride, int nactive, double* acct,
+                         cudaStream_t s) {
+  k_setup<T><<<p.g.nslots, 64, 0, s>>>(p, prob, w, wstride, nactive, acct);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s) {
+  k_eigenvalues<<<(n + 255) / 256, 256, 0, s>>>(n, lam64, lam32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, cudaStream_t s) {
+  k_count_active<<<1, 256, 0, s>>>(st, nslots, out);
+  return cudaGetLastError();
+}
+
+#define LRP_INST(T)                                                                                          \
+  template cudaError_t launch_chol<T>(const CoreParams&, const CoreBufs<T>&, int, int, cudaStream_t);       \
+  template cudaError_t launch_core<T>(const CoreParams&, const CoreBufs<T>&, int, cudaStream_t);            \
+  template cudaError_t launch_select<T>(const CoreParams&, const CoreBufs<T>&, int, cudaStream_t);          \
+  template cudaError_t launch_stop<T>(const CoreParams&, const CoreBufs<T>&, int, cudaStream_t);            \
+  template cudaError_t launch_finalize_impl<T>(const CoreParams&, const CoreBufs<T>&,                      \
+                                               const DstBatch<T, double>&, T* const*, int64_t, int64_t,      \
+                                               cudaStream_t);                                                 \
+  template cudaError_t launch_setup<T>(const CoreParams&, const ProblemDev*, T*, int, int, double*, cudaStream_t);
+LRP_INST(double)
+LRP_INST(float)
+#undef LRP_INST
+
+}  // namespace lrp

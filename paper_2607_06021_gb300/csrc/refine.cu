@@ -1,0 +1,301 @@
+// Mixed-precision refinement (an extension beyond the paper).
+//
+// The FP32 Cross-DEIM solve gives a trial solution What0 = Uh0 S0 Vh0^T in
+// transformed variables.  Because T = Z Lambda Z (Sec. 3), the residual of
+// T W + W T = h^2 F in the same variables is
+//     Rhat = h^2 Fhat - (Lambda What0 + What0 Lambda)
+//          = [Uh_f, Lambda Uh0, Uh0] diag(h^2 s_f, -S0, -S0) [Vh_f, Vh0, Lambda Vh0]^T,
+// a rank r_f + 2 r0 product that is recompressed in FP64 (shifted CholeskyQR of
+// both factor blocks and an SVD of the small core R_X diag(d) R_Y^T).  The
+// correction dWhat(i,j) = Rhat(i,j)/(lambda_i + lambda_j) is then one more
+// Cross-DEIM solve, and What1 = What0 + dWhat is recompressed in FP64 the same
+// way before the back transform.
+//
+// Kernels here assemble the stacked factor blocks, form and factor the small
+// cores and convert between the FP32 iteration workspace and the FP64 one.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "core.cuh"
+#include "dense.cuh"
+#include "refine.cuh"
+
+namespace lrp {
+
+namespace {
+constexpr int RT = 256;
+}
+
+
+// After the first FP32 solve: r0 = rank of the trial solution (capped so that
+// r_f + 2 r0 <= M), d = [h^2 s_f, -S0, -S0], mx = r_f + 2 r0.
+__global__ void k_prepare_refine(RefineArgs a) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  const int M = a.M;
+  const int rf = st->rf0;
+  int r0 = st->r;
+  const int cap = (M - rf) / 2;
+  if (r0 > cap) r0 = cap;
+  if (r0 < 1) r0 = 1;
+  const int par = (st->k - 1) & 1;
+  const double* sig = a.sig32 + (int64_t)slot * 2 * M + (int64_t)par * M;
+  double* d = a.dvec + (int64_t)slot * M;
+  double* s0 = a.s0 + (int64_t)slot * M;
+  const double h = 1.0 / (double)(a.n + 1);
+  const ProblemDev& pr = a.prob[slot];
+  for (int k = threadIdx.x; k < rf; k += blockDim.x) d[k] = h * h * pr.s_f[k];
+  for (int t = threadIdx.x; t < r0; t += blockDim.x) {
+    s0[t] = sig[t];
+    d[rf + t] = -sig[t];
+    d[rf + r0 + t] = -sig[t];
+  }
+  if (threadIdx.x == 0) {
+    st->r0 = r0;
+    st->mx[0] = st->mx[1] = rf + 2 * r0;
+    st->active = 1;
+    st->upar = par;
+  }
+}
+
+// Stacked blocks of the residual factors (FP64, ld = a.ld); side 0:
+// [Uh_f | Lambda Uh0 | Uh0], side 1: [Vh_f | Vh0 | Lambda Vh0].  Also stashes
+// Uh0, Vh0 in FP64 for the final sum.
+__global__ void k_assemble_residual(RefineArgs a) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState& st = a.st[slot];
+  if (!st.valid) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int rf = st.rf0, r0 = st.r0;
+  const double lam = a.lam[i];
+  const double* Fh = a.Fh64.at(slot, side);
+  const float* U0 = a.U32[st.upar].at(slot, side);
+  double* X = a.X.at(slot, side);
+  double* stash = a.stash.at(slot, side);
+  for (int j = 0; j < rf; ++j) X[(int64_t)j * a.ld + i] = Fh[(int64_t)j * a.ld + i];
+  for (int t = 0; t < r0; ++t) {
+    const double u = (double)U0[(int64_t)t * a.ld + i];
+    stash[(int64_t)t * a.ld + i] = u;
+    const double first = (side == 0) ? lam * u : u;
+    const double second = (side == 0) ? u : lam * u;
+    X[(int64_t)(rf + t) * a.ld + i] = first;
+    X[(int64_t)(rf + r0 + t) * a.ld + i] = second;
+  }
+}
+
+// Small core K = R_0 diag(d) R_1^T (m = mx), its SVD by one-sided Jacobi, and the
+// factors Bf_s = P3_s * (left / right singular vectors) so that the recompressed
+// product is (Q2_0 Bf_0) diag(sigma) (Q2_1 Bf_1)^T.  mode 0 keeps the tail-rule
+// rank at rel_tol (capped at rcap); mode 1 keeps every numerically nonzero value.
+__global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, double rel_tol, int rcap) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  const int M = a.M;
+  const int64_t MM = (int64_t)M * M;
+  const int m = st->mx[0];
+  const double* R0 = a.Racc.at(slot, 0);
+  const double* R1 = a.Racc.at(slot, 1);
+  const double* P0 = a.P.at(slot, 0);
+  const double* P1 = a.P.at(slot, 1);
+  const double* d = a.dvec + (int64_t)slot * M;
+  double* base = a.scratch + (int64_t)slot * a.scratch_stride;
+  double* K = base;           // m x m
+  double* V = base + MM;      // m x m
+  double* B0 = a.Bf.at(slot, 0);
+  double* B1 = a.Bf.at(slot, 1);
+  double* sig_out = a.sig_out + (int64_t)slot * a.sig_out_stride;
+  __shared__ double sig[kMaxM];
+  __shared__ int perm[kMaxM];
+  __shared__ int flag;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // K(i, j) = sum_{l >= max(i, j)} R0(i, l) d_l R1(j, l)
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    double s = 0.0;
+    for (int l = max(i, j); l < m; ++l) s += R0[(int64_t)l * M + i] * d[l] * R1[(int64_t)l * M + j];
+    K[(int64_t)j * M + i] = s;
+  }
+  __syncthreads();
+  blk_jacobi(K, M, m, m, V, M, sig, &flag);
+  blk_sort_desc(sig, m, perm);
+  int r = 0;
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int t = 0; t < m; ++t) tot += sig[t] * sig[t];
+    const double s1 = sig[perm[0]];
+    if (mode == 0) {
+      double tail = 0.0;
+      r = m;
+      for (int t = m; t >= 1; --t) {
+        if (t < m) tail += sig[perm[t]] * sig[perm[t]];
+        if (tail < rel_tol * rel_tol * tot) r = t;
+        else break;
+      }
+    } else {
+      r = 0;
+      for (int t = 0; t < m; ++t) r += (sig[perm[t]] > (double)m * 2.220446049250313e-16 * s1) ? 1 : 0;
+    }
+    if (r > rcap) r = rcap;
+    if (r < 1) r = 1;
+    flag = r;
+  }
+  __syncthreads();
+  r = flag;
+  // Left vectors: K(:, perm[t]) / sigma (K now holds U' Sigma); right: V(:, perm[t]).
+  for (int e = tid; e < m * r; e += nt) {
+    const int i = e % m, t = e / m;
+    const int j = perm[t];
+    double s0 = 0.0, s1 = 0.0;
+    const double sv = sig[j];
+    for (int c = i; c < m; ++c) {
+      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? K[(int64_t)j * M + c] / sv : 0.0);
+      s1 += P1[(int64_t)c * M + i] * V[(int64_t)j * M + c];
+    }
+    B0[(int64_t)t * M + i] = s0;
+    B1[(int64_t)t * M + i] = s1;
+  }
+  for (int t = tid; t < r; t += nt) sig_out[t] = sig[perm[t]];
+  if (tid == 0) st->r = r;
+}
+
+// Prepare the FP32 correction solve: its right-hand side in transformed
+// variables is the recompressed residual (factors already transformed) with
+// weights sigma_R (no h^2: the residual already carries it).
+__global__ void k_setup_correction(RefineArgs a) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  const int rR = st->r;
+  const double* sR = a.sig_out + (int64_t)slot * a.sig_out_stride;
+  for (int k = threadIdx.x; k < rR; k += blockDim.x) a.w32[(int64_t)slot * a.wstride + k] = (float)sR[k];
+  if (threadIdx.x == 0) {
+    const int total = st->total_iters;
+    const int r0 = st->r0, rf0 = st->rf0;
+    SolveState z;
+    memset(&z, 0, sizeof(z));
+    z.active = 1;
+    z.valid = 1;
+    z.rf = rR;
+    z.rf0 = rf0;
+    z.r0 = r0;
+    z.total_iters = total;
+    z.flags = st->flags & ~kFlagConverged;
+    z.first_converged = (st->flags & kFlagConverged) ? 1 : 0;
+    *st = z;
+  }
+}
+
+// dst[s](:, j) = (TD) src[s](:, j) for j < dim(sel).
+template <typename TS, typename TD>
+__global__ void k_convert(int n, int64_t ld, const SolveState* st_all, Strided<const TS> src, Strided<TD> dst,
+                          int sel) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState& st = st_all[slot];
+  if (!st.valid) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = dim_of(st, side, sel);
+  const TS* s = src.at(slot, side);
+  TD* d = dst.at(slot, side);
+  for (int j = 0; j < c; ++j) d[(int64_t)j * ld + i] = (TD)s[(int64_t)j * ld + i];
+}
+
+// After the correction solve: d = [S0, dS], mx = r0 + rd.
+__global__ void k_prepare_sum(RefineArgs a) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  const int M = a.M;
+  const int r0 = st->r0;
+  int rd = st->r;
+  if (rd > M - r0) rd = M - r0;
+  const int par = (st->k - 1) & 1;
+  const double* sig = a.sig32 + (int64_t)slot * 2 * M + (int64_t)par * M;
+  double* d = a.dvec + (int64_t)slot * M;
+  const double* s0 = a.s0 + (int64_t)slot * M;
+  for (int t = threadIdx.x; t < r0; t += blockDim.x) d[t] = s0[t];
+  for (int t = threadIdx.x; t < rd; t += blockDim.x) d[r0 + t] = sig[t];
+  if (threadIdx.x == 0) {
+    st->mx[0] = st->mx[1] = r0 + rd;
+    st->upar = par;
+    st->rd = rd;
+    st->active = 1;
+  }
+}
+
+// Stacked [Uh0 | dUh] (side 0) and [Vh0 | dVh] (side 1) in FP64.
+__global__ void k_assemble_sum(RefineArgs a) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState& st = a.st[slot];
+  if (!st.valid) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int r0 = st.r0, rd = st.rd;
+  const double* stash = a.stash.at(slot, side);
+  const float* dU = a.U32[st.upar].at(slot, side);
+  double* X = a.X.at(slot, side);
+  for (int t = 0; t < r0; ++t) X[(int64_t)t * a.ld + i] = stash[(int64_t)t * a.ld + i];
+  for (int t = 0; t < rd; ++t) X[(int64_t)(r0 + t) * a.ld + i] = (double)dU[(int64_t)t * a.ld + i];
+}
+
+// The final recompressed iterate becomes "iteration 0" of the FP64 workspace so
+// that the common finalize kernel truncates and transforms it back.
+__global__ void k_final_state(RefineArgs a) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid || threadIdx.x != 0) return;
+  const bool conv = st->first_converged && (st->flags & kFlagConverged);
+  st->k = 1;
+  st->iters = st->total_iters;
+  st->flags = conv ? (st->flags | kFlagConverged) : (st->flags & ~kFlagConverged);
+  st->active = 0;
+}
+
+// ------------------------------------------------------------------ launches
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+cudaError_t launch_prepare_refine(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_prepare_refine<<<nslots, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_assemble_residual(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_assemble_residual<<<dim3(cdiv(a.n, 256), 2 * nslots), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_recompress(const RefineArgs& a, int nslots, int mode, double rel_tol, int rcap, cudaStream_t s) {
+  k_recompress<<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
+  return cudaGetLastError();
+}
+cudaError_t launch_setup_correction(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_setup_correction<<<nslots, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename TS, typename TD>
+cudaError_t launch_convert(int n, int64_t ld, int nslots, const SolveState* st, Strided<const TS> src,
+                           Strided<TD> dst, int sel, cudaStream_t s) {
+  k_convert<TS, TD><<<dim3(cdiv(n, 256), 2 * nslots), 256, 0, s>>>(n, ld, st, src, dst, sel);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(int, int64_t, int, const SolveState*, Strided<const double>,
+                                                   Strided<float>, int, cudaStream_t);
+template cudaError_t launch_convert<float, double>(int, int64_t, int, const SolveState*, Strided<const float>,
+                                                   Strided<double>, int, cudaStream_t);
+cudaError_t launch_prepare_sum(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_prepare_sum<<<nslots, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_assemble_sum(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_assemble_sum<<<dim3(cdiv(a.n, 256), 2 * nslots), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_final_state(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_final_state<<<nslots, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace lrp

@@ -1,0 +1,809 @@
+// Host driver and C ABI (include/lrp.h).
+//
+// A plan owns all device workspace for `batch` problems of one grid size n and
+// runs the low-rank Poisson solve of the paper's Sec. 3.2: DST-I of the
+// right-hand-side factors, Cross-DEIM (Algorithm "Cross-DEIM") on the
+// transformed solution What = h^2 Fhat ./ (lambda_i + lambda_j) (Eq. g_for_p),
+// final truncation and the back transform.  Every step runs in this library's
+// kernels; the host only sequences launches and reads one device counter of
+// still-iterating problems between iterations.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "core.cuh"
+#include "dst.cuh"
+#include "refine.cuh"
+#include "solver.cuh"
+#include "tall.cuh"
+
+namespace lrp {
+
+thread_local std::string g_last_error;
+
+lrp_status set_error(lrp_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define LRP_CUDA(call)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return set_error(LRP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + " @" +        \
+                                      std::to_string(__LINE__));                                    \
+  } while (0)
+
+// Brackets one library call that launches `nk` kernels of class `cls`.
+#define LRP_LAUNCH(P, CLS, NK, S, call)                                                             \
+  do {                                                                                              \
+    int ev0_ = (P)->stats.timing ? (P)->stats.take(S) : -1;                                         \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return set_error(LRP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + " @" +        \
+                                      std::to_string(__LINE__));                                    \
+    (P)->stats.launches[CLS] += (NK);                                                               \
+    if (ev0_ >= 0) (P)->stats.pending.push_back({(CLS), ev0_, (P)->stats.take(S)});                 \
+  } while (0)
+
+template <typename T>
+lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc) {
+  const int64_t nm = d.ld * d.M;
+  const int64_t MM = (int64_t)d.M * d.M;
+  rf_cap = rfc;
+  Fh = arena.get<T>((size_t)d.B * 2 * d.ld * rf_cap);
+  w = arena.get<T>((size_t)d.B * rf_cap);
+  A = arena.get<T>((size_t)d.B * 2 * nm);
+  Q1 = arena.get<T>((size_t)d.B * 2 * nm);
+  Q2 = arena.get<T>((size_t)d.B * 2 * nm);
+  U[0] = arena.get<T>((size_t)d.B * 2 * nm);
+  U[1] = arena.get<T>((size_t)d.B * 2 * nm);
+  part = arena.get<double>((size_t)d.B * 2 * d.NB * MM);
+  G = arena.get<double>((size_t)d.B * 2 * MM);
+  Racc = arena.get<double>((size_t)d.B * 2 * MM);
+  P = arena.get<double>((size_t)d.B * 2 * MM);
+  Bf = arena.get<double>((size_t)d.B * 2 * MM);
+  X = arena.get<double>((size_t)d.B * 2 * MM);
+  GE = arena.get<double>((size_t)d.B * 2 * MM);
+  sig = arena.get<double>((size_t)d.B * 2 * d.M);
+  scratch = arena.get<double>((size_t)d.B * kCoreScratch * MM);
+  idx = arena.get<int32_t>((size_t)d.B * 2 * d.M);
+  cand_score = arena.get<double>((size_t)d.B * 2 * d.cand_blocks * d.cand_per_block);
+  cand_idx = arena.get<int32_t>((size_t)d.B * 2 * d.cand_blocks * d.cand_per_block);
+  back_in = arena.get<T*>((size_t)2 * d.B);
+  back_out = arena.get<double*>((size_t)2 * d.B);
+  back_ldi = arena.get<int64_t>((size_t)2 * d.B);
+  back_ldo = arena.get<int64_t>((size_t)2 * d.B);
+  ubufs = arena.get<T*>(2);
+  fwd_in = arena.get<const double*>((size_t)2 * d.B);
+  fwd_out = arena.get<T*>((size_t)2 * d.B);
+  fwd_ldi = arena.get<int64_t>((size_t)2 * d.B);
+  fwd_ldo = arena.get<int64_t>((size_t)2 * d.B);
+  if (!arena.ok()) return set_error(LRP_ENOMEM, "workspace allocation failed");
+  T* ub[2] = {U[0], U[1]};
+  LRP_CUDA(cudaMemcpy(ubufs, ub, sizeof(ub), cudaMemcpyHostToDevice));
+  return LRP_OK;
+}
+
+template struct Workspace<double>;
+template struct Workspace<float>;
+
+}  // namespace lrp
+
+using namespace lrp;
+
+// ------------------------------------------------------------------- stats
+
+int KernelStats::take(cudaStream_t s) {
+  if (next_event >= (int)pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    pool.push_back(e);
+  }
+  const int i = next_event++;
+  cudaEventRecord(pool[i], s);
+  return i;
+}
+
+void KernelStats::drain() {
+  for (const Rec& r : pending) {
+    if (r.e0 < 0 || r.e1 < 0) continue;
+    float ms_ = 0.f;
+    if (cudaEventElapsedTime(&ms_, pool[r.e0], pool[r.e1]) == cudaSuccess) ms[r.cls] += ms_;
+  }
+  pending.clear();
+  next_event = 0;
+}
+
+void KernelStats::release() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  pool.clear();
+  pending.clear();
+  next_event = 0;
+}
+
+extern "C" lrp_status lrp_plan_set_timing(lrp_plan_t p, int32_t enable) {
+  if (!p) return set_error(LRP_EINVAL, "NULL plan");
+  std::lock_guard<std::mutex> lock(p->mu);
+  p->stats.timing = enable != 0;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_kernel_stats(lrp_plan_t p, int32_t kclass, int64_t* launches, double* total_ms) {
+  if (!p || !launches || !total_ms) return set_error(LRP_EINVAL, "NULL argument");
+  if (kclass < -1 || kclass >= LRP_K_COUNT) return set_error(LRP_EINVAL, "kernel class out of range");
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (cudaDeviceSynchronize() != cudaSuccess) return set_error(LRP_ECUDA, "synchronize failed");
+  p->stats.drain();
+  int64_t l = 0;
+  double t = 0.0;
+  for (int c = 0; c < LRP_K_COUNT; ++c)
+    if (kclass < 0 || c == kclass) {
+      l += p->stats.launches[c];
+      t += p->stats.ms[c];
+    }
+  *launches = l;
+  *total_ms = t;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_kernel_work(lrp_plan_t p, int32_t kclass, double* flops, double* bytes) {
+  if (!p || !flops || !bytes) return set_error(LRP_EINVAL, "NULL argument");
+  if (kclass < -1 || kclass >= LRP_K_COUNT) return set_error(LRP_EINVAL, "kernel class out of range");
+  std::lock_guard<std::mutex> lock(p->mu);
+  std::vector<double> h((size_t)p->dims.B * 2 * LRP_K_COUNT);
+  LRP_CUDA(cudaDeviceSynchronize());
+  LRP_CUDA(cudaMemcpy(h.data(), p->acct, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+  double f = 0.0, b = 0.0;
+  for (int s = 0; s < p->dims.B; ++s)
+    for (int c = 0; c < LRP_K_COUNT; ++c)
+      if (kclass < 0 || c == kclass) {
+        f += h[((size_t)s * LRP_K_COUNT + c) * 2];
+        b += h[((size_t)s * LRP_K_COUNT + c) * 2 + 1];
+      }
+  *flops = f;
+  *bytes = b;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_reset_stats(lrp_plan_t p) {
+  if (!p) return set_error(LRP_EINVAL, "NULL plan");
+  std::lock_guard<std::mutex> lock(p->mu);
+  cudaDeviceSynchronize();
+  cudaMemset(p->acct, 0, sizeof(double) * (size_t)p->dims.B * 2 * LRP_K_COUNT);
+  p->stats.drain();
+  for (int c = 0; c < LRP_K_COUNT; ++c) {
+    p->stats.launches[c] = 0;
+    p->stats.ms[c] = 0.0;
+  }
+  return LRP_OK;
+}
+
+// ------------------------------------------------------------------- arena
+
+void* DeviceArena::raw(size_t bytes) {
+  if (failed) return nullptr;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    failed = true;
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaMemset(p, 0, bytes);
+  blocks.push_back(p);
+  total += bytes;
+  return p;
+}
+
+void DeviceArena::release() {
+  for (void* p : blocks) cudaFree(p);
+  blocks.clear();
+  total = 0;
+}
+
+// ------------------------------------------------------------------- plan
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
+  if (!o) return set_error(LRP_EINVAL, "opts is NULL");
+  o->precision = LRP_FP64;
+  o->selector = LRP_SEL_LEVERAGE;
+  o->max_iter = 30;
+  o->refine_steps = 1;
+  o->max_rhs_rank = 64;
+  o->batch = 1;
+  o->m_cap = 0;
+  o->check_every = 1;
+  o->seed = 0;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts) {
+  if (!out) return set_error(LRP_EINVAL, "out is NULL");
+  *out = nullptr;
+  lrp_opts o;
+  lrp_default_opts(&o);
+  if (opts) o = *opts;
+  if (n < 1 || !is_pow2(n + 1)) return set_error(LRP_EINVAL, "n+1 must be a power of two >= 2");
+  if (!(tol > 0.0) || !(tol < 1.0)) return set_error(LRP_EINVAL, "tol must be in (0, 1)");
+  if (max_rank < 1) return set_error(LRP_EINVAL, "max_rank must be >= 1");
+  if (o.max_iter < 1 || o.max_iter > 1000) return set_error(LRP_EINVAL, "max_iter out of range");
+  if (o.max_rhs_rank < 1 || o.max_rhs_rank > kMaxRF) return set_error(LRP_EINVAL, "max_rhs_rank out of range");
+  if (o.batch < 1 || o.batch > 65535) return set_error(LRP_EINVAL, "batch out of range");
+  if (o.precision != LRP_FP64 && o.precision != LRP_MIXED) return set_error(LRP_EINVAL, "unknown precision");
+  if (o.selector != LRP_SEL_LEVERAGE) return set_error(LRP_EINVAL, "only the leverage-score selector is built");
+  if (o.check_every < 1) o.check_every = 1;
+  const bool fp64 = (o.precision == LRP_FP64);
+  if (!dst_smem_supported(n, true)) return set_error(LRP_EINVAL, "n+1 > 8192 needs the multi-pass DST (not built)");
+
+  lrp_plan_s* p = new (std::nothrow) lrp_plan_s();
+  if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
+  p->n = n;
+  p->tol = tol;
+  p->mixed_inner_tol = 3e-5;
+  p->mixed_redundancy = 1e-6;
+  p->mixed_residual_tol = 1e-7;
+  p->r_max = max_rank;
+  p->opts = o;
+  PlanDims& d = p->dims;
+  d.n = (int)n;
+  d.ld = (n + 31) / 32 * 32;
+  d.B = o.batch;
+  d.RF = o.max_rhs_rank;
+  int M = o.m_cap > 0 ? o.m_cap : 2 * max_rank + o.max_rhs_rank;
+  if (M > kMaxM) M = kMaxM;
+  if (M < o.max_rhs_rank) M = o.max_rhs_rank;  // the initial bases have r_f columns
+  if (M < 2) M = 2;
+  d.M = M;
+  // Gram partial blocks: at least 256 rows each, at most 64 blocks.
+  d.NB = (int)((n + 255) / 256);
+  if (d.NB > 64) d.NB = 64;
+  if (d.NB < 1) d.NB = 1;
+  d.rows_per_block = (int)(((n + d.NB - 1) / d.NB + 31) / 32 * 32);
+  d.NB = (int)((n + d.rows_per_block - 1) / d.rows_per_block);
+  // Leverage candidate blocks of at most 1024 rows.
+  d.cand_blocks = (int)((n + 1023) / 1024);
+  d.cand_per_block = M;
+  if (d.cand_blocks * d.cand_per_block > 16384) {
+    delete p;
+    return set_error(LRP_EINVAL, "candidate merge too large for this n and m_cap");
+  }
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return set_error(LRP_ECUDA, "no CUDA device");
+  }
+  lrp_status s = LRP_OK;
+  cudaStream_t st0 = nullptr;
+  p->st = p->arena.get<SolveState>((size_t)d.B);
+  p->lam64 = p->arena.get<double>((size_t)d.n);
+  p->lam32 = p->arena.get<float>((size_t)d.n);
+  p->prob_dev = p->arena.get<ProblemDev>((size_t)d.B);
+  p->active_dev = p->arena.get<int32_t>(4);
+  p->acct = p->arena.get<double>((size_t)d.B * 2 * LRP_K_COUNT);
+  p->dvec = p->arena.get<double>((size_t)d.B * d.M);
+  p->s0 = p->arena.get<double>((size_t)d.B * d.M);
+  if (!p->arena.ok()) s = set_error(LRP_ENOMEM, "plan allocation failed");
+  if (s == LRP_OK) s = p->w64.allocate(d, p->arena, d.RF);
+  // the FP32 workspace also holds the recompressed residual (up to m_cap columns)
+  if (s == LRP_OK && !fp64) s = p->w32.allocate(d, p->arena, d.RF > d.M ? d.RF : d.M);
+  if (s == LRP_OK && !fp64 && d.M < d.RF + 2) s = set_error(LRP_EINVAL, "mixed precision needs m_cap >= max_rhs_rank + 2");
+  if (s == LRP_OK && !fp64 && o.refine_steps != 1)
+    s = set_error(LRP_EINVAL, "refine_steps must be 1 (one refinement step is built)");
+  if (s == LRP_OK) {
+    p->tw64 = dst_make_twiddles(n + 1, true, st0);
+    p->tw32 = dst_make_twiddles(n + 1, false, st0);
+    if (!p->tw64 || !p->tw32) s = set_error(LRP_ENOMEM, "twiddle allocation failed");
+  }
+  if (s == LRP_OK) {
+    cudaError_t e = launch_eigenvalues(d.n, p->lam64, p->lam32, st0);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->prob_host, sizeof(ProblemDev) * d.B);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_ptrs, (sizeof(void*) * 2 + sizeof(int64_t) * 2) * 2 * d.B);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->active_host, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) s = set_error(LRP_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
+  }
+  if (s != LRP_OK) {
+    lrp_plan_destroy(p);
+    return s;
+  }
+  *out = p;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
+  if (!p) return LRP_OK;
+  cudaDeviceSynchronize();
+  p->arena.release();
+  if (p->tw64) cudaFree(p->tw64);
+  if (p->tw32) cudaFree(p->tw32);
+  if (p->prob_host) cudaFreeHost(p->prob_host);
+  if (p->host_ptrs) cudaFreeHost(p->host_ptrs);
+  if (p->active_host) cudaFreeHost(p->active_host);
+  p->stats.release();
+  delete p;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_workspace_bytes(lrp_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return set_error(LRP_EINVAL, "NULL argument");
+  *bytes = p->arena.total;
+  return LRP_OK;
+}
+
+// ------------------------------------------------------------------- solve
+
+namespace lrp {
+
+template <typename T>
+static CoreBufs<T> make_core_bufs(lrp_plan_s* p, Workspace<T>& w) {
+  const PlanDims& d = p->dims;
+  const int64_t MM = (int64_t)d.M * d.M;
+  const int64_t nm = d.ld * d.M;
+  CoreBufs<T> b;
+  b.G = {w.G, MM, 2 * MM};
+  b.Racc = {w.Racc, MM, 2 * MM};
+  b.P = {w.P, MM, 2 * MM};
+  b.Bf = {w.Bf, MM, 2 * MM};
+  b.X = {w.X, MM, 2 * MM};
+  b.GE = {w.GE, MM, 2 * MM};
+  b.Q2 = {w.Q2, nm, 2 * nm};
+  b.idx = {w.idx, d.M, 2 * (int64_t)d.M};
+  b.sig = w.sig;
+  b.scratch = w.scratch;
+  b.scratch_stride = kCoreScratch * MM;
+  b.cand_score = w.cand_score;
+  b.cand_idx = w.cand_idx;
+  b.prob = p->prob_dev;
+  b.acct = p->acct;
+  return b;
+}
+
+template <typename T>
+static Strided<const T> cs(const T* base, int64_t side, int64_t slot) {
+  return Strided<const T>{base, side, slot};
+}
+
+// One CholeskyQR pass chain: Gram of X -> chol(pass 0, shifted) -> Q1 = X P,
+// Gram -> chol(1) -> Q2 = Q1 P, Gram -> chol(2).  Leaves P3 in w.P, Q2 in w.Q2.
+template <typename T>
+static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T> x, int sx, Strided<const T> y,
+                              int sy, double* part, Strided<double> G, bool sym, cudaStream_t s) {
+  LRP_LAUNCH(p, LRP_K_GRAM, 1, s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s));
+  LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, sx, sy, part, G, sym, s));
+  return LRP_OK;
+}
+
+template <typename T>
+static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, const CoreParams& cp,
+                          const CoreBufs<T>& cb, const T* X, int64_t side_stride, int64_t slot_stride, int sel,
+                          cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  const int64_t MM = (int64_t)d.M * d.M;
+  const int64_t nm = d.ld * d.M;
+  Strided<double> G{w.G, MM, 2 * MM};
+  Strided<const double> P{w.P, MM, 2 * MM};
+  const Strided<const T> none{nullptr, 0, 0};
+  lrp_status st;
+  if ((st = gram_reduce<T>(p, g, cs(X, side_stride, slot_stride), sel, cs(X, side_stride, slot_stride), sel, w.part,
+                           G, true, s)))
+    return st;
+  LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 0, s));
+  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+             launch_gemm_nn<T>(g, p->st, cs(X, side_stride, slot_stride), sel, P, sel, Strided<T>{w.Q1, nm, 2 * nm},
+                               none, 0, s));
+  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), sel, cs<T>(w.Q1, nm, 2 * nm), sel, w.part, G, true, s)))
+    return st;
+  LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 1, s));
+  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+             launch_gemm_nn<T>(g, p->st, cs<T>(w.Q1, nm, 2 * nm), sel, P, sel, Strided<T>{w.Q2, nm, 2 * nm}, none, 0,
+                               s));
+  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q2, nm, 2 * nm), sel, cs<T>(w.Q2, nm, 2 * nm), sel, w.part, G, true, s)))
+    return st;
+  LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 2, s));
+  return LRP_OK;
+}
+
+template <typename T>
+static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double eps_data, double redundancy) {
+  const PlanDims& d = p->dims;
+  CoreParams cp;
+  cp.g = TallGeom{d.n, d.ld, d.M, count, d.NB, d.rows_per_block};
+  cp.st = p->st;
+  cp.max_iter = p->opts.max_iter;
+  cp.r_max = p->r_max;
+  cp.tol = tol;
+  cp.eps_data = eps_data;
+  cp.shift_rel = 1e-15;
+  cp.drop_rel = 64.0 * 2.220446049250313e-16;
+  cp.redundancy = redundancy;
+  cp.seed = p->opts.seed;
+  cp.selector = p->opts.selector;
+  cp.cand_blocks = d.cand_blocks;
+  cp.cand_per_block = d.cand_per_block;
+  return cp;
+}
+
+// Forward DST of the caller's factors into w.Fh (type T); with do_setup the
+// per-slot state and the h^2-scaled weights are initialised too.
+template <typename T>
+static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, bool do_setup,
+                                cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  const int64_t fm = d.ld * w.rf_cap;
+  const double** hin = (const double**)p->host_ptrs;
+  T** hout = (T**)(hin + 2 * d.B);
+  int64_t* hldi = (int64_t*)(hout + 2 * d.B);
+  int64_t* hldo = hldi + 2 * d.B;
+  // The pinned staging is shared by both precisions: wait for earlier copies from it.
+  LRP_CUDA(cudaStreamSynchronize(s));
+  for (int mat = 0; mat < 2; ++mat)
+    for (int sl = 0; sl < count; ++sl) {
+      const ProblemDev& pr = p->prob_host[sl];
+      hin[mat * count + sl] = mat == 0 ? pr.U_f : pr.V_f;
+      hldi[mat * count + sl] = mat == 0 ? pr.ldu_f : pr.ldv_f;
+      hout[mat * count + sl] = w.Fh + (int64_t)sl * 2 * fm + (int64_t)mat * fm;
+      hldo[mat * count + sl] = d.ld;
+    }
+  LRP_CUDA(cudaMemcpyAsync(w.fwd_in, hin, sizeof(void*) * 2 * count, cudaMemcpyHostToDevice, s));
+  LRP_CUDA(cudaMemcpyAsync(w.fwd_out, hout, sizeof(void*) * 2 * count, cudaMemcpyHostToDevice, s));
+  LRP_CUDA(cudaMemcpyAsync(w.fwd_ldi, hldi, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice, s));
+  LRP_CUDA(cudaMemcpyAsync(w.fwd_ldo, hldo, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice, s));
+  if (do_setup)
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_setup<T>(cp, p->prob_dev, w.w, w.rf_cap, count, p->acct, s));
+  DstBatch<double, T> job;
+  job.in = w.fwd_in;
+  job.out = w.fwd_out;
+  job.ld_in = w.fwd_ldi;
+  job.ld_out = w.fwd_ldo;
+  job.nslots = count;
+  job.fixed_cols = 0;
+  job.ncols_dev = &p->prob_dev[0].rf;
+  job.ncols_stride = (int)(sizeof(ProblemDev) / sizeof(int32_t));
+  job.ncols_mat_stride = 0;
+  job.active_dev = nullptr;
+  job.active_stride = 0;
+  job.require_active = 0;
+  const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
+  LRP_LAUNCH(p, LRP_K_DST, 1, s, (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s)));
+  return LRP_OK;
+}
+
+// Cross-DEIM (Algorithm Cross-DEIM) on the transformed right-hand side held in
+// w.Fh / w.w: initial bases orth(Fh), then iterations until every slot stops.
+template <typename T>
+static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  const int64_t MM = (int64_t)d.M * d.M;
+  const int64_t nm = d.ld * d.M;
+  const int64_t fm = d.ld * w.rf_cap;
+  const TallGeom& g = cp.g;
+  CoreBufs<T> cb = make_core_bufs<T>(p, w);
+  const Strided<const T> none{nullptr, 0, 0};
+  // U_{-1} = orth(Uhat_f), V_{-1} = orth(Vhat_f) and their leverage candidates.
+  {
+    lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.Fh, fm, 2 * fm, kDimRF, s);
+    if (st) return st;
+  }
+  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+             launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
+                               kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
+  LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
+             launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimRF, w.cand_score, w.cand_idx,
+                                d.cand_blocks, d.cand_per_block, s));
+  Strided<double> Gx{w.X, MM, 2 * MM};
+  Strided<double> Ge{w.GE, MM, 2 * MM};
+  CrossArgs<T> ca;
+  ca.F = {w.Fh, fm, 2 * fm};
+  ca.w = w.w;
+  ca.wstride = w.rf_cap;
+  ca.lam = (sizeof(T) == 8) ? (const T*)p->lam64 : (const T*)p->lam32;
+  ca.idx = {w.idx, d.M, 2 * (int64_t)d.M};
+  ca.A = {w.A, nm, 2 * nm};
+  for (int k = 0; k < p->opts.max_iter; ++k) {
+    const int par = k & 1;
+    LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimRF : kDimR, s));
+    LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(g, p->st, ca, s));
+    {
+      lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.A, nm, 2 * nm, kDimOther, s);
+      if (st) return st;
+    }
+    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cp, cb, par, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+               launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
+                                 Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
+                                 none, 0, s));
+    LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
+               launch_leverage<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR, w.cand_score, w.cand_idx,
+                                  d.cand_blocks, d.cand_per_block, s));
+    if (k > 0) {
+      // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
+      lrp_status st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm),
+                                     kDimRPrev, w.part, Gx, false, s);
+      if (st) return st;
+      LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+                 launch_gemm_nn<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
+                                   Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev, Strided<T>{w.Q1, nm, 2 * nm},
+                                   cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
+      st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part, Ge,
+                          true, s);
+      if (st) return st;
+    }
+    LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cp, cb, par, s));
+    if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, s));
+      LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LRP_CUDA(cudaStreamSynchronize(s));
+      if (*p->active_host == 0) break;
+    }
+  }
+  return LRP_OK;
+}
+
+// Final truncation, singular values, info, then W factors = DST of the first r columns.
+template <typename T>
+static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  const int64_t nm = d.ld * d.M;
+  CoreBufs<T> cb = make_core_bufs<T>(p, w);
+  DstBatch<T, double> back;
+  back.in = w.back_in;
+  back.out = w.back_out;
+  back.ld_in = w.back_ldi;
+  back.ld_out = w.back_ldo;
+  back.nslots = count;
+  back.fixed_cols = 0;
+  back.ncols_dev = &p->st[0].r_out;
+  back.ncols_stride = (int)(sizeof(SolveState) / sizeof(int32_t));
+  back.ncols_mat_stride = 0;
+  back.active_dev = nullptr;
+  back.active_stride = 0;
+  back.require_active = 0;
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_finalize_impl<T>(cp, cb, back, w.ubufs, nm, 2 * nm, s));
+  const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
+  const int maxc = p->r_max < d.M ? p->r_max : d.M;
+  LRP_LAUNCH(p, LRP_K_DST, 1, s, (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s)));
+  return LRP_OK;
+}
+
+static lrp_status run_fp64(lrp_plan_s* p, int count, cudaStream_t s) {
+  CoreParams cp = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
+  lrp_status st;
+  if ((st = phase_forward<double>(p, p->w64, cp, count, true, s))) return st;
+  if ((st = phase_iterate<double>(p, p->w64, cp, count, s))) return st;
+  return phase_finalize<double>(p, p->w64, cp, count, s);
+}
+
+static RefineArgs make_refine_args(lrp_plan_s* p) {
+  const PlanDims& d = p->dims;
+  const int64_t MM = (int64_t)d.M * d.M;
+  const int64_t nm = d.ld * d.M;
+  const int64_t fm = d.ld * d.RF;
+  RefineArgs a;
+  a.n = d.n;
+  a.ld = d.ld;
+  a.M = d.M;
+  a.st = p->st;
+  a.prob = p->prob_dev;
+  a.lam = p->lam64;
+  a.Fh64 = {p->w64.Fh, fm, 2 * fm};
+  a.U32[0] = {p->w32.U[0], nm, 2 * nm};
+  a.U32[1] = {p->w32.U[1], nm, 2 * nm};
+  a.X = {p->w64.A, nm, 2 * nm};
+  a.stash = {p->w64.U[1], nm, 2 * nm};
+  a.Racc = {p->w64.Racc, MM, 2 * MM};
+  a.P = {p->w64.P, MM, 2 * MM};
+  a.Bf = {p->w64.Bf, MM, 2 * MM};
+  a.sig32 = p->w32.sig;
+  a.dvec = p->dvec;
+  a.s0 = p->s0;
+  a.sig_out = p->w64.sig;
+  a.sig_out_stride = 2 * (int64_t)d.M;
+  a.scratch = p->w64.scratch;
+  a.scratch_stride = kCoreScratch * MM;
+  a.w32 = p->w32.w;
+  a.wstride = p->w32.rf_cap;
+  return a;
+}
+
+// Mixed precision: FP32 Cross-DEIM to tol_in, FP64 residual recompression, an
+// FP32 correction solve, FP64 recompression of the sum, FP64 back transform.
+static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  const int64_t MM = (int64_t)d.M * d.M;
+  const int64_t nm = d.ld * d.M;
+  const int64_t fm32 = d.ld * p->w32.rf_cap;
+  const double eps32 = 1.1920928955078125e-07;
+  const double tol_in = p->tol > p->mixed_inner_tol ? p->tol : p->mixed_inner_tol;
+  CoreParams c32 = make_core_params<float>(p, count, tol_in, eps32, p->mixed_redundancy);
+  CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
+  CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
+  RefineArgs ra = make_refine_args(p);
+  const TallGeom& g = c64.g;
+  const Strided<const double> none{nullptr, 0, 0};
+  lrp_status st;
+  if ((st = phase_forward<float>(p, p->w32, c32, count, true, s))) return st;
+  if ((st = phase_forward<double>(p, p->w64, c64, count, false, s))) return st;
+  if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
+  for (int step = 0; step < p->opts.refine_steps; ++step) {
+    // Residual of the trial solution, recompressed in FP64.
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_prepare_refine(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_assemble_residual(ra, count, s));
+    if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
+    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
+                                      Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
+                                      Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
+    // FP32 correction solve on the residual (already in transformed variables).
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_setup_correction(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s,
+               (launch_convert<double, float>(d.n, d.ld, count, p->st, cs<double>(p->w64.Q1, nm, 2 * nm),
+                                              Strided<float>{p->w32.Fh, fm32, 2 * fm32}, kDimRF, s)));
+    if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
+    // What1 = What0 + dWhat, recompressed in FP64.
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_prepare_sum(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_assemble_sum(ra, count, s));
+    if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
+    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
+                                      Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
+                                      Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
+    if (step + 1 < p->opts.refine_steps) {
+      // Another step refines the FP64 sum: hand it back to the FP32 workspace.
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
+      return set_error(LRP_EINVAL, "refine_steps > 1 is not built");
+    }
+  }
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
+  return phase_finalize<double>(p, p->w64, c64, count, s);
+}
+}  // namespace lrp
+
+static lrp_status validate_problem(const lrp_plan_s* p, const lrp_problem& pr) {
+  const int64_t n = p->n;
+  if (pr.r_f < 1 || pr.r_f > p->dims.RF) return set_error(LRP_EINVAL, "r_f out of range [1, max_rhs_rank]");
+  if (!pr.d_U_f || !pr.d_V_f || !pr.d_s_f || !pr.d_U || !pr.d_S || !pr.d_V)
+    return set_error(LRP_EINVAL, "NULL factor pointer");
+  if (pr.ldu_f < n || pr.ldv_f < n || pr.ldu < n || pr.ldv < n) return set_error(LRP_EINVAL, "leading dimension < n");
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_problem* hp, void* stream) {
+  if (!p || !hp) return set_error(LRP_EINVAL, "NULL argument");
+  if (count < 1 || count > p->dims.B) return set_error(LRP_EINVAL, "count out of range [1, batch]");
+  std::lock_guard<std::mutex> lock(p->mu);
+  for (int i = 0; i < count; ++i) {
+    lrp_status s = validate_problem(p, hp[i]);
+    if (s != LRP_OK) return s;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    ProblemDev& d = p->prob_host[i];
+    d.rf = hp[i].r_f;
+    d.pad = 0;
+    d.U_f = hp[i].d_U_f;
+    d.ldu_f = hp[i].ldu_f;
+    d.s_f = hp[i].d_s_f;
+    d.V_f = hp[i].d_V_f;
+    d.ldv_f = hp[i].ldv_f;
+    d.U = hp[i].d_U;
+    d.ldu = hp[i].ldu;
+    d.S = hp[i].d_S;
+    d.V = hp[i].d_V;
+    d.ldv = hp[i].ldv;
+    d.info = hp[i].d_info;
+  }
+  LRP_CUDA(cudaMemcpyAsync(p->prob_dev, p->prob_host, sizeof(ProblemDev) * count, cudaMemcpyHostToDevice, s));
+  if (p->opts.precision == LRP_FP64) return run_fp64(p, count, s);
+  return run_mixed(p, count, s);
+}
+
+extern "C" lrp_status lrp_solve(lrp_plan_t p, int32_t r_f, const double* U_f, int64_t ldu_f, const double* s_f,
+                                const double* V_f, int64_t ldv_f, double* U, int64_t ldu, double* S, double* V,
+                                int64_t ldv, lrp_info* info, void* stream) {
+  lrp_problem pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.r_f = r_f;
+  pr.d_U_f = U_f;
+  pr.ldu_f = ldu_f;
+  pr.d_s_f = s_f;
+  pr.d_V_f = V_f;
+  pr.ldv_f = ldv_f;
+  pr.d_U = U;
+  pr.ldu = ldu;
+  pr.d_S = S;
+  pr.d_V = V;
+  pr.ldv = ldv;
+  pr.d_info = info;
+  return lrp_solve_batch(p, 1, &pr, stream);
+}
+
+extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                               void* stream) {
+  if (n < 1 || !is_pow2(n + 1)) return set_error(LRP_EINVAL, "n+1 must be a power of two >= 2");
+  if (ncols < 0 || !X || !Y || ldx < n || ldy < n) return set_error(LRP_EINVAL, "bad DST arguments");
+  if (!dst_smem_supported(n, true)) return set_error(LRP_EINVAL, "n+1 > 8192 needs the multi-pass DST (not built)");
+  if (ncols == 0) return LRP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Per-call job arrays: tiny device allocation kept for the lifetime of the process per n.
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  struct Cache {
+    int64_t n = 0;
+    int dev = -1;
+    void* tw = nullptr;
+    void* arrays = nullptr;
+  };
+  static Cache cache[8];
+  int dev = 0;
+  LRP_CUDA(cudaGetDevice(&dev));
+  Cache* c = nullptr;
+  for (auto& e : cache)
+    if (e.n == n && e.dev == dev) c = &e;
+  if (!c) {
+    for (auto& e : cache)
+      if (e.n == 0) {
+        c = &e;
+        break;
+      }
+    if (!c) {
+      c = &cache[0];
+      cudaFree(c->tw);
+      cudaFree(c->arrays);
+    }
+    c->n = n;
+    c->dev = dev;
+    c->tw = dst_make_twiddles(n + 1, true, nullptr);
+    LRP_CUDA(cudaMalloc(&c->arrays, 4 * sizeof(void*)));
+    LRP_CUDA(cudaDeviceSynchronize());
+  }
+  const void* h[4] = {X, Y, (const void*)(intptr_t)ldx, (const void*)(intptr_t)ldy};
+  LRP_CUDA(cudaMemcpyAsync(c->arrays, h, sizeof(h), cudaMemcpyHostToDevice, s));
+  LRP_CUDA(cudaStreamSynchronize(s));  // h lives on this stack frame
+  DstBatch<double, double> job;
+  const void* const* arr = (const void* const*)c->arrays;
+  job.in = (const double* const*)(arr + 0);
+  job.out = (double* const*)(arr + 1);
+  job.ld_in = (const int64_t*)(arr + 2);
+  job.ld_out = (const int64_t*)(arr + 3);
+  job.nslots = 1;
+  job.fixed_cols = ncols;
+  job.ncols_dev = nullptr;
+  job.ncols_stride = 0;
+  job.ncols_mat_stride = 0;
+  job.active_dev = nullptr;
+  job.active_stride = 0;
+  job.require_active = 0;
+  LRP_CUDA((dst1_launch<double, double, double>(n, job, ncols, 1, 1, c->tw, s)));
+  return LRP_OK;
+}
+
+extern "C" const char* lrp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* lrp_status_string(lrp_status s) {
+  switch (s) {
+    case LRP_OK: return "LRP_OK";
+    case LRP_EINVAL: return "LRP_EINVAL";
+    case LRP_ENOMEM: return "LRP_ENOMEM";
+    case LRP_ECUDA: return "LRP_ECUDA";
+    case LRP_ETIMEDOUT: return "LRP_ETIMEDOUT";
+    case LRP_NOT_CONVERGED: return "LRP_NOT_CONVERGED";
+    case LRP_RANK_CAPPED: return "LRP_RANK_CAPPED";
+    case LRP_EAGAIN: return "LRP_EAGAIN";
+    case LRP_ECAPACITY: return "LRP_ECAPACITY";
+  }
+  return "LRP_UNKNOWN";
+}
+
+static_assert(sizeof(lrp_opts) == 40, "lrp_opts layout");
+static_assert(sizeof(lrp_info) == 64, "lrp_info layout");
+static_assert(sizeof(lrp_problem) == 96, "lrp_problem layout");

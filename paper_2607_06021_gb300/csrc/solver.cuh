@@ -1,0 +1,130 @@
+// Plan object and workspace layout (see solver.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "core.cuh"
+
+// Device allocations of one plan (released together).
+struct DeviceArena {
+  std::vector<void*> blocks;
+  size_t total = 0;
+  bool failed = false;
+  void* raw(size_t bytes);
+  template <typename T>
+  T* get(size_t count) {
+    return reinterpret_cast<T*>(raw(count * sizeof(T) + 1));
+  }
+  bool ok() const { return !failed; }
+  void release();
+};
+
+namespace lrp {
+
+lrp_status set_error(lrp_status s, const std::string& msg);
+
+struct PlanDims {
+  int n;
+  int64_t ld;          // leading dimension of n-row workspace matrices
+  int B;               // batch slots
+  int RF;              // right-hand-side rank capacity
+  int M;               // index-set / rank capacity (m_cap)
+  int NB;              // Gram partial row blocks
+  int rows_per_block;
+  int cand_blocks;     // leverage candidate blocks (<= 1024 rows each)
+  int cand_per_block;
+};
+
+// HBM layout per batch slot b and side s (0 = rows/U/I, 1 = columns/V/J); every
+// n-row matrix is column-major with leading dimension ld:
+//   Fh   [b][s]  n x RF   transformed right-hand-side factor (Uhat_f, Vhat_f)
+//   A    [b][s]  n x M    cross matrix C = What(:,J) / R^T = What(I,:)^T
+//   Q1,Q2[b][s]  n x M    CholeskyQR pass outputs (Q = Q2 P3 implicitly)
+//   U[2] [b][s]  n x M    current / previous factors U_k, V_k (ping-pong)
+//   part [b][s][NB] M x M FP64 Gram partials; G, Racc, P, Bf, X, GE: M x M FP64
+template <typename T>
+struct Workspace {
+  T* Fh = nullptr;
+  T* w = nullptr;
+  T* A = nullptr;
+  T* Q1 = nullptr;
+  T* Q2 = nullptr;
+  T* U[2] = {nullptr, nullptr};
+  double* part = nullptr;
+  double* G = nullptr;
+  double* Racc = nullptr;
+  double* P = nullptr;
+  double* Bf = nullptr;
+  double* X = nullptr;
+  double* GE = nullptr;
+  double* sig = nullptr;
+  double* scratch = nullptr;
+  int32_t* idx = nullptr;
+  double* cand_score = nullptr;
+  int32_t* cand_idx = nullptr;
+  T** back_in = nullptr;
+  double** back_out = nullptr;
+  int64_t* back_ldi = nullptr;
+  int64_t* back_ldo = nullptr;
+  T** ubufs = nullptr;
+  const double** fwd_in = nullptr;
+  T** fwd_out = nullptr;
+  int64_t* fwd_ldi = nullptr;
+  int64_t* fwd_ldo = nullptr;
+  int rf_cap = 0;  // columns of Fh (and entries of w) per slot and side
+  lrp_status allocate(const PlanDims& d, DeviceArena& arena, int rf_cap);
+};
+
+}  // namespace lrp
+
+// Launch counts and optional CUDA-event timing per kernel class.
+struct KernelStats {
+  bool timing = false;
+  int64_t launches[LRP_K_COUNT] = {};
+  double ms[LRP_K_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int cls, e0, e1;
+  };
+  std::vector<Rec> pending;
+  int next_event = 0;
+  int take(cudaStream_t s);
+  void drain();
+  void release();
+};
+
+struct lrp_plan_s {
+  int64_t n = 0;
+  double tol = 0.0;
+  int r_max = 0;
+  lrp_opts opts;
+  lrp::PlanDims dims;
+  int device = 0;
+  DeviceArena arena;
+  lrp::SolveState* st = nullptr;
+  double* lam64 = nullptr;
+  float* lam32 = nullptr;
+  void* tw64 = nullptr;
+  void* tw32 = nullptr;
+  lrp::ProblemDev* prob_dev = nullptr;
+  lrp::ProblemDev* prob_host = nullptr;  // pinned
+  void* host_ptrs = nullptr;             // pinned staging for DST job arrays
+  int32_t* active_dev = nullptr;
+  double* acct = nullptr;                // [B][LRP_K_COUNT][2] algorithmic flops / bytes
+  double* dvec = nullptr;                // [B][M] weights of the stacked refinement products
+  double* s0 = nullptr;                  // [B][M] singular values of the trial solution
+  double mixed_inner_tol = 3e-5;         // FP32 Cross-DEIM tolerance (relative)
+  double mixed_redundancy = 1e-6;        // redundancy threshold on FP32 data
+  double mixed_residual_tol = 1e-7;      // tail-rule truncation of the recompressed residual
+  int32_t* active_host = nullptr;        // pinned
+  lrp::Workspace<double> w64;
+  lrp::Workspace<float> w32;
+  KernelStats stats;
+  std::mutex mu;
+};

@@ -1,0 +1,389 @@
+// Tall-skinny kernels of the Cross-DEIM iteration, batched over problems and
+// the two sides (blockIdx.z = slot * 2 + side).
+//
+//  k_cross     C = What(:,J) and R^T = What(I,:)^T from the transformed
+//              right-hand side (Algorithm scross, "C = G(:,J), R = G(I,:)";
+//              entries by Eq. g_for_p at O(r_f) each, Sec. 2.1 / Sec. 3.2).
+//  k_gemm_nn   n x m times m x m' (the triangular applies of CholeskyQR, the
+//              factor update U_k = Q U~ of Algorithm scross, and E = U' - U X).
+//  k_gram      per-row-block partial products X^T Y in FP64 (Gram matrices of
+//              CholeskyQR, cross-Grams of consecutive iterates).
+//  k_reduce    deterministic sum of the partials.
+//  k_leverage  leverage scores pi_i = sum_c U(i,c)^2 / c (Algorithm
+//              LeverageScores) and per-block top-c candidates.
+//
+// All kernels read their data-dependent sizes (|I|, |J|, ranks) from the
+// per-slot SolveState and return early for finished slots.  Tiles are 64 rows
+// x 64 columns with 256 threads, each thread owning a 4 x 4 strided block.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "tall.cuh"
+
+namespace lrp {
+
+namespace {
+constexpr int TM = 64;
+constexpr int TN = 64;
+constexpr int TK = 16;
+constexpr int TKG = 32;
+constexpr int NT = 256;
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __restrict__ st_all, CrossArgs<T> a) {
+  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const SolveState st = st_all[slot];
+  if (!st.active) return;
+  const int m = st.cnt[1 - side];
+  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
+  if (c0 >= m || r0 >= g.n) return;
+  const int rf = st.rf;
+  const T* Fs = a.F.at(slot, side);
+  const T* Fo = a.F.at(slot, 1 - side);
+  const int32_t* ix = a.idx.at(slot, 1 - side);
+  const T* w = a.w + (int64_t)slot * a.wstride;
+
+  __shared__ T As[TK][TM];
+  __shared__ T Bs[TK][TN];
+  __shared__ int jc[TN];
+  __shared__ T lamc[TN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < TN) {
+    const int c = c0 + tid;
+    const int j = (c < m) ? ix[c] : -1;
+    jc[tid] = j;
+    lamc[tid] = (j >= 0) ? a.lam[j] : (T)1;
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+
+  for (int k0 = 0; k0 < rf; k0 += TK) {
+#pragma unroll
+    for (int q = 0; q < (TK * TM) / NT; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e / TM, i = e % TM;
+      const int row = r0 + i, k = k0 + kk;
+      As[kk][i] = (row < g.n && k < rf) ? Fs[(int64_t)k * g.ld + row] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < (TK * TN) / NT; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e / TN, c = e % TN;
+      const int k = k0 + kk, j = jc[c];
+      Bs[kk][c] = (j >= 0 && k < rf) ? w[k] * Fo[(int64_t)k * g.ld + j] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  T* A = a.A.at(slot, side);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + ty + 16 * i;
+    if (row >= g.n) continue;
+    const T li = a.lam[row];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tx + 16 * j;
+      if (c0 + c < m) A[(int64_t)(c0 + c) * g.ld + row] = acc[i][j] / (li + lamc[c]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
+                                                int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
+                                                Strided<const T> zsub, int mode) {
+  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const SolveState st = st_all[slot];
+  if (!st.active) return;
+  const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
+  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
+  if (c0 >= mo || r0 >= g.n) return;
+  const T* X = in.at(slot, side);
+  const double* Bm = bm.at(slot, side);
+  __shared__ T As[TK][TM];
+  __shared__ T Bs[TK][TN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+  for (int k0 = 0; k0 < mi; k0 += TK) {
+#pragma unroll
+    for (int q = 0; q < (TK * TM) / NT; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e / TM, i = e % TM;
+      const int row = r0 + i, k = k0 + kk;
+      As[kk][i] = (row < g.n && k < mi) ? X[(int64_t)k * g.ld + row] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < (TK * TN) / NT; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e % TK, c = e / TK;
+      const int k = k0 + kk, col = c0 + c;
+      Bs[kk][c] = (k < mi && col < mo) ? (T)Bm[(int64_t)col * g.M + k] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  T* O = out.at(slot, side);
+  const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + ty + 16 * i;
+    if (row >= g.n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tx + 16 * j;
+      if (col >= mo) continue;
+      const int64_t o = (int64_t)col * g.ld + row;
+      O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gram(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> xs,
+                                             int sel_x, Strided<const T> ys, int sel_y, double* __restrict__ part,
+                                             int tiles, bool symmetric) {
+  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const SolveState st = st_all[slot];
+  if (!st.active) return;
+  const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
+  const int ta = blockIdx.y / tiles, tb = blockIdx.y % tiles;
+  const int a0 = ta * TM, b0 = tb * TN;
+  if (a0 >= mx || b0 >= my) return;
+  if (symmetric && tb < ta) return;
+  const int blk = blockIdx.x;
+  const int rbeg = blk * g.rows_per_block;
+  const int rend = min(g.n, rbeg + g.rows_per_block);
+  const T* X = xs.at(slot, side);
+  const T* Y = ys.at(slot, side);
+  __shared__ T As[TKG][TM + 1];
+  __shared__ T Bs[TKG][TN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int r = rbeg; r < rend; r += TKG) {
+#pragma unroll
+    for (int q = 0; q < (TKG * TM) / NT; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e % TKG, c = e / TKG;
+      const int row = r + kk;
+      As[kk][c] = (row < rend && a0 + c < mx) ? X[(int64_t)(a0 + c) * g.ld + row] : (T)0;
+      Bs[kk][c] = (row < rend && b0 + c < my) ? Y[(int64_t)(b0 + c) * g.ld + row] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TKG; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = (double)As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = (double)Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 16 * i;
+    if (a >= mx) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx + 16 * j;
+      if (b < my) P[(int64_t)b * g.M + a] = acc[i][j];
+    }
+  }
+}
+
+__global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int sel_x, int sel_y,
+                         const double* __restrict__ part, Strided<double> G, bool symmetric) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState& st = st_all[slot];
+  if (!st.active) return;
+  const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = (int)(e % g.M), b = (int)(e / g.M);
+  if (b >= g.M || a >= mx || b >= my) return;
+  if (symmetric && b < a) return;
+  const double* P = part + (int64_t)(slot * 2 + side) * g.NB * (int64_t)g.M * g.M + (int64_t)b * g.M + a;
+  double s = 0.0;
+  for (int blk = 0; blk < g.NB; ++blk) s += P[(int64_t)blk * g.M * g.M];
+  double* out = G.at(slot, side);
+  out[(int64_t)b * g.M + a] = s;
+  if (symmetric) out[(int64_t)a * g.M + b] = s;
+}
+
+// Bitonic sort of (score desc, index asc) pairs in shared memory; len a power of two.
+__device__ inline bool before(double sa, int ia, double sb, int ib) {
+  return (sa > sb) || (sa == sb && ia < ib);
+}
+
+__device__ void bitonic_sort(double* key, int* idx, int len) {
+  for (int size = 2; size <= len; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const int p = t ^ stride;
+        if (p > t) {
+          const bool up = ((t & size) == 0);
+          const bool t_first = before(key[t], idx[t], key[p], idx[p]);
+          if (up != t_first) {
+            const double k = key[t];
+            key[t] = key[p];
+            key[p] = k;
+            const int i = idx[t];
+            idx[t] = idx[p];
+            idx[p] = i;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> us, int sel,
+                           double* __restrict__ cscore, int32_t* __restrict__ cidx, int cand_blocks,
+                           int cand_per_block, int rows_per_cand_block, int sort_len) {
+  extern __shared__ unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int* id = reinterpret_cast<int*>(key + sort_len);
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState st = st_all[slot];
+  if (!st.active) return;
+  const int c = dim_of(st, side, sel);
+  const int blk = blockIdx.x;
+  const int rbeg = blk * rows_per_cand_block;
+  const int rend = min(g.n, rbeg + rows_per_cand_block);
+  const T* U = us.at(slot, side);
+  for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+    const int row = rbeg + t;
+    double s = -1.0;
+    int ii = 0x7fffffff;
+    if (row < rend) {
+      s = 0.0;
+      for (int q = 0; q < c; ++q) {
+        const double v = (double)U[(int64_t)q * g.ld + row];
+        s = fma(v, v, s);
+      }
+      ii = row;
+    }
+    key[t] = s;
+    id[t] = ii;
+  }
+  __syncthreads();
+  bitonic_sort(key, id, sort_len);
+  const int64_t base = ((int64_t)(slot * 2 + side) * cand_blocks + blk) * cand_per_block;
+  for (int t = threadIdx.x; t < cand_per_block; t += blockDim.x) {
+    const bool ok = (t < c) && (t < sort_len) && key[t] >= 0.0;
+    cscore[base + t] = ok ? key[t] : -1.0;
+    cidx[base + t] = ok ? id[t] : -1;
+  }
+}
+
+// ------------------------------------------------------------------ launches
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+template <typename T>
+cudaError_t launch_cross(const TallGeom& g, const SolveState* st, const CrossArgs<T>& a, cudaStream_t s) {
+  dim3 grid(cdiv(g.n, TM), cdiv(g.M, TN), g.nslots * 2);
+  k_cross<T><<<grid, NT, 0, s>>>(g, st, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
+                           Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
+                           cudaStream_t s) {
+  dim3 grid(cdiv(g.n, TM), cdiv(g.M, TN), g.nslots * 2);
+  k_gemm_nn<T><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T> x, int sel_x,
+                        Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
+                        cudaStream_t s) {
+  const int tiles = cdiv(g.M, TM);
+  dim3 grid(g.NB, tiles * tiles, g.nslots * 2);
+  k_gram<T><<<grid, NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, tiles, symmetric);
+  (void)G;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, int sel_y, const double* part,
+                          Strided<double> G, bool symmetric, cudaStream_t s) {
+  dim3 rgrid(cdiv(g.M * g.M, 256), g.nslots * 2);
+  k_reduce<<<rgrid, 256, 0, s>>>(g, st, sel_x, sel_y, part, G, symmetric);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel, double* cand_score,
+                            int32_t* cand_idx, int cand_blocks, int cand_per_block, cudaStream_t s) {
+  const int rows = cdiv(g.n, cand_blocks);
+  int len = 1;
+  while (len < rows) len <<= 1;
+  const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
+  auto kern = k_leverage<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(cand_blocks, g.nslots * 2);
+  kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len);
+  return cudaGetLastError();
+}
+
+#define LRP_INST(T)                                                                                           \
+  template cudaError_t launch_cross<T>(const TallGeom&, const SolveState*, const CrossArgs<T>&, cudaStream_t); \
+  template cudaError_t launch_gemm_nn<T>(const TallGeom&, const SolveState*, Strided<const T>, int,          \
+                                         Strided<const double>, int, Strided<T>, Strided<const T>, int,       \
+                                         cudaStream_t);                                                        \
+  template cudaError_t launch_gram<T>(const TallGeom&, const SolveState*, Strided<const T>, int,             \
+                                      Strided<const T>, int, double*, Strided<double>, bool, cudaStream_t);   \
+  template cudaError_t launch_leverage<T>(const TallGeom&, SolveState*, Strided<const T>, int, double*,      \
+                                          int32_t*, int, int, cudaStream_t);
+LRP_INST(double)
+LRP_INST(float)
+#undef LRP_INST
+
+}  // namespace lrp

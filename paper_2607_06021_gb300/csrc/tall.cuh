@@ -1,0 +1,56 @@
+// Tall-skinny kernels over all problems of a batch (see tall.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lrp {
+
+// Geometry shared by the tall kernels of one plan.
+struct TallGeom {
+  int n;        // rows
+  int64_t ld;   // leading dimension of every n-row workspace matrix (>= n, multiple of 32)
+  int M;        // capacity (m_cap): columns of n-row matrices, order of small matrices
+  int nslots;   // batch slots launched
+  int NB;       // row blocks of the Gram partials
+  int rows_per_block;  // ceil(n / NB) rounded up to 32
+};
+
+template <typename T>
+struct CrossArgs {
+  Strided<const T> F;          // transformed RHS factors, n x rf, ld = geom.ld
+  const T* w;                  // per slot: rf weights h^2 s_f (slot stride wstride)
+  int wstride;
+  const T* lam;                // eigenvalues lambda_1..lambda_n (shared)
+  Strided<const int32_t> idx;  // index sets, M entries per (slot, side)
+  Strided<T> A;                // out: n x M
+};
+
+template <typename T>
+cudaError_t launch_cross(const TallGeom& g, const SolveState* st, const CrossArgs<T>& a, cudaStream_t s);
+
+// Out[s] = In[s](:, :mi) * Bm[s](:mi, :mo)  (mode 0)  or  Out = Zsub - In * Bm  (mode 1).
+// mi, mo come from the state through the DimSel codes; Bm is M x M col-major (ld M).
+template <typename T>
+cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
+                           Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
+                           cudaStream_t s);
+
+// part[s][blk] = X[s](rows of blk, :mx)^T Y[s](rows of blk, :my) in FP64 (launch_gram),
+// then G[s] = sum over blk (launch_reduce).
+template <typename T>
+cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T> x, int sel_x,
+                        Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
+                        cudaStream_t s);
+
+cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, int sel_y, const double* part,
+                          Strided<double> G, bool symmetric, cudaStream_t s);
+
+// Leverage scores of U[s](:, :c) rows (c from sel) and per-block top-c candidates.
+template <typename T>
+cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel,
+                            double* cand_score, int32_t* cand_idx, int cand_blocks, int cand_per_block,
+                            cudaStream_t s);
+
+}  // namespace lrp

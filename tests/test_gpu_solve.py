@@ -1,0 +1,76 @@
+"""FP64 solver parity: the GPU Cross-DEIM path against the CPU oracle (same
+reading of the paper) and against the exact solution (Eq. g_for_p)."""
+import numpy as np
+import pytest
+
+import lrp_inputs as li
+from oracle import cross_deim as cd
+from oracle import poisson as po
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_solve(rhs, tol, r_max, m_cap=0, batch=1, **kw):
+    import paper_2607_06021_gb300 as lrp
+    from tests.gpu_util import rhs_dev, to_np
+    plan = lrp.Plan(rhs.n, tol, r_max, max_rhs_rank=max(rhs.rank, 1), m_cap=m_cap, batch=batch, **kw)
+    U, S, V, info = plan.solve(*rhs_dev(rhs))
+    plan.close()
+    return to_np(U), to_np(S), to_np(V), info
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_n255_fp64_matches_oracle(seed):
+    rhs = li.workload_single_small(seed)
+    tol, r_max, m_cap = 1e-10, 32, 68
+    U, S, V, info = _gpu_solve(rhs, tol, r_max, m_cap=m_cap, seed=seed)
+    Uo, So, Vo, oinfo, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, r_max, seed=seed, m_cap=m_cap)
+    err_gpu = po.rel_error_vs_exact(U, S, V, G)
+    err_cpu = po.rel_error_vs_exact(Uo, So, Vo, G)
+    diff = po.lowrank_rel_diff(U, S, V, Uo, So, Vo)
+    assert err_gpu < 1e-9, (err_gpu, err_cpu, info)
+    assert diff < 1e-9, (diff, info, oinfo.iterations)
+    assert np.abs(U.T @ U - np.eye(S.shape[0])).max() < 1e-10
+    assert np.all(np.diff(S) <= 1e-15 * S[0])
+
+
+def test_eigenfunction_rhs_rank_one_exact():
+    n, p, q = 255, 9, 40
+    rhs = li.eigenfunction_rhs(n, p, q, 2.5)
+    U, S, V, info = _gpu_solve(rhs, 1e-12, 8)
+    G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+    assert info["rank"] == 1
+    assert po.rel_error_vs_exact(U, S, V, G) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_n4095_fp64_matches_oracle(seed):
+    rhs = li.workload_n4095(seed)
+    tol, r_max, m_cap = 1e-8, 64, 148
+    U, S, V, info = _gpu_solve(rhs, tol, r_max, m_cap=m_cap, seed=seed)
+    Uo, So, Vo, oinfo, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, r_max, seed=seed, m_cap=m_cap)
+    err_gpu = po.rel_error_vs_exact(U, S, V, G)
+    diff = po.lowrank_rel_diff(U, S, V, Uo, So, Vo)
+    assert err_gpu < 10 * tol, (err_gpu, info)
+    assert diff < 10 * tol, (diff, info)
+
+
+@pytest.mark.parametrize("n", [1, 3, 7, 31, 8191])
+def test_edge_sizes(n):
+    rhs = li.gaussian_eigen_rhs(n, 5, 1 if n < 7 else 3)
+    U, S, V, info = _gpu_solve(rhs, 1e-10, 16)
+    G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+    assert po.rel_error_vs_exact(U, S, V, G) < 1e-8
+
+
+def test_batch_equals_individual_solves():
+    import paper_2607_06021_gb300 as lrp
+    from tests.gpu_util import rhs_dev, to_np
+    rhss = [li.gaussian_eigen_rhs(1023, s, r) for s, r in [(1, 2), (2, 7), (3, 12), (4, 5)]]
+    plan = lrp.Plan(1023, 1e-10, 32, max_rhs_rank=16, batch=4)
+    res = plan.solve_batch([rhs_dev(r) for r in rhss])
+    for rhs, (U, S, V, info) in zip(rhss, res):
+        Ua, Sa, Va, _ = _gpu_solve(rhs, 1e-10, 32, m_cap=0)
+        assert po.lowrank_rel_diff(to_np(U), to_np(S), to_np(V), Ua, Sa, Va) < 1e-12
+    plan.close()
