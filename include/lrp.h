@@ -175,7 +175,8 @@ typedef enum lrp_kernel_class {
   LRP_K_SELECT = 8,    /* index-set enrichment per problem */
   LRP_K_STOP = 9,      /* convergence test per problem */
   LRP_K_OTHER = 10,    /* setup, finalize, counters */
-  LRP_K_COUNT = 11
+  LRP_K_REFINE = 11,   /* mixed precision: residual/sum assembly and recompression cores */
+  LRP_K_COUNT = 12
 } lrp_kernel_class;
 
 /*

@@ -84,17 +84,27 @@ __device__ void acct_back(double* row, int n_, int r_out, int w_) {
 
 // ------------------------------------------------------------------- kernels
 
+constexpr int kCholSmemDim = 64;
+constexpr size_t kCholSmemBytes = 3 * kCholSmemDim * kCholSmemDim * sizeof(double);
+
 template <typename T>
 __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int sel, int pass) {
+  extern __shared__ double chol_smem[];
   const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
   const int m = dim_of(*stp, side, sel);
   const double* G = b.G.at(slot, side);
+  // Working triangle W, R^{-1} / product buffer Tm and a copy of R_acc: shared
+  // memory (leading dimension kCholSmemDim) when m <= kCholSmemDim, else the
+  // slot's global scratch (leading dimension M).
+  const bool in_smem = m <= kCholSmemDim;
+  const int Lc = in_smem ? kCholSmemDim : M;
   double* base = b.scratch + (int64_t)slot * b.scratch_stride;
-  double* W = base + (int64_t)(8 + side) * M * M;     // working triangle
-  double* Tm = base + (int64_t)(10 + side) * M * M;   // R^{-1} (FP64), then R * Racc
+  double* W = in_smem ? chol_smem : base + (int64_t)(8 + side) * M * M;
+  double* Tm = in_smem ? chol_smem + kCholSmemDim * kCholSmemDim : base + (int64_t)(10 + side) * M * M;
+  double* Rc = in_smem ? chol_smem + 2 * kCholSmemDim * kCholSmemDim : nullptr;
   double* P = b.P.at(slot, side);
   double* Racc = b.Racc.at(slot, side);
   __shared__ double red[32];
@@ -114,7 +124,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
     const double v = G[(int64_t)j * M + i] * dsc[i] * dsc[j];
-    W[(int64_t)j * M + i] = (i <= j) ? v : 0.0;
+    W[(int64_t)j * Lc + i] = (i <= j) ? v : 0.0;
     if (i == j) {
       tr += v;
       mx = fmax(mx, v);
@@ -124,21 +134,21 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   mx = block_max(mx, red);
   const double shift = (pass == 0) ? p.shift_rel * tr : 0.0;
   if (pass == 0 && tid == 0) stp->gram_trace[side] = tr;
-  for (int j = tid; j < m; j += nt) W[(int64_t)j * M + j] += (dsc[j] > 0.0) ? shift : 0.0;
+  for (int j = tid; j < m; j += nt) W[(int64_t)j * Lc + j] += (dsc[j] > 0.0) ? shift : 0.0;
   const double thr = (pass == 0) ? 0.0 : p.drop_rel * mx;
   __syncthreads();
 
   for (int j = 0; j < m; ++j) {
-    const double d = W[(int64_t)j * M + j];
+    const double d = W[(int64_t)j * Lc + j];
     const bool drop = !(d > thr);
     const double rjj = drop ? 0.0 : sqrt(d);
     __syncthreads();
     for (int l = j + 1 + tid; l < m; l += nt) {
-      double* wl = W + (int64_t)l * M + j;
+      double* wl = W + (int64_t)l * Lc + j;
       *wl = drop ? 0.0 : (*wl / rjj);
     }
     if (tid == 0) {
-      W[(int64_t)j * M + j] = rjj;
+      W[(int64_t)j * Lc + j] = rjj;
       dropped[j] = drop ? 1 : 0;
     }
     __syncthreads();
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
         const int kk = e % t, ll = e / t;
         if (kk > ll) continue;
         const int k = j + 1 + kk, l = j + 1 + ll;
-        W[(int64_t)l * M + k] -= W[(int64_t)k * M + j] * W[(int64_t)l * M + j];
+        W[(int64_t)l * Lc + k] -= W[(int64_t)k * Lc + j] * W[(int64_t)l * Lc + j];
       }
     }
     __syncthreads();
@@ -156,7 +166,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
 
   // P = R^{-1}: column l by back substitution (dropped rows give zeros).
   for (int l = tid; l < m; l += nt) {
-    double* x = Tm + (int64_t)l * M;
+    double* x = Tm + (int64_t)l * Lc;
     for (int i = m - 1; i > l; --i) x[i] = 0.0;
     for (int i = l; i >= 0; --i) {
       if (dropped[i]) {
@@ -164,45 +174,68 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
         continue;
       }
       double s = (i == l) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= l; ++k) s -= W[(int64_t)k * M + i] * x[k];
-      x[i] = s / W[(int64_t)i * M + i];
+      for (int k = i + 1; k <= l; ++k) s -= W[(int64_t)k * Lc + i] * x[k];
+      x[i] = s / W[(int64_t)i * Lc + i];
     }
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
-    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * M + i];
+    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * Lc + i];
   }
   __syncthreads();
   // Racc <- R (pass 0, undoing the equilibration) or R * Racc.
   if (pass == 0) {
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? W[(int64_t)j * M + i] / dsc[j] : 0.0;
+      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? W[(int64_t)j * Lc + i] / dsc[j] : 0.0;
     }
   } else {
+    const double* Ro = Racc;
+    int ldr = M;
+    if (in_smem) {
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = e % m, j = e / m;
+        Rc[(int64_t)j * Lc + i] = Racc[(int64_t)j * M + i];
+      }
+      __syncthreads();
+      Ro = Rc;
+      ldr = Lc;
+    }
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, l = e / m;
       double s = 0.0;
       if (i <= l)
-        for (int k = i; k <= l; ++k) s += W[(int64_t)k * M + i] * Racc[(int64_t)l * M + k];
-      Tm[(int64_t)l * M + i] = s;
+        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * Ro[(int64_t)l * ldr + k];
+      Tm[(int64_t)l * Lc + i] = s;
     }
     __syncthreads();
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * M + i];
+      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * Lc + i];
     }
   }
 }
 
+// Small matrices of k_core live in six regions of L x L doubles: shared memory
+// when |I|, |J| <= kCoreSmemDim (L = kCoreSmemDim), else the slot's global scratch
+// (L = M).  Region use: R0 Q(I,:) -> compaction work; R1 Z(J,:) -> eta work;
+// R2 pinv work -> V of the core SVD -> V_k(J,:); R3 V of the pinv SVD -> U~;
+// R4 T1 -> V~; R5 core -> U_k(I,:).
+constexpr int kCoreSmemDim = 64;
+constexpr size_t kCoreSmemBytes = 6 * kCoreSmemDim * kCoreSmemDim * sizeof(double);
+
+// The small core computes in the precision of the iteration (TC = T): FP64 for
+// the FP64 solve, FP32 for the inner solves of the mixed-precision path.
 template <typename T>
 __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int parity) {
+  using TC = T;
+  extern __shared__ double core_smem_d[];
+  TC* core_smem = reinterpret_cast<TC*>(core_smem_d);
   const int slot = blockIdx.x;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
-  const int64_t MM = (int64_t)M * M;
   const int q = stp->cnt[0];   // |I|
   const int pc = stp->cnt[1];  // |J|
   if (q < 1 || pc < 1) {
@@ -212,17 +245,18 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
     }
     return;
   }
-  double* base = b.scratch + (int64_t)slot * b.scratch_stride;
-  double* QI = base + 0 * MM;  // q x pc
-  double* ZJ = base + 1 * MM;  // pc x q
-  double* W1 = base + 2 * MM;
-  double* V1 = base + 3 * MM;
-  double* Mt = base + 4 * MM;
-  double* V2 = base + 5 * MM;
-  double* T1 = base + 6 * MM;
-  double* UI = base + 7 * MM;  // U_k(I,:)  q x r
-  double* VJ = base + 8 * MM;  // V_k(J,:)  pc x r
-  double* WK = base + 9 * MM;  // eta work
+  const bool in_smem = (q <= kCoreSmemDim && pc <= kCoreSmemDim);
+  const int L = in_smem ? kCoreSmemDim : M;
+  const int64_t LL = (int64_t)L * L;
+  TC* base = in_smem ? core_smem : reinterpret_cast<TC*>(b.scratch + (int64_t)slot * b.scratch_stride);
+  TC* R0 = base + 0 * LL;
+  TC* R1 = base + 1 * LL;
+  TC* R2 = base + 2 * LL;
+  TC* R3 = base + 3 * LL;
+  TC* R4 = base + 4 * LL;
+  TC* R5 = base + 5 * LL;
+  TC* QI = R0;  // q x pc
+  TC* ZJ = R1;  // pc x q
   const T* Q20 = b.Q2.at(slot, 0);
   const T* Q21 = b.Q2.at(slot, 1);
   const double* P0 = b.P.at(slot, 0);
@@ -244,87 +278,91 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
   for (int e = tid; e < q * pc; e += nt) {
     const int a = e % q, c = e / q;
     const int64_t row = I[a];
-    double s = 0.0;
-    for (int d = 0; d <= c; ++d) s += (double)Q20[(int64_t)d * ld + row] * P0[(int64_t)c * M + d];
-    QI[(int64_t)c * M + a] = s;
+    TC s = 0;
+    for (int d = 0; d <= c; ++d) s += (TC)Q20[(int64_t)d * ld + row] * (TC)P0[(int64_t)c * M + d];
+    QI[(int64_t)c * L + a] = s;
   }
   for (int e = tid; e < pc * q; e += nt) {
     const int a = e % pc, c = e / pc;
     const int64_t row = J[a];
-    double s = 0.0;
-    for (int d = 0; d <= c; ++d) s += (double)Q21[(int64_t)d * ld + row] * P1[(int64_t)c * M + d];
-    ZJ[(int64_t)c * M + a] = s;
+    TC s = 0;
+    for (int d = 0; d <= c; ++d) s += (TC)Q21[(int64_t)d * ld + row] * (TC)P1[(int64_t)c * M + d];
+    ZJ[(int64_t)c * L + a] = s;
   }
   __syncthreads();
-  const double eps64 = 2.220446049250313e-16;
+  const double eps_c = Eps<TC>::value;
   const int mx = max(pc, q);
   const int branch = (pc <= q) ? 0 : 1;
+  // Pseudoinverse solve and the core M (pc x q), stored as Mt in R5 (tall orientation).
+  TC* W1 = R2;
+  TC* V1 = R3;
+  TC* T1 = R4;
+  TC* Mt = R5;
+  TC* V2 = R2;  // reuses W1 once T1 is formed
   int nsv;
   if (branch == 0) {
-    // pinv(Q(I,:)) R_R^T: Q(I,:) = U1 S1 V1^T (q x pc), then M = V1 S1^+ U1^T R_R^T (pc x q).
+    // Q(I,:) = U1 S1 V1^T (q x pc); M = V1 S1^+ U1^T R_R^T (pc x q); Mt = M^T (q x pc).
     for (int e = tid; e < q * pc; e += nt) {
       const int i = e % q, j = e / q;
-      W1[(int64_t)j * M + i] = QI[(int64_t)j * M + i];
+      W1[(int64_t)j * L + i] = QI[(int64_t)j * L + i];
     }
     __syncthreads();
-    blk_jacobi(W1, M, q, pc, V1, M, sig1, &flag);
+    blk_jacobi(W1, L, q, pc, V1, L, sig1, &flag);
     double smax = 0.0;
     for (int j = tid; j < pc; j += nt) smax = fmax(smax, sig1[j]);
     smax = block_max(smax, red);
-    const double cut = mx * eps64 * smax;
+    const double cut = mx * eps_c * smax;
     // T1(a, c) = sum_{d >= c} W1(d, a) R_R(c, d) / sig1[a]^2   (pc x q)
     for (int e = tid; e < pc * q; e += nt) {
       const int a = e % pc, c = e / pc;
-      double s = 0.0;
+      TC s = 0;
       if (sig1[a] > cut) {
-        for (int d = c; d < q; ++d) s += W1[(int64_t)a * M + d] * RR[(int64_t)d * M + c];
-        s /= sig1[a] * sig1[a];
+        for (int d = c; d < q; ++d) s += W1[(int64_t)a * L + d] * (TC)RR[(int64_t)d * M + c];
+        s /= (TC)(sig1[a] * sig1[a]);
       }
-      T1[(int64_t)c * M + a] = s;
+      T1[(int64_t)c * L + a] = s;
     }
     __syncthreads();
-    // Mt = M^T (q x pc): Mt(c, i) = sum_a V1(i, a) T1(a, c)
     for (int e = tid; e < q * pc; e += nt) {
       const int c = e % q, i = e / q;
-      double s = 0.0;
-      for (int a = 0; a < pc; ++a) s += V1[(int64_t)a * M + i] * T1[(int64_t)c * M + a];
-      Mt[(int64_t)i * M + c] = s;
+      TC s = 0;
+      for (int a = 0; a < pc; ++a) s += V1[(int64_t)a * L + i] * T1[(int64_t)c * L + a];
+      Mt[(int64_t)i * L + c] = s;
     }
     __syncthreads();
-    blk_jacobi(Mt, M, q, pc, V2, M, sig2, &flag);
+    blk_jacobi(Mt, L, q, pc, V2, L, sig2, &flag);
     nsv = pc;
   } else {
-    // Mirror: M = R_C pinv(Z(J,:))^T with Z(J,:) = U2 S2 V2^T (pc x q).
+    // Mirror: Z(J,:) = U2 S2 V2^T (pc x q); M = R_C U2 S2^+ V2^T (pc x q), tall.
     for (int e = tid; e < pc * q; e += nt) {
       const int i = e % pc, j = e / pc;
-      W1[(int64_t)j * M + i] = ZJ[(int64_t)j * M + i];
+      W1[(int64_t)j * L + i] = ZJ[(int64_t)j * L + i];
     }
     __syncthreads();
-    blk_jacobi(W1, M, pc, q, V1, M, sig1, &flag);
+    blk_jacobi(W1, L, pc, q, V1, L, sig1, &flag);
     double smax = 0.0;
     for (int j = tid; j < q; j += nt) smax = fmax(smax, sig1[j]);
     smax = block_max(smax, red);
-    const double cut = mx * eps64 * smax;
+    const double cut = mx * eps_c * smax;
     // T1(i, a) = sum_{c >= i} R_C(i, c) W1(c, a) / sig1[a]^2  (pc x q)
     for (int e = tid; e < pc * q; e += nt) {
       const int i = e % pc, a = e / pc;
-      double s = 0.0;
+      TC s = 0;
       if (sig1[a] > cut) {
-        for (int c = i; c < pc; ++c) s += RC[(int64_t)c * M + i] * W1[(int64_t)a * M + c];
-        s /= sig1[a] * sig1[a];
+        for (int c = i; c < pc; ++c) s += (TC)RC[(int64_t)c * M + i] * W1[(int64_t)a * L + c];
+        s /= (TC)(sig1[a] * sig1[a]);
       }
-      T1[(int64_t)a * M + i] = s;
+      T1[(int64_t)a * L + i] = s;
     }
     __syncthreads();
-    // Mt = M (pc x q): M(i, bb) = sum_a T1(i, a) V1(bb, a)
     for (int e = tid; e < pc * q; e += nt) {
       const int i = e % pc, bb = e / pc;
-      double s = 0.0;
-      for (int a = 0; a < q; ++a) s += T1[(int64_t)a * M + i] * V1[(int64_t)a * M + bb];
-      Mt[(int64_t)bb * M + i] = s;
+      TC s = 0;
+      for (int a = 0; a < q; ++a) s += T1[(int64_t)a * L + i] * V1[(int64_t)a * L + bb];
+      Mt[(int64_t)bb * L + i] = s;
     }
     __syncthreads();
-    blk_jacobi(Mt, M, pc, q, V2, M, sig2, &flag);
+    blk_jacobi(Mt, L, pc, q, V2, L, sig2, &flag);
     nsv = q;
   }
   blk_sort_desc(sig2, nsv, perm);
@@ -335,54 +373,56 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
     for (int t = 0; t < nsv; ++t) r += (sig2[perm[t]] >= cut && sig2[perm[t]] > 0.0) ? 1 : 0;
     if (r < 1) r = 1;
   }
-  // U~ (pc x r) and V~ (q x r): branch 0: U~ = V2, V~ = Mt/sig; branch 1: U~ = Mt/sig, V~ = V2.
-  // Reuse W1 for U~ and V1 for V~ (their previous contents are no longer needed).
-  double* Ut = W1;
-  double* Vt = V1;
+  // U~ (pc x r) -> R3, V~ (q x r) -> R4.  Branch 0: U~ = V2, V~ = Mt/sig; branch 1: U~ = Mt/sig, V~ = V2.
+  TC* Ut = R3;
+  TC* Vt = R4;
   for (int e = tid; e < pc * r; e += nt) {
     const int i = e % pc, t = e / pc;
     const int j = perm[t];
-    const double sv = sig2[j];
-    Ut[(int64_t)t * M + i] = (branch == 0) ? V2[(int64_t)j * M + i] : (sv > 0 ? Mt[(int64_t)j * M + i] / sv : 0.0);
+    const TC sv = (TC)sig2[j];
+    Ut[(int64_t)t * L + i] = (branch == 0) ? V2[(int64_t)j * L + i] : (sv > 0 ? Mt[(int64_t)j * L + i] / sv : (TC)0);
   }
   for (int e = tid; e < q * r; e += nt) {
     const int i = e % q, t = e / q;
     const int j = perm[t];
-    const double sv = sig2[j];
-    Vt[(int64_t)t * M + i] = (branch == 0) ? (sv > 0 ? Mt[(int64_t)j * M + i] / sv : 0.0) : V2[(int64_t)j * M + i];
+    const TC sv = (TC)sig2[j];
+    Vt[(int64_t)t * L + i] = (branch == 0) ? (sv > 0 ? Mt[(int64_t)j * L + i] / sv : (TC)0) : V2[(int64_t)j * L + i];
   }
   double* sig_out = b.sig + (int64_t)slot * 2 * M + (int64_t)parity * M;
   for (int t = tid; t < r; t += nt) sig_out[t] = sig2[perm[t]];
   __syncthreads();
-  // Bf0 = P3_0 U~ (pc x r), Bf1 = P3_1 V~ (q x r)
+  // Bf0 = P3_0 U~ (pc x r), Bf1 = P3_1 V~ (q x r); U_k(I,:) = Q(I,:) U~ -> R5, V_k(J,:) = Z(J,:) V~ -> R2.
   double* B0 = b.Bf.at(slot, 0);
   double* B1 = b.Bf.at(slot, 1);
+  TC* UI = R5;
+  TC* VJ = R2;
   for (int e = tid; e < pc * r; e += nt) {
     const int i = e % pc, t = e / pc;
-    double s = 0.0;
-    for (int d = i; d < pc; ++d) s += P0[(int64_t)d * M + i] * Ut[(int64_t)t * M + d];
-    B0[(int64_t)t * M + i] = s;
+    TC s = 0;
+    for (int d = i; d < pc; ++d) s += (TC)P0[(int64_t)d * M + i] * Ut[(int64_t)t * L + d];
+    B0[(int64_t)t * M + i] = (double)s;
   }
   for (int e = tid; e < q * r; e += nt) {
     const int i = e % q, t = e / q;
-    double s = 0.0;
-    for (int d = i; d < q; ++d) s += P1[(int64_t)d * M + i] * Vt[(int64_t)t * M + d];
-    B1[(int64_t)t * M + i] = s;
+    TC s = 0;
+    for (int d = i; d < q; ++d) s += (TC)P1[(int64_t)d * M + i] * Vt[(int64_t)t * L + d];
+    B1[(int64_t)t * M + i] = (double)s;
   }
-  // U_k(I,:) = Q(I,:) U~ (q x r), V_k(J,:) = Z(J,:) V~ (pc x r)
   for (int e = tid; e < q * r; e += nt) {
     const int a = e % q, t = e / q;
-    double s = 0.0;
-    for (int c = 0; c < pc; ++c) s += QI[(int64_t)c * M + a] * Ut[(int64_t)t * M + c];
-    UI[(int64_t)t * M + a] = s;
+    TC s = 0;
+    for (int c = 0; c < pc; ++c) s += QI[(int64_t)c * L + a] * Ut[(int64_t)t * L + c];
+    UI[(int64_t)t * L + a] = s;
   }
   for (int e = tid; e < pc * r; e += nt) {
     const int a = e % pc, t = e / pc;
-    double s = 0.0;
-    for (int c = 0; c < q; ++c) s += ZJ[(int64_t)c * M + a] * Vt[(int64_t)t * M + c];
-    VJ[(int64_t)t * M + a] = s;
+    TC s = 0;
+    for (int c = 0; c < q; ++c) s += ZJ[(int64_t)c * L + a] * Vt[(int64_t)t * L + c];
+    VJ[(int64_t)t * L + a] = s;
   }
   __syncthreads();
+  TC* WK = R0;  // Q(I,:) no longer needed
+  TC* WE = R1;  // Z(J,:) no longer needed
 
   // Redundancy removal: keep I_l iff |R_R(l,l)| >= tau max|diag R_R|, J_l likewise with R_C.
   double mR = 0.0, mC = 0.0;
@@ -390,7 +430,6 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
   for (int l = tid; l < pc; l += nt) mC = fmax(mC, fabs(RC[(int64_t)l * M + l]));
   mR = block_max(mR, red);
   mC = block_max(mC, red);
-  int qn = 0, pn = 0;
   for (int l = tid; l < q; l += nt) keep[l] = (mR > 0.0 && fabs(RR[(int64_t)l * M + l]) >= p.redundancy * mR) ? 1 : 0;
   __syncthreads();
   if (tid == 0) {
@@ -405,17 +444,15 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
     flag = w;
   }
   __syncthreads();
-  qn = flag;
-  // compact rows of UI into WK (qn x r), then back
+  const int qn = flag;
   for (int e = tid; e < qn * r; e += nt) {
     const int a = e % qn, t = e / qn;
-    WK[(int64_t)t * M + a] = UI[(int64_t)t * M + perm[a]];
+    WK[(int64_t)t * L + a] = UI[(int64_t)t * L + perm[a]];
   }
   __syncthreads();
-  for (int e = tid; e < qn * r; e += nt) {
-    const int a = e % qn, t = e / qn;
-    UI[(int64_t)t * M + a] = WK[(int64_t)t * M + a];
-  }
+  __shared__ double vec_d[2 * kMaxM];
+  TC* vec = reinterpret_cast<TC*>(vec_d);  // 2 k values, k <= kMaxM
+  const double e1 = blk_inv_smin(WK, L, qn, r, WE, R3, L, vec, &flag);
   for (int l = tid; l < pc; l += nt) keep[l] = (mC > 0.0 && fabs(RC[(int64_t)l * M + l]) >= p.redundancy * mC) ? 1 : 0;
   __syncthreads();
   if (tid == 0) {
@@ -430,30 +467,25 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
     flag = w;
   }
   __syncthreads();
-  pn = flag;
+  const int pn = flag;
   for (int e = tid; e < pn * r; e += nt) {
     const int a = e % pn, t = e / pn;
-    WK[(int64_t)t * M + a] = VJ[(int64_t)t * M + perm[a]];
+    WK[(int64_t)t * L + a] = VJ[(int64_t)t * L + perm[a]];
   }
   __syncthreads();
-  for (int e = tid; e < pn * r; e += nt) {
-    const int a = e % pn, t = e / pn;
-    VJ[(int64_t)t * M + a] = WK[(int64_t)t * M + a];
-  }
-  __syncthreads();
-  // eta_1 = 1/sigma_min(U_k(I,:)), eta_2 = 1/sigma_min(V_k(J,:)), with the reduced sets.
-  const double sm1 = blk_smin(UI, M, qn, r, WK, M, sig1, &flag);
-  const double sm2 = blk_smin(VJ, M, pn, r, WK, M, sig1, &flag);
+  // eta_1 = ||U_k(I,:)^+||_2, eta_2 = ||V_k(J,:)^+||_2 with the reduced sets.
+  const double e2 = blk_inv_smin(WK, L, pn, r, WE, R3, L, vec, &flag);
   double snorm2 = 0.0;
   for (int t = tid; t < r; t += nt) snorm2 += sig_out[t] * sig_out[t];
   snorm2 = block_sum(snorm2, red);
   if (tid == 0) {
     const double snorm = sqrt(snorm2);
-    const double e1 = (sm1 > 0.0) ? 1.0 / sm1 : INFINITY;
-    const double e2 = (sm2 > 0.0) ? 1.0 / sm2 : INFINITY;
     const double smin = snorm > 0.0 ? sig_out[r - 1] / snorm : 0.0;
     const double f = fmin(e1 * (1.0 + e2), e2 * (1.0 + e1));
     stp->eta_smin = snorm > 0.0 ? f * smin : 0.0;
+    // Mixed-precision inner solves: singular values at the data's noise floor
+    // cannot be resolved further, so the index set is as rich as the data allow.
+    if (p.noise_floor_stop && sig_out[r - 1] <= 16.0 * (double)mx * p.eps_data * s1) stp->eta_smin = 0.0;
     stp->snorm = snorm;
     if (b.acct)
       acct_iteration(b.acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, pc, q, r, stp->r_prev, stp->rf, p.g.NB,
@@ -725,13 +757,14 @@ __global__ void k_count_active(const SolveState* st, int nslots, int32_t* out) {
 
 template <typename T>
 cudaError_t launch_chol(const CoreParams& p, const CoreBufs<T>& b, int sel, int pass, cudaStream_t s) {
-  k_chol<T><<<p.g.nslots * 2, CT, 0, s>>>(p, b, sel, pass);
+  k_chol<T><<<p.g.nslots * 2, CT, kCholSmemBytes, s>>>(p, b, sel, pass);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_core(const CoreParams& p, const CoreBufs<T>& b, int parity, cudaStream_t s) {
-  k_core<T><<<p.g.nslots, CT, 0, s>>>(p, b, parity);
+  auto kern = k_core<T>;
+  kern<<<p.g.nslots, CT, kCoreSmemBytes, s>>>(p, b, parity);
   return cudaGetLastError();
 }
 
@@ -742,8 +775,6 @@ cudaError_t launch_select(const CoreParams& p, const CoreBufs<T>& b, int sel_c, 
   while (len < total) len <<= 1;
   const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
   auto kern = k_select<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   kern<<<p.g.nslots * 2, 512, smem, s>>>(p, b, sel_c, len);
   return cudaGetLastError();
 }
@@ -766,6 +797,22 @@ cudaError_t launch_setup(const CoreParams& p, const ProblemDev* prob, T* w, int 
                          cudaStream_t s) {
   k_setup<T><<<p.g.nslots, 64, 0, s>>>(p, prob, w, wstride, nactive, acct);
   return cudaGetLastError();
+}
+
+cudaError_t core_configure() {
+  cudaError_t e = cudaSuccess;
+  const int sel_bytes = 16384 * (int)(sizeof(double) + sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
+  return e;
 }
 
 cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s) {

@@ -38,6 +38,7 @@ struct CoreParams {
   double redundancy;   // |diag R| threshold relative to max |diag R| (paper: 1e-12)
   uint64_t seed;
   int selector;        // lrp_selector
+  int noise_floor_stop;  // 1: the eta S_min term counts as met once S_min is at the data's noise floor
   int cand_blocks;     // leverage candidate blocks per side
   int cand_per_block;
 };
@@ -90,6 +91,9 @@ cudaError_t launch_finalize_impl(const CoreParams& p, const CoreBufs<T>& b, cons
 template <typename T>
 cudaError_t launch_setup(const CoreParams& p, const ProblemDev* prob, T* w, int wstride, int nslots_active,
                          double* acct, cudaStream_t s);
+
+// Raises the dynamic shared-memory limits of the per-problem kernels (once per process).
+cudaError_t core_configure();
 
 // Eigenvalues lambda_k = 4 sin^2(pi k / (2(n+1))), k = 1..n, in FP64 and FP32.
 cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s);

@@ -10,20 +10,35 @@ namespace lrp {
 
 constexpr int kJacobiSweeps = 40;
 
+template <typename TC>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double value = 2.220446049250313e-16;
+};
+template <>
+struct Eps<float> {
+  static constexpr double value = 1.1920928955078125e-07;
+};
+
 // One-sided Jacobi SVD of the mr x nc matrix A (col-major, lda; mr >= nc is the
-// intended use).  On exit the columns of A are U*Sigma (mutually orthogonal),
-// sig[j] = ||A(:,j)|| and, if V != nullptr, A_in = A_out V^T with V orthogonal.
-__device__ inline void blk_jacobi(double* A, int lda, int mr, int nc, double* V, int ldv, double* sig, int* flag) {
+// intended use) in arithmetic TC.  On exit the columns of A are U*Sigma
+// (mutually orthogonal), sig[j] = ||A(:,j)|| and, if V != nullptr,
+// A_in = A_out V^T with V orthogonal.
+template <typename TC>
+__device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv, double* sig, int* flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (V) {
     for (int e = tid; e < nc * nc; e += blockDim.x) {
       const int i = e % nc, j = e / nc;
-      V[(int64_t)j * ldv + i] = (i == j) ? 1.0 : 0.0;
+      V[(int64_t)j * ldv + i] = (i == j) ? (TC)1 : (TC)0;
     }
   }
   __syncthreads();
   const int ne = nc + (nc & 1);
-  const double tol = 1e-15;
+  // Rotate while |a_i . a_j| > tol ||a_i|| ||a_j||; below mr * eps the computed
+  // inner products are rounding noise.
+  const TC tol = (TC)((double)(mr > 1 ? mr : 1) * Eps<TC>::value);
   for (int sweep = 0; sweep < kJacobiSweeps && ne >= 2; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
@@ -43,11 +58,11 @@ __device__ inline void blk_jacobi(double* A, int lda, int mr, int nc, double* V,
           a = b;
           b = t;
         }
-        double* ca = A + (int64_t)a * lda;
-        double* cb = A + (int64_t)b * lda;
-        double alpha = 0.0, beta = 0.0, gamma = 0.0;
+        TC* ca = A + (int64_t)a * lda;
+        TC* cb = A + (int64_t)b * lda;
+        TC alpha = 0, beta = 0, gamma = 0;
         for (int i = lane; i < mr; i += 32) {
-          const double x = ca[i], y = cb[i];
+          const TC x = ca[i], y = cb[i];
           alpha = fma(x, x, alpha);
           beta = fma(y, y, beta);
           gamma = fma(x, y, gamma);
@@ -55,21 +70,21 @@ __device__ inline void blk_jacobi(double* A, int lda, int mr, int nc, double* V,
         alpha = warp_sum(alpha);
         beta = warp_sum(beta);
         gamma = warp_sum(gamma);
-        if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
-        const double zeta = (beta - alpha) / (2.0 * gamma);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
+        if (gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+        const TC zeta = (beta - alpha) / ((TC)2 * gamma);
+        const TC t = copysign((TC)1, zeta) / (fabs(zeta) + sqrt((TC)1 + zeta * zeta));
+        const TC c = (TC)1 / sqrt((TC)1 + t * t);
+        const TC s = c * t;
         for (int i = lane; i < mr; i += 32) {
-          const double x = ca[i], y = cb[i];
+          const TC x = ca[i], y = cb[i];
           ca[i] = c * x - s * y;
           cb[i] = s * x + c * y;
         }
         if (V) {
-          double* va = V + (int64_t)a * ldv;
-          double* vb = V + (int64_t)b * ldv;
+          TC* va = V + (int64_t)a * ldv;
+          TC* vb = V + (int64_t)b * ldv;
           for (int i = lane; i < nc; i += 32) {
-            const double x = va[i], y = vb[i];
+            const TC x = va[i], y = vb[i];
             va[i] = c * x - s * y;
             vb[i] = s * x + c * y;
           }
@@ -83,11 +98,11 @@ __device__ inline void blk_jacobi(double* A, int lda, int mr, int nc, double* V,
     if (!rotated) break;
   }
   for (int j = warp; j < nc; j += nwarps) {
-    const double* cj = A + (int64_t)j * lda;
-    double s = 0.0;
+    const TC* cj = A + (int64_t)j * lda;
+    TC s = 0;
     for (int i = lane; i < mr; i += 32) s = fma(cj[i], cj[i], s);
     s = warp_sum(s);
-    if (lane == 0) sig[j] = sqrt(s);
+    if (lane == 0) sig[j] = sqrt((double)s);
   }
   __syncthreads();
 }
@@ -106,21 +121,124 @@ __device__ inline void blk_sort_desc(const double* v, int n, int* perm) {
   __syncthreads();
 }
 
-// Smallest singular value of the mr x nc matrix (copied to work first).
-__device__ inline double blk_smin(const double* src, int lds, int mr, int nc, double* work, int ldw, double* sig, int* flag) {
-  if (nc == 0) return 0.0;
-  if (mr < nc) return 0.0;
+// Smallest nonzero-rank singular value of the mr x nc matrix: sigma_min(A) for a
+// tall A, and the smallest of the mr singular values of a wide A, so that
+// 1/result = ||A^+||_2 for a full-rank A of either shape.
+template <typename TC>
+__device__ inline double blk_smin(const TC* src, int lds, int mr, int nc, TC* work, int ldw, double* sig, int* flag) {
+  if (nc == 0 || mr == 0) return 0.0;
+  const bool wide = mr < nc;
+  const int rows = wide ? nc : mr, cols = wide ? mr : nc;
   for (int e = threadIdx.x; e < mr * nc; e += blockDim.x) {
     const int i = e % mr, j = e / mr;
-    work[(int64_t)j * ldw + i] = src[(int64_t)j * lds + i];
+    const TC v = src[(int64_t)j * lds + i];
+    if (wide)
+      work[(int64_t)i * ldw + j] = v;
+    else
+      work[(int64_t)j * ldw + i] = v;
   }
   __syncthreads();
-  blk_jacobi(work, ldw, mr, nc, nullptr, 0, sig, flag);
+  blk_jacobi<TC>(work, ldw, rows, cols, nullptr, 0, sig, flag);
   __shared__ double red[32];
   double mn = 1e308;
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) mn = fmin(mn, sig[j]);
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) mn = fmin(mn, sig[j]);
   mn = -block_max(-mn, red);
   return mn;
+}
+
+// ||A^+||_2 for the mr x nc matrix A (1 / its smallest nonzero-rank singular
+// value), from the Gram of the smaller side: G = A^T A (mr >= nc) or A A^T,
+// Cholesky G = R^T R, G^{-1} = R^{-1} R^{-T}, and power iteration on G^{-1}
+// (lambda_max(G^{-1}) = 1 / sigma_min^2).  Returns +inf when G is numerically
+// singular.  G, Ri are k x k work areas (k = min(mr, nc)), vec holds 2k values.
+template <typename TC>
+__device__ inline double blk_inv_smin(const TC* A, int lda, int mr, int nc, TC* G, TC* Ri, int ldg, TC* vec,
+                                      int* flag) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool tall = mr >= nc;
+  const int k = tall ? nc : mr, len = tall ? mr : nc;
+  __shared__ double red_i[32];
+  if (k == 0) return INFINITY;
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e % k, j = e / k;
+    if (i > j) continue;
+    TC s = 0;
+    for (int l = 0; l < len; ++l) {
+      const TC x = tall ? A[(int64_t)i * lda + l] : A[(int64_t)l * lda + i];
+      const TC y = tall ? A[(int64_t)j * lda + l] : A[(int64_t)l * lda + j];
+      s = fma(x, y, s);
+    }
+    G[(int64_t)j * ldg + i] = s;
+  }
+  if (tid == 0) *flag = 0;
+  __syncthreads();
+  // Cholesky (upper R in the upper triangle of G).
+  for (int j = 0; j < k; ++j) {
+    const TC d = G[(int64_t)j * ldg + j];
+    const bool bad = !(d > (TC)0);
+    if (bad) {
+      if (tid == 0) *flag = 1;
+      break;
+    }
+    const TC rjj = sqrt(d);
+    __syncthreads();
+    for (int l = j + 1 + tid; l < k; l += nt) G[(int64_t)l * ldg + j] /= rjj;
+    if (tid == 0) G[(int64_t)j * ldg + j] = rjj;
+    __syncthreads();
+    const int t = k - j - 1;
+    for (int e = tid; e < t * t; e += nt) {
+      const int a = e % t, b = e / t;
+      if (a > b) continue;
+      G[(int64_t)(j + 1 + b) * ldg + (j + 1 + a)] -= G[(int64_t)(j + 1 + a) * ldg + j] * G[(int64_t)(j + 1 + b) * ldg + j];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (*flag) return INFINITY;
+  // Ri = R^{-1} (upper), column l by back substitution.
+  for (int l = tid; l < k; l += nt) {
+    for (int i = k - 1; i > l; --i) Ri[(int64_t)l * ldg + i] = (TC)0;
+    for (int i = l; i >= 0; --i) {
+      TC s = (i == l) ? (TC)1 : (TC)0;
+      for (int c = i + 1; c <= l; ++c) s -= G[(int64_t)c * ldg + i] * Ri[(int64_t)l * ldg + c];
+      Ri[(int64_t)l * ldg + i] = s / G[(int64_t)i * ldg + i];
+    }
+  }
+  __syncthreads();
+  // Power iteration on G^{-1} = Ri Ri^T: x <- Ri (Ri^T x).
+  TC* x = vec;
+  TC* y = vec + k;
+  for (int i = tid; i < k; i += nt) x[i] = (TC)1 / sqrt((TC)k) * (TC)(1 + (i & 1));
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < 30; ++it) {
+    for (int i = tid; i < k; i += nt) {  // y = Ri^T x
+      TC s = 0;
+      for (int c = 0; c <= i; ++c) s = fma(Ri[(int64_t)i * ldg + c], x[c], s);
+      y[i] = s;
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    for (int i = tid; i < k; i += nt) {  // x_new = Ri y
+      TC s = 0;
+      for (int c = i; c < k; ++c) s = fma(Ri[(int64_t)c * ldg + i], y[c], s);
+      nrm += (double)s * (double)s;
+    }
+    nrm = block_sum(nrm, red_i);
+    const double prev = lam;
+    double xx = 0.0;
+    for (int i = tid; i < k; i += nt) xx += (double)x[i] * (double)x[i];
+    xx = block_sum(xx, red_i);
+    lam = sqrt(nrm / xx);  // ||G^{-1} x|| / ||x|| -> lambda_max(G^{-1})
+    for (int i = tid; i < k; i += nt) {
+      TC s = 0;
+      for (int c = i; c < k; ++c) s = fma(Ri[(int64_t)c * ldg + i], y[c], s);
+      x[i] = s / (TC)sqrt(nrm);
+    }
+    __syncthreads();
+    if (it > 3 && fabs(lam - prev) <= 1e-3 * lam) break;
+  }
+  return sqrt(lam);
 }
 
 }  // namespace lrp

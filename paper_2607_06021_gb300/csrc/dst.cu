@@ -155,13 +155,24 @@ cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols,
   const int logN = ilog2(N);
   const size_t smem = (size_t)N * sizeof(cplx<TC>);
   auto kern = k_dst1_smem<TIn, TOut, TC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int threads = N >= 2048 ? 512 : (N >= 512 ? 256 : 128);
   dim3 grid(max_cols, nslots, nmats);
   if (max_cols <= 0 || nslots <= 0) return cudaSuccess;
   kern<<<grid, threads, smem, st>>>((int)n, logN, job, (const cplx<TC>*)tw);
   return cudaGetLastError();
+}
+
+cudaError_t dst_configure() {
+  const int bytes = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_dst1_smem<double, double, double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dst1_smem<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dst1_smem<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dst1_smem<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 template cudaError_t dst1_launch<double, double, double>(int64_t, const DstBatch<double, double>&, int, int, int,

@@ -90,6 +90,10 @@ __global__ void k_assemble_residual(RefineArgs a) {
 // factors Bf_s = P3_s * (left / right singular vectors) so that the recompressed
 // product is (Q2_0 Bf_0) diag(sigma) (Q2_1 Bf_1)^T.  mode 0 keeps the tail-rule
 // rank at rel_tol (capped at rcap); mode 1 keeps every numerically nonzero value.
+// K is always formed in FP64 (the cancellation between the stacked blocks happens
+// there); its SVD runs in TC: FP32 suffices for the residual, whose correction is
+// an FP32 solve, and FP64 keeps the final sum exact to working precision.
+template <typename TC>
 __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, double rel_tol, int rcap) {
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
@@ -102,9 +106,9 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
   const double* P0 = a.P.at(slot, 0);
   const double* P1 = a.P.at(slot, 1);
   const double* d = a.dvec + (int64_t)slot * M;
-  double* base = a.scratch + (int64_t)slot * a.scratch_stride;
-  double* K = base;           // m x m
-  double* V = base + MM;      // m x m
+  TC* base = reinterpret_cast<TC*>(a.scratch + (int64_t)slot * a.scratch_stride);
+  TC* K = base;           // m x m
+  TC* V = base + MM;      // m x m
   double* B0 = a.Bf.at(slot, 0);
   double* B1 = a.Bf.at(slot, 1);
   double* sig_out = a.sig_out + (int64_t)slot * a.sig_out_stride;
@@ -117,10 +121,10 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     const int i = e % m, j = e / m;
     double s = 0.0;
     for (int l = max(i, j); l < m; ++l) s += R0[(int64_t)l * M + i] * d[l] * R1[(int64_t)l * M + j];
-    K[(int64_t)j * M + i] = s;
+    K[(int64_t)j * M + i] = (TC)s;
   }
   __syncthreads();
-  blk_jacobi(K, M, m, m, V, M, sig, &flag);
+  blk_jacobi<TC>(K, M, m, m, V, M, sig, &flag);
   blk_sort_desc(sig, m, perm);
   int r = 0;
   if (tid == 0) {
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
       }
     } else {
       r = 0;
-      for (int t = 0; t < m; ++t) r += (sig[perm[t]] > (double)m * 2.220446049250313e-16 * s1) ? 1 : 0;
+      for (int t = 0; t < m; ++t) r += (sig[perm[t]] > (double)m * Eps<TC>::value * s1) ? 1 : 0;
     }
     if (r > rcap) r = rcap;
     if (r < 1) r = 1;
@@ -152,8 +156,8 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     double s0 = 0.0, s1 = 0.0;
     const double sv = sig[j];
     for (int c = i; c < m; ++c) {
-      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? K[(int64_t)j * M + c] / sv : 0.0);
-      s1 += P1[(int64_t)c * M + i] * V[(int64_t)j * M + c];
+      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? (double)K[(int64_t)j * M + c] / sv : 0.0);
+      s1 += P1[(int64_t)c * M + i] * (double)V[(int64_t)j * M + c];
     }
     B0[(int64_t)t * M + i] = s0;
     B1[(int64_t)t * M + i] = s1;
@@ -268,7 +272,10 @@ cudaError_t launch_assemble_residual(const RefineArgs& a, int nslots, cudaStream
   return cudaGetLastError();
 }
 cudaError_t launch_recompress(const RefineArgs& a, int nslots, int mode, double rel_tol, int rcap, cudaStream_t s) {
-  k_recompress<<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
+  if (mode == 0)
+    k_recompress<float><<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
+  else
+    k_recompress<double><<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
   return cudaGetLastError();
 }
 cudaError_t launch_setup_correction(const RefineArgs& a, int nslots, cudaStream_t s) {

@@ -91,6 +91,16 @@ lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc
   return LRP_OK;
 }
 
+template <typename T>
+void Workspace<T>::release_graphs() {
+  for (auto& g : graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  graph_count = -1;
+}
+
 template struct Workspace<double>;
 template struct Workspace<float>;
 
@@ -212,6 +222,20 @@ void DeviceArena::release() {
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Kernel attributes (dynamic shared-memory limits) are set once per device,
+// never during a stream capture.
+static lrp_status ensure_configured(int device) {
+  static std::mutex cfg_mu;
+  static uint64_t configured = 0;
+  std::lock_guard<std::mutex> lock(cfg_mu);
+  if (device >= 0 && device < 64 && (configured & (1ull << device))) return LRP_OK;
+  cudaError_t e = dst_configure();
+  if (e == cudaSuccess) e = core_configure();
+  if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
+  if (device >= 0 && device < 64) configured |= (1ull << device);
+  return LRP_OK;
+}
+
 extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   if (!o) return set_error(LRP_EINVAL, "opts is NULL");
   o->precision = LRP_FP64;
@@ -248,7 +272,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
   p->n = n;
   p->tol = tol;
-  p->mixed_inner_tol = 3e-5;
+  p->mixed_inner_tol = 1e-4;
   p->mixed_redundancy = 1e-6;
   p->mixed_residual_tol = 1e-7;
   p->r_max = max_rank;
@@ -280,6 +304,13 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     delete p;
     return set_error(LRP_ECUDA, "no CUDA device");
   }
+  {
+    lrp_status cs_ = ensure_configured(p->device);
+    if (cs_ != LRP_OK) {
+      delete p;
+      return cs_;
+    }
+  }
   lrp_status s = LRP_OK;
   cudaStream_t st0 = nullptr;
   p->st = p->arena.get<SolveState>((size_t)d.B);
@@ -307,6 +338,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->prob_host, sizeof(ProblemDev) * d.B);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_ptrs, (sizeof(void*) * 2 + sizeof(int64_t) * 2) * 2 * d.B);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->active_host, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) s = set_error(LRP_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
   }
@@ -328,6 +360,9 @@ extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
   if (p->host_ptrs) cudaFreeHost(p->host_ptrs);
   if (p->active_host) cudaFreeHost(p->active_host);
   p->stats.release();
+  p->w64.release_graphs();
+  p->w32.release_graphs();
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
   return LRP_OK;
 }
@@ -341,6 +376,10 @@ extern "C" lrp_status lrp_plan_workspace_bytes(lrp_plan_t p, size_t* bytes) {
 // ------------------------------------------------------------------- solve
 
 namespace lrp {
+
+// Kernels launched by one tall GEMM / Gram call (narrow and wide variants).
+static inline int gemm_kernels(const lrp_plan_s* p) { return p->dims.M > 32 ? 2 : 1; }
+static inline int gram_kernels(const lrp_plan_s* p) { return p->dims.M > 64 ? 2 : 1; }
 
 template <typename T>
 static CoreBufs<T> make_core_bufs(lrp_plan_s* p, Workspace<T>& w) {
@@ -375,8 +414,8 @@ static Strided<const T> cs(const T* base, int64_t side, int64_t slot) {
 // Gram -> chol(1) -> Q2 = Q1 P, Gram -> chol(2).  Leaves P3 in w.P, Q2 in w.Q2.
 template <typename T>
 static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T> x, int sx, Strided<const T> y,
-                              int sy, double* part, Strided<double> G, bool sym, cudaStream_t s) {
-  LRP_LAUNCH(p, LRP_K_GRAM, 1, s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s));
+                              int sy, double* part, Strided<double> G, bool sym, cudaStream_t s, bool acc64 = true) {
+  LRP_LAUNCH(p, LRP_K_GRAM, gram_kernels(p), s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s, acc64));
   LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, sx, sy, part, G, sym, s));
   return LRP_OK;
 }
@@ -396,16 +435,20 @@ static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, con
                            G, true, s)))
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 0, s));
-  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+  LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs(X, side_stride, slot_stride), sel, P, sel, Strided<T>{w.Q1, nm, 2 * nm},
                                none, 0, s));
-  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), sel, cs<T>(w.Q1, nm, 2 * nm), sel, w.part, G, true, s)))
+  // Later passes see a well-conditioned basis: FP32 data keep an FP32 Gram.
+  const bool acc64 = sizeof(T) == 8;
+  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), sel, cs<T>(w.Q1, nm, 2 * nm), sel, w.part, G, true, s,
+                           acc64)))
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 1, s));
-  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+  LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs<T>(w.Q1, nm, 2 * nm), sel, P, sel, Strided<T>{w.Q2, nm, 2 * nm}, none, 0,
                                s));
-  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q2, nm, 2 * nm), sel, cs<T>(w.Q2, nm, 2 * nm), sel, w.part, G, true, s)))
+  if ((st = gram_reduce<T>(p, g, cs<T>(w.Q2, nm, 2 * nm), sel, cs<T>(w.Q2, nm, 2 * nm), sel, w.part, G, true, s,
+                           acc64)))
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 2, s));
   return LRP_OK;
@@ -424,6 +467,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   cp.shift_rel = 1e-15;
   cp.drop_rel = 64.0 * 2.220446049250313e-16;
   cp.redundancy = redundancy;
+  cp.noise_floor_stop = 0;
   cp.seed = p->opts.seed;
   cp.selector = p->opts.selector;
   cp.cand_blocks = d.cand_blocks;
@@ -478,6 +522,47 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
 
 // Cross-DEIM (Algorithm Cross-DEIM) on the transformed right-hand side held in
 // w.Fh / w.w: initial bases orth(Fh), then iterations until every slot stops.
+// Runs `body` directly, or (when graphs are enabled and timing is off) replays
+// a CUDA graph captured from it on first use for this batch count.
+template <typename T, typename Body>
+static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int kind, cudaStream_t s, Body body) {
+  if (!p->use_graphs || p->stats.timing || !p->cap_stream) return body(s);
+  if (w.graph_count != count) {
+    w.release_graphs();
+    w.graph_count = count;
+  }
+  if (!w.graphs[kind]) {
+    int64_t before[LRP_K_COUNT];
+    for (int c = 0; c < LRP_K_COUNT; ++c) before[c] = p->stats.launches[c];
+    // Captured on the plan's own stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's.
+    LRP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    lrp_status st = body(p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (st != LRP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&w.graphs[kind], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      w.graphs[kind] = nullptr;
+      return set_error(LRP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    for (int c = 0; c < LRP_K_COUNT; ++c) {
+      w.graph_launches[kind][c] = p->stats.launches[c] - before[c];
+      p->stats.launches[c] = before[c];
+    }
+  }
+  LRP_CUDA(cudaGraphLaunch(w.graphs[kind], s));
+  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += w.graph_launches[kind][c];
+  return LRP_OK;
+}
+
+// Cross-DEIM (Algorithm Cross-DEIM) on the transformed right-hand side held in
+// w.Fh / w.w: initial bases orth(Fh), then iterations until every slot stops.
 template <typename T>
 static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, cudaStream_t s) {
   const PlanDims& d = p->dims;
@@ -488,16 +573,19 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   CoreBufs<T> cb = make_core_bufs<T>(p, w);
   const Strided<const T> none{nullptr, 0, 0};
   // U_{-1} = orth(Uhat_f), V_{-1} = orth(Vhat_f) and their leverage candidates.
-  {
+  auto init = [&](cudaStream_t s) -> lrp_status {
     lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.Fh, fm, 2 * fm, kDimRF, s);
     if (st) return st;
-  }
-  LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
-             launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
-                               kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
-  LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-             launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimRF, w.cand_score, w.cand_idx,
-                                d.cand_blocks, d.cand_per_block, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+               launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
+                                 kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
+    LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
+               launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimRF, w.cand_score, w.cand_idx,
+                                  d.cand_blocks, d.cand_per_block, s));
+    return LRP_OK;
+  };
+  lrp_status st0 = run_captured<T>(p, w, count, 3, s, init);
+  if (st0) return st0;
   Strided<double> Gx{w.X, MM, 2 * MM};
   Strided<double> Ge{w.GE, MM, 2 * MM};
   CrossArgs<T> ca;
@@ -509,36 +597,40 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   ca.A = {w.A, nm, 2 * nm};
   for (int k = 0; k < p->opts.max_iter; ++k) {
     const int par = k & 1;
-    LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimRF : kDimR, s));
-    LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(g, p->st, ca, s));
-    {
+    auto iteration = [&](cudaStream_t s) -> lrp_status {
+      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimRF : kDimR, s));
+      LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(g, p->st, ca, s));
       lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.A, nm, 2 * nm, kDimOther, s);
       if (st) return st;
-    }
-    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cp, cb, par, s));
-    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
-               launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
-                                 Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
-                                 none, 0, s));
-    LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-               launch_leverage<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR, w.cand_score, w.cand_idx,
-                                  d.cand_blocks, d.cand_per_block, s));
-    if (k > 0) {
-      // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
-      lrp_status st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm),
-                                     kDimRPrev, w.part, Gx, false, s);
-      if (st) return st;
-      LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
-                 launch_gemm_nn<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
-                                   Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev, Strided<T>{w.Q1, nm, 2 * nm},
-                                   cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
-      st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part, Ge,
-                          true, s);
-      if (st) return st;
-    }
-    LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cp, cb, par, s));
-    if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
+      LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cp, cb, par, s));
+      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+                 launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
+                                   Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
+                                   none, 0, s));
+      LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
+                 launch_leverage<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR, w.cand_score, w.cand_idx,
+                                    d.cand_blocks, d.cand_per_block, s));
+      if (k > 0) {
+        // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
+        st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
+                            w.part, Gx, false, s, sizeof(T) == 8);
+        if (st) return st;
+        LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+                   launch_gemm_nn<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
+                                     Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
+                                     Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
+        st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part,
+                            Ge, true, s, sizeof(T) == 8);
+        if (st) return st;
+      }
+      LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cp, cb, par, s));
       LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, s));
+      return LRP_OK;
+    };
+    const int kind = (k == 0) ? 0 : ((k & 1) ? 1 : 2);
+    lrp_status st = run_captured<T>(p, w, count, kind, s, iteration);
+    if (st) return st;
+    if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
       LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       LRP_CUDA(cudaStreamSynchronize(s));
       if (*p->active_host == 0) break;
@@ -623,6 +715,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   const double eps32 = 1.1920928955078125e-07;
   const double tol_in = p->tol > p->mixed_inner_tol ? p->tol : p->mixed_inner_tol;
   CoreParams c32 = make_core_params<float>(p, count, tol_in, eps32, p->mixed_redundancy);
+  c32.noise_floor_stop = 1;
   CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
   RefineArgs ra = make_refine_args(p);
@@ -634,26 +727,26 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
   for (int step = 0; step < p->opts.refine_steps; ++step) {
     // Residual of the trial solution, recompressed in FP64.
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_prepare_refine(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_assemble_residual(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(ra, count, s));
     if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
-    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M, s));
-    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
                launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
                                       Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                       Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
     // FP32 correction solve on the residual (already in transformed variables).
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_setup_correction(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s,
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_setup_correction(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s,
                (launch_convert<double, float>(d.n, d.ld, count, p->st, cs<double>(p->w64.Q1, nm, 2 * nm),
                                               Strided<float>{p->w32.Fh, fm32, 2 * fm32}, kDimRF, s)));
     if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
     // What1 = What0 + dWhat, recompressed in FP64.
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_prepare_sum(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_assemble_sum(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(ra, count, s));
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(ra, count, s));
     if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
-    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
-    LRP_LAUNCH(p, LRP_K_GEMM, 1, s,
+    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
+    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
                launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
                                       Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                       Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
@@ -746,6 +839,10 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
   static Cache cache[8];
   int dev = 0;
   LRP_CUDA(cudaGetDevice(&dev));
+  {
+    lrp_status cs_ = ensure_configured(dev);
+    if (cs_ != LRP_OK) return cs_;
+  }
   Cache* c = nullptr;
   for (auto& e : cache)
     if (e.n == n && e.dev == dev) c = &e;

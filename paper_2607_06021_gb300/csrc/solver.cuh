@@ -78,6 +78,13 @@ struct Workspace {
   int64_t* fwd_ldi = nullptr;
   int64_t* fwd_ldo = nullptr;
   int rf_cap = 0;  // columns of Fh (and entries of w) per slot and side
+  // Captured CUDA graphs of one Cross-DEIM iteration: [0] the first iteration,
+  // [1] odd iterations, [2] even iterations >= 2, [3] the initial bases; valid for
+  // graph_count problems (grids depend on the batch count).
+  int graph_count = -1;
+  cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t graph_launches[4][LRP_K_COUNT] = {};
+  void release_graphs();
   lrp_status allocate(const PlanDims& d, DeviceArena& arena, int rf_cap);
 };
 
@@ -119,7 +126,9 @@ struct lrp_plan_s {
   double* acct = nullptr;                // [B][LRP_K_COUNT][2] algorithmic flops / bytes
   double* dvec = nullptr;                // [B][M] weights of the stacked refinement products
   double* s0 = nullptr;                  // [B][M] singular values of the trial solution
-  double mixed_inner_tol = 3e-5;         // FP32 Cross-DEIM tolerance (relative)
+  double mixed_inner_tol = 1e-4;         // FP32 Cross-DEIM tolerance (relative)
+  bool use_graphs = true;                // replay captured CUDA graphs of each iteration
+  cudaStream_t cap_stream = nullptr;     // plan-owned stream used only for graph capture
   double mixed_redundancy = 1e-6;        // redundancy threshold on FP32 data
   double mixed_residual_tol = 1e-7;      // tail-rule truncation of the recompressed residual
   int32_t* active_host = nullptr;        // pinned

@@ -30,6 +30,10 @@ constexpr int TKG = 32;
 constexpr int NT = 256;
 }  // namespace
 
+constexpr int kSmallGram = 64;
+constexpr int kSmallAcc = 16;
+constexpr int kSmallRows = 32;
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __restrict__ st_all, CrossArgs<T> a) {
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
@@ -106,24 +110,30 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   }
 }
 
-template <typename T>
+// Output tile 64 rows x TN columns; TN = 32 serves mo <= 32 (it exits for wider
+// outputs) and TN = 64 the rest (it exits for mo <= 32).
+template <typename T, int TNW>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
                                                 Strided<const T> zsub, int mode) {
+  constexpr int TX = TNW / 4;   // threads along columns
+  constexpr int TY = NT / TX;   // threads along rows
+  constexpr int RI = TM / TY;   // rows per thread
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
   const SolveState st = st_all[slot];
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
-  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
+  if (TNW == 32 ? (mo > 32) : (mo <= 32)) return;
+  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TNW;
   if (c0 >= mo || r0 >= g.n) return;
   const T* X = in.at(slot, side);
   const double* Bm = bm.at(slot, side);
   __shared__ T As[TK][TM];
-  __shared__ T Bs[TK][TN];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
+  __shared__ T Bs[TK][TNW];
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  T acc[RI][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
   for (int k0 = 0; k0 < mi; k0 += TK) {
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
       As[kk][i] = (row < g.n && k < mi) ? X[(int64_t)k * g.ld + row] : (T)0;
     }
 #pragma unroll
-    for (int q = 0; q < (TK * TN) / NT; ++q) {
+    for (int q = 0; q < (TK * TNW) / NT; ++q) {
       const int e = tid + NT * q;
       const int kk = e % TK, c = e / TK;
       const int k = k0 + kk, col = c0 + c;
@@ -144,13 +154,13 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      T av[4], bv[4];
+      T av[RI], bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < RI; ++i) av[i] = As[kk][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TX * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
@@ -159,12 +169,12 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   T* O = out.at(slot, side);
   const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = r0 + ty + 16 * i;
+  for (int i = 0; i < RI; ++i) {
+    const int row = r0 + ty + TY * i;
     if (row >= g.n) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int col = c0 + tx + 16 * j;
+      const int col = c0 + tx + TX * j;
       if (col >= mo) continue;
       const int64_t o = (int64_t)col * g.ld + row;
       O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
@@ -180,6 +190,7 @@ __global__ void __launch_bounds__(NT) k_gram(TallGeom g, const SolveState* __res
   const SolveState st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
+  if (mx <= kSmallGram && my <= kSmallGram) return;  // handled by k_gram_small
   const int ta = blockIdx.y / tiles, tb = blockIdx.y % tiles;
   const int a0 = ta * TM, b0 = tb * TN;
   if (a0 >= mx || b0 >= my) return;
@@ -232,6 +243,87 @@ __global__ void __launch_bounds__(NT) k_gram(TallGeom g, const SolveState* __res
       if (b < my) P[(int64_t)b * g.M + a] = acc[i][j];
     }
   }
+}
+
+// Gram partials for small column counts (mx, my <= kSmallGram): each thread
+// owns up to kSmallAcc output entries (upper triangle only when symmetric) and
+// accumulates them in FP64 over the row block, read through shared memory in
+// chunks of 32 rows.  Exits when either count exceeds kSmallGram (the tiled
+// kernel then does the work).
+// TA is the accumulation type: FP64 for every Gram of the FP64 path and for the
+// first (ill-conditioned) CholeskyQR pass of the FP32 iterations, FP32 for the
+// FP32 iterations' later passes and cross-Grams.
+template <typename T, typename TA>
+__global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState* __restrict__ st_all,
+                                                   Strided<const T> xs, int sel_x, Strided<const T> ys, int sel_y,
+                                                   double* __restrict__ part, bool symmetric) {
+  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const SolveState st = st_all[slot];
+  if (!st.active) return;
+  const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
+  if (mx > kSmallGram || my > kSmallGram || mx < 1 || my < 1) return;
+  const int blk = blockIdx.x;
+  const int rbeg = blk * g.rows_per_block;
+  const int rend = min(g.n, rbeg + g.rows_per_block);
+  const T* X = xs.at(slot, side);
+  const T* Y = ys.at(slot, side);
+  __shared__ TA Xs[kSmallRows][kSmallGram + 1];
+  __shared__ TA Ys[kSmallRows][kSmallGram + 1];
+  const int tid = threadIdx.x;
+  const int nent = symmetric ? mx * (mx + 1) / 2 : mx * my;
+  int ea[kSmallAcc], eb[kSmallAcc];
+  TA acc[kSmallAcc];
+#pragma unroll
+  for (int k = 0; k < kSmallAcc; ++k) {
+    const int e = tid + NT * k;
+    int a = 0, b = 0;
+    if (e < nent) {
+      if (symmetric) {
+        b = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+        while ((b + 1) * (b + 2) / 2 <= e) ++b;
+        while (b * (b + 1) / 2 > e) --b;
+        a = e - b * (b + 1) / 2;
+      } else {
+        a = e % mx;
+        b = e / mx;
+      }
+    } else {
+      a = -1;
+    }
+    ea[k] = a;
+    eb[k] = b;
+    acc[k] = (TA)0;
+  }
+  const bool same = symmetric;
+  for (int r = rbeg; r < rend; r += kSmallRows) {
+    for (int e = tid; e < kSmallRows * mx; e += NT) {
+      const int kk = e % kSmallRows, c = e / kSmallRows;
+      const int row = r + kk;
+      Xs[kk][c] = (row < rend) ? (TA)X[(int64_t)c * g.ld + row] : (TA)0;
+    }
+    if (!same) {
+      for (int e = tid; e < kSmallRows * my; e += NT) {
+        const int kk = e % kSmallRows, c = e / kSmallRows;
+        const int row = r + kk;
+        Ys[kk][c] = (row < rend) ? (TA)Y[(int64_t)c * g.ld + row] : (TA)0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSmallAcc; ++k) {
+      if (ea[k] < 0) continue;
+      const int a = ea[k], b = eb[k];
+      TA s = acc[k];
+#pragma unroll 8
+      for (int kk = 0; kk < kSmallRows; ++kk) s = fma(Xs[kk][a], same ? Xs[kk][b] : Ys[kk][b], s);
+      acc[k] = s;
+    }
+    __syncthreads();
+  }
+  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+#pragma unroll
+  for (int k = 0; k < kSmallAcc; ++k)
+    if (ea[k] >= 0) P[(int64_t)eb[k] * g.M + ea[k]] = (double)acc[k];
 }
 
 __global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int sel_x, int sel_y,
@@ -335,15 +427,25 @@ template <typename T>
 cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
                            Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
                            cudaStream_t s) {
+  k_gemm_nn<T, 32><<<dim3(cdiv(g.n, TM), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub,
+                                                                         mode);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.M <= 32) return e;
   dim3 grid(cdiv(g.n, TM), cdiv(g.M, TN), g.nslots * 2);
-  k_gemm_nn<T><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
+  k_gemm_nn<T, 64><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T> x, int sel_x,
                         Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool acc64) {
+  if (acc64 || sizeof(T) == 8)
+    k_gram_small<T, double><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
+  else
+    k_gram_small<T, float><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.M <= kSmallGram) return e;
   const int tiles = cdiv(g.M, TM);
   dim3 grid(g.NB, tiles * tiles, g.nslots * 2);
   k_gram<T><<<grid, NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, tiles, symmetric);
@@ -366,8 +468,6 @@ cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> 
   while (len < rows) len <<= 1;
   const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
   auto kern = k_leverage<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   dim3 grid(cand_blocks, g.nslots * 2);
   kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len);
   return cudaGetLastError();
@@ -379,7 +479,8 @@ cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> 
                                          Strided<const double>, int, Strided<T>, Strided<const T>, int,       \
                                          cudaStream_t);                                                        \
   template cudaError_t launch_gram<T>(const TallGeom&, const SolveState*, Strided<const T>, int,             \
-                                      Strided<const T>, int, double*, Strided<double>, bool, cudaStream_t);   \
+                                      Strided<const T>, int, double*, Strided<double>, bool, cudaStream_t,    \
+                                      bool);                                                                  \
   template cudaError_t launch_leverage<T>(const TallGeom&, SolveState*, Strided<const T>, int, double*,      \
                                           int32_t*, int, int, cudaStream_t);
 LRP_INST(double)

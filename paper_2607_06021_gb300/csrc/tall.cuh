@@ -42,7 +42,7 @@ cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<cons
 template <typename T>
 cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T> x, int sel_x,
                         Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
-                        cudaStream_t s);
+                        cudaStream_t s, bool acc64 = true);
 
 cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, int sel_y, const double* part,
                           Strided<double> G, bool symmetric, cudaStream_t s);
