@@ -93,8 +93,12 @@ __global__ void k_assemble_residual(RefineArgs a) {
 // K is always formed in FP64 (the cancellation between the stacked blocks happens
 // there); its SVD runs in TC: FP32 suffices for the residual, whose correction is
 // an FP32 solve, and FP64 keeps the final sum exact to working precision.
+constexpr int kRecSmemDim = 64;
+constexpr size_t kRecSmemBytes = 2 * kRecSmemDim * kRecSmemDim * sizeof(double);
+
 template <typename TC>
 __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, double rel_tol, int rcap) {
+  extern __shared__ double rec_smem[];
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
   if (!st->valid) return;
@@ -106,9 +110,14 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
   const double* P0 = a.P.at(slot, 0);
   const double* P1 = a.P.at(slot, 1);
   const double* d = a.dvec + (int64_t)slot * M;
-  TC* base = reinterpret_cast<TC*>(a.scratch + (int64_t)slot * a.scratch_stride);
-  TC* K = base;           // m x m
-  TC* V = base + MM;      // m x m
+  // K and V in shared memory (leading dimension kRecSmemDim) when m is small,
+  // else in the slot's global scratch (leading dimension M).
+  const bool in_smem = m <= kRecSmemDim;
+  const int L = in_smem ? kRecSmemDim : M;
+  TC* base = in_smem ? reinterpret_cast<TC*>(rec_smem) : reinterpret_cast<TC*>(a.scratch + (int64_t)slot * a.scratch_stride);
+  TC* K = base;                          // m x m
+  TC* V = base + (int64_t)L * L;         // m x m
+  (void)MM;
   double* B0 = a.Bf.at(slot, 0);
   double* B1 = a.Bf.at(slot, 1);
   double* sig_out = a.sig_out + (int64_t)slot * a.sig_out_stride;
@@ -121,10 +130,10 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     const int i = e % m, j = e / m;
     double s = 0.0;
     for (int l = max(i, j); l < m; ++l) s += R0[(int64_t)l * M + i] * d[l] * R1[(int64_t)l * M + j];
-    K[(int64_t)j * M + i] = (TC)s;
+    K[(int64_t)j * L + i] = (TC)s;
   }
   __syncthreads();
-  blk_jacobi<TC>(K, M, m, m, V, M, sig, &flag);
+  blk_jacobi<TC>(K, L, m, m, V, L, sig, &flag);
   blk_sort_desc(sig, m, perm);
   int r = 0;
   if (tid == 0) {
@@ -156,8 +165,8 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     double s0 = 0.0, s1 = 0.0;
     const double sv = sig[j];
     for (int c = i; c < m; ++c) {
-      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? (double)K[(int64_t)j * M + c] / sv : 0.0);
-      s1 += P1[(int64_t)c * M + i] * (double)V[(int64_t)j * M + c];
+      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? (double)K[(int64_t)j * L + c] / sv : 0.0);
+      s1 += P1[(int64_t)c * M + i] * (double)V[(int64_t)j * L + c];
     }
     B0[(int64_t)t * M + i] = s0;
     B1[(int64_t)t * M + i] = s1;
@@ -263,6 +272,14 @@ __global__ void k_final_state(RefineArgs a) {
 
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+cudaError_t refine_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_recompress<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kRecSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_recompress<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRecSmemBytes);
+  return e;
+}
+
 cudaError_t launch_prepare_refine(const RefineArgs& a, int nslots, cudaStream_t s) {
   k_prepare_refine<<<nslots, 128, 0, s>>>(a);
   return cudaGetLastError();
@@ -273,9 +290,9 @@ cudaError_t launch_assemble_residual(const RefineArgs& a, int nslots, cudaStream
 }
 cudaError_t launch_recompress(const RefineArgs& a, int nslots, int mode, double rel_tol, int rcap, cudaStream_t s) {
   if (mode == 0)
-    k_recompress<float><<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
+    k_recompress<float><<<nslots, RT, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
   else
-    k_recompress<double><<<nslots, RT, 0, s>>>(a, mode, rel_tol, rcap);
+    k_recompress<double><<<nslots, RT, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
   return cudaGetLastError();
 }
 cudaError_t launch_setup_correction(const RefineArgs& a, int nslots, cudaStream_t s) {

@@ -33,6 +33,8 @@ struct RefineArgs {
   int wstride;
 };
 
+// Raises the dynamic shared-memory limit of the recompression kernels (once per device).
+cudaError_t refine_configure();
 cudaError_t launch_prepare_refine(const RefineArgs& a, int nslots, cudaStream_t s);
 cudaError_t launch_assemble_residual(const RefineArgs& a, int nslots, cudaStream_t s);
 cudaError_t launch_recompress(const RefineArgs& a, int nslots, int mode, double rel_tol, int rcap, cudaStream_t s);

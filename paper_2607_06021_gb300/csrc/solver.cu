@@ -231,6 +231,7 @@ static lrp_status ensure_configured(int device) {
   if (device >= 0 && device < 64 && (configured & (1ull << device))) return LRP_OK;
   cudaError_t e = dst_configure();
   if (e == cudaSuccess) e = core_configure();
+  if (e == cudaSuccess) e = refine_configure();
   if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
   if (device >= 0 && device < 64) configured |= (1ull << device);
   return LRP_OK;
@@ -420,10 +421,12 @@ static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T>
   return LRP_OK;
 }
 
+// Shifted CholeskyQR with `passes` (1..3) passes; Q = B P with B = X (1 pass),
+// Q1 (2 passes) or Q2 (3 passes) and P the inverse R of the last pass (w.P).
 template <typename T>
-static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, const CoreParams& cp,
-                          const CoreBufs<T>& cb, const T* X, int64_t side_stride, int64_t slot_stride, int sel,
-                          cudaStream_t s) {
+static lrp_status cholqr(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, const CoreParams& cp,
+                         const CoreBufs<T>& cb, const T* X, int64_t side_stride, int64_t slot_stride, int sel,
+                         cudaStream_t s, int passes) {
   const PlanDims& d = p->dims;
   const int64_t MM = (int64_t)d.M * d.M;
   const int64_t nm = d.ld * d.M;
@@ -435,6 +438,7 @@ static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, con
                            G, true, s)))
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 0, s));
+  if (passes < 2) return LRP_OK;
   LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs(X, side_stride, slot_stride), sel, P, sel, Strided<T>{w.Q1, nm, 2 * nm},
                                none, 0, s));
@@ -444,6 +448,7 @@ static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, con
                            acc64)))
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 1, s));
+  if (passes < 3) return LRP_OK;
   LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs<T>(w.Q1, nm, 2 * nm), sel, P, sel, Strided<T>{w.Q2, nm, 2 * nm}, none, 0,
                                s));
@@ -452,6 +457,13 @@ static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, con
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 2, s));
   return LRP_OK;
+}
+
+template <typename T>
+static lrp_status cholqr3(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, const CoreParams& cp,
+                          const CoreBufs<T>& cb, const T* X, int64_t side_stride, int64_t slot_stride, int sel,
+                          cudaStream_t s) {
+  return cholqr<T>(p, w, g, cp, cb, X, side_stride, slot_stride, sel, s, 3);
 }
 
 template <typename T>
@@ -729,10 +741,12 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
     // Residual of the trial solution, recompressed in FP64.
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(ra, count, s));
-    if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
+    // One shifted-Cholesky pass: the residual only needs the accuracy of the
+    // FP32 correction solve, and its cancellation happens in the FP64 core.
+    if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 1))) return st;
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M, s));
     LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
-               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
+               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.A, nm, 2 * nm), kDimX,
                                       Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                       Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
     // FP32 correction solve on the residual (already in transformed variables).
@@ -744,10 +758,12 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
     // What1 = What0 + dWhat, recompressed in FP64.
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(ra, count, s));
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(ra, count, s));
-    if ((st = cholqr3<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s))) return st;
+    // Two passes: the stacked blocks are two near-orthonormal bases, and the
+    // result is the output.
+    if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 2))) return st;
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
     LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
-               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q2, nm, 2 * nm), kDimX,
+               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q1, nm, 2 * nm), kDimX,
                                       Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                       Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
     if (step + 1 < p->opts.refine_steps) {
