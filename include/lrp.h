@@ -160,6 +160,23 @@ lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* d_X, int64_t ldx,
                     double* d_Y, int64_t ldy, void* stream);
 
 /*
+ * lrp_dst1 without any device allocation.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory when they call in (a host
+ * callback or plugin running while another framework owns the memory pool, a
+ * fixed memory budget handed out up front, or code that must avoid the implicit
+ * synchronisation of cudaMalloc/cudaFree).  Its scratch (one twiddle table and
+ * the job descriptor, 128 KiB + 256 B) is a fixed array inside the library that
+ * every device which loads the library holds until the process exits.
+ * Arguments and result are those of lrp_dst1, restricted to n+1 <= 8192;
+ * larger n returns LRP_EINVAL.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (for example on two
+ * unordered streams) race on it.
+ */
+lrp_status lrp_dst1_noalloc(int64_t n, int32_t ncols, const double* d_X, int64_t ldx,
+                            double* d_Y, int64_t ldy, void* stream);
+
+/*
  * Measurement hooks (not part of the paper's method).  Kernel classes of the
  * solve, for per-class launch counts and CUDA-event timings.
  */

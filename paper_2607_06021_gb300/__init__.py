@@ -71,6 +71,7 @@ def _load():
         "lrp_solve": ([P, I32, VP, I64, VP, VP, I64, VP, I64, VP, VP, I64, VP, VP], I32),
         "lrp_solve_batch": ([P, I32, ctypes.POINTER(lrp_problem), VP], I32),
         "lrp_dst1": ([I64, I32, VP, I64, VP, I64, VP], I32),
+        "lrp_dst1_noalloc": ([I64, I32, VP, I64, VP, I64, VP], I32),
         "lrp_plan_set_timing": ([P, I32], I32),
         "lrp_plan_kernel_stats": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], I32),
         "lrp_plan_reset_stats": ([P], I32),
@@ -141,6 +142,12 @@ def lrp_solve_batch(plan, problems, stream) -> int:
 
 def lrp_dst1(n, ncols, d_X, ldx, d_Y, ldy, stream) -> int:
     return _check(_lib.lrp_dst1(int(n), int(ncols), d_X, int(ldx), d_Y, int(ldy), stream), "lrp_dst1")
+
+
+def lrp_dst1_noalloc(n, ncols, d_X, ldx, d_Y, ldy, stream) -> int:
+    """lrp_dst1 for callers that cannot allocate device memory (n+1 <= 8192)."""
+    return _check(_lib.lrp_dst1_noalloc(int(n), int(ncols), d_X, int(ldx), d_Y, int(ldy), stream),
+                  "lrp_dst1_noalloc")
 
 
 def lrp_plan_set_timing(plan, enable: bool) -> None:
