@@ -249,6 +249,7 @@ def cross_deim(G, U0, V0, tol: float, r_max: int, maxiter: int = 30,
     info.r_star = r_star
     info.rank_capped = r_star > r_max
     info.I, info.J = I, J
+    info.last = (res.U, res.S, res.V)  # the last iterate before the final truncation
     return res.U[:, :r], res.S[:r], res.V[:, :r], info
 
 
@@ -265,7 +266,9 @@ def poisson_solve(U_f, s_f, V_f, tol: float, r_max: int, maxiter: int = 30,
 
     Fhat = DST(U_f) S_f DST(V_f)^T, Cross-DEIM on What (Eq. g_for_p), then
     W = DST(Uhat) S DST(Vhat)^T.  `warm` = (I, J, (Uh, S, Vh)) from an earlier
-    solve reuses its index sets and iterate.  Returns (U, S, V, info, G).
+    solve (its info.I, info.J and info.last) replaces the initial bases and the
+    empty index sets; the first iteration's change rho is still measured from
+    zero, as in a cold start.  Returns (U, S, V, info, G).
     """
     from .poisson import SpectralSolution, dst1
 
@@ -273,8 +276,8 @@ def poisson_solve(U_f, s_f, V_f, tol: float, r_max: int, maxiter: int = 30,
     if warm is None:
         U0, V0, I0, J0, A0 = orth(G.Uh), orth(G.Vh), None, None, None
     else:
-        I0, J0, A0 = warm
-        U0, V0 = A0[0], A0[2]
+        I0, J0, last = warm
+        U0, V0, A0 = last[0], last[2], None
     Uh, S, Vh, info = cross_deim(G, U0, V0, tol, r_max, maxiter, selector, seed,
                                  m_cap, inloop_rel, I0=I0, J0=J0, A0=A0)
     info.spectral = (Uh, S, Vh)
