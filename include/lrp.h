@@ -87,6 +87,20 @@ typedef struct lrp_info {
   double reserved1;
 } lrp_info;
 
+/*
+ * Warm-start record of one problem: the index sets I, J and the transformed
+ * iterate (Uh, Vh) that a solve ended with (device memory owned by the record,
+ * sized by the plan it was created for).  Algorithm Cross-DEIM starts from
+ * initial bases and empty index sets; a record that holds a result instead seeds
+ * the next solve of a related problem with them (the abstract presents
+ * Cross-DEIM as a warm-startable iteration).  The first iteration's change rho
+ * is measured from zero as in a cold start, so a warm solve runs at least two
+ * iterations.  A record serves one problem at a time: lrp_solve_batch rejects a
+ * batch that names one record twice (LRP_EINVAL), and two batches in flight on
+ * unordered streams must not share a record.
+ */
+typedef struct lrp_warm_s* lrp_warm_t;
+
 /* One problem of a batch (all problems of a plan share n). */
 typedef struct lrp_problem {
   int32_t r_f;           /* right-hand-side rank, 1 <= r_f <= max_rhs_rank */
@@ -102,6 +116,9 @@ typedef struct lrp_problem {
   double* d_V;           /* out: n x max_rank, ld ldv */
   int64_t ldv;
   lrp_info* d_info;      /* out: device memory for one lrp_info (may be NULL) */
+  lrp_warm_t warm;       /* NULL, or a record of this plan: when it holds a result the
+                            solve starts from its I, J and iterate; on return it holds
+                            this solve's (mixed precision: its first FP32 solve's) */
 } lrp_problem;
 
 typedef struct lrp_plan_s* lrp_plan_t;
@@ -122,6 +139,18 @@ lrp_status lrp_default_opts(lrp_opts* opts);
  */
 lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank,
                     const lrp_opts* opts);
+
+/*
+ * Create an empty warm-start record for problems of `plan` (device memory of
+ * about 2 n m_cap doubles).  Errors: LRP_EINVAL, LRP_ENOMEM.
+ */
+lrp_status lrp_warm_create(lrp_plan_t plan, lrp_warm_t* out);
+
+/* Mark a record empty again (the next solve starts cold and refills it). */
+lrp_status lrp_warm_reset(lrp_warm_t warm);
+
+/* Release a record (synchronises the device first). */
+lrp_status lrp_warm_destroy(lrp_warm_t warm);
 
 /* Release a plan and its workspace (synchronises the device first). */
 lrp_status lrp_plan_destroy(lrp_plan_t plan);
@@ -183,7 +212,7 @@ lrp_status lrp_dst1_noalloc(int64_t n, int32_t ncols, const double* d_X, int64_t
 typedef enum lrp_kernel_class {
   LRP_K_DST = 0,       /* forward and back DST-I */
   LRP_K_CROSS = 1,     /* sampled columns/rows of the transformed solution */
-  LRP_K_GRAM = 2,      /* per-block FP64 partial Gram / cross-Gram products */
+  LRP_K_GRAM = 2,      /* per-block partial Gram / cross-Gram products, FP64 accumulation */
   LRP_K_REDUCE = 3,    /* reduction of the Gram partials */
   LRP_K_GEMM = 4,      /* tall-skinny n x m times m x m' products */
   LRP_K_LEVERAGE = 5,  /* leverage scores and block top-c */
@@ -193,7 +222,8 @@ typedef enum lrp_kernel_class {
   LRP_K_STOP = 9,      /* convergence test per problem */
   LRP_K_OTHER = 10,    /* setup, finalize, counters */
   LRP_K_REFINE = 11,   /* mixed precision: residual/sum assembly and recompression cores */
-  LRP_K_COUNT = 12
+  LRP_K_GRAM_F32 = 12, /* partial Gram products with FP32 accumulation (FP32 iterations) */
+  LRP_K_COUNT = 13
 } lrp_kernel_class;
 
 /*

@@ -19,7 +19,7 @@ LRP_NOT_CONVERGED, LRP_RANK_CAPPED, LRP_EAGAIN, LRP_ECAPACITY = 5, 6, 7, 8
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_SEL_LEVERAGE, LRP_SEL_QDEIM = 0, 1
 KERNEL_CLASSES = ["dst", "cross", "gram", "reduce", "gemm", "leverage", "chol", "core", "select", "stop",
-                  "other", "refine"]
+                  "other", "refine", "gram_f32"]
 
 
 class LrpError(RuntimeError):
@@ -51,7 +51,7 @@ class lrp_problem(ctypes.Structure):
                 ("d_s_f", ctypes.c_void_p), ("d_V_f", ctypes.c_void_p),
                 ("ldv_f", ctypes.c_int64), ("d_U", ctypes.c_void_p), ("ldu", ctypes.c_int64),
                 ("d_S", ctypes.c_void_p), ("d_V", ctypes.c_void_p), ("ldv", ctypes.c_int64),
-                ("d_info", ctypes.c_void_p)]
+                ("d_info", ctypes.c_void_p), ("warm", ctypes.c_void_p)]
 
 
 INFO_BYTES = ctypes.sizeof(lrp_info)
@@ -67,6 +67,9 @@ def _load():
         "lrp_default_opts": ([ctypes.POINTER(lrp_opts)], I32),
         "lrp_plan": ([ctypes.POINTER(P), I64, D, I32, ctypes.POINTER(lrp_opts)], I32),
         "lrp_plan_destroy": ([P], I32),
+        "lrp_warm_create": ([P, ctypes.POINTER(P)], I32),
+        "lrp_warm_reset": ([P], I32),
+        "lrp_warm_destroy": ([P], I32),
         "lrp_plan_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I32),
         "lrp_solve": ([P, I32, VP, I64, VP, VP, I64, VP, I64, VP, VP, I64, VP, VP], I32),
         "lrp_solve_batch": ([P, I32, ctypes.POINTER(lrp_problem), VP], I32),
@@ -118,6 +121,20 @@ def lrp_plan(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None):
     _check(_lib.lrp_plan(ctypes.byref(h), int(n), float(tol), int(max_rank),
                          ctypes.byref(opts) if opts is not None else None), "lrp_plan")
     return h
+
+
+def lrp_warm_create(plan):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_warm_create(plan, ctypes.byref(h)), "lrp_warm_create")
+    return h
+
+
+def lrp_warm_reset(warm) -> None:
+    _check(_lib.lrp_warm_reset(warm), "lrp_warm_reset")
+
+
+def lrp_warm_destroy(warm) -> None:
+    _check(_lib.lrp_warm_destroy(warm), "lrp_warm_destroy")
 
 
 def lrp_plan_destroy(plan) -> None:
@@ -173,4 +190,4 @@ def lrp_plan_reset_stats(plan) -> None:
     _check(_lib.lrp_plan_reset_stats(plan), "lrp_plan_reset_stats")
 
 
-from .api import Plan, dst1, colmajor, parse_info, solve  # noqa: E402,F401
+from .api import Plan, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401

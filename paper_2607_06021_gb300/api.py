@@ -8,7 +8,8 @@ import torch
 from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
-               lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch)
+               lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
+               lrp_warm_destroy, lrp_warm_reset)
 
 
 def colmajor(x: torch.Tensor) -> torch.Tensor:
@@ -90,9 +91,13 @@ class Plan:
         info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=device)
         return U, S, V, info
 
-    def problem(self, U_f, s_f, V_f, outs) -> lrp_problem:
+    def warm_record(self) -> "WarmRecord":
+        return WarmRecord(self)
+
+    def problem(self, U_f, s_f, V_f, outs, warm=None) -> lrp_problem:
         U, S, V, info = outs
         p = lrp_problem()
+        p.warm = warm.handle if warm is not None else None
         p.r_f = int(U_f.shape[1])
         p.d_U_f, p.ldu_f = U_f.data_ptr(), _ld(U_f)
         p.d_s_f = s_f.data_ptr()
@@ -103,14 +108,15 @@ class Plan:
         p.d_info = info.data_ptr()
         return p
 
-    def solve_batch_into(self, inputs, outputs, stream=None) -> None:
+    def solve_batch_into(self, inputs, outputs, stream=None, warms=None) -> None:
         """Enqueue a batch; inputs/outputs are lists of (U_f, s_f, V_f) / alloc_outputs()."""
-        probs = [self.problem(*i, o) for i, o in zip(inputs, outputs)]
+        warms = warms if warms is not None else [None] * len(inputs)
+        probs = [self.problem(*i, o, w) for i, o, w in zip(inputs, outputs, warms)]
         lrp_solve_batch(self.handle, probs, _stream(stream))
 
-    def solve_batch(self, inputs, stream=None):
+    def solve_batch(self, inputs, stream=None, warms=None):
         outs = [self.alloc_outputs() for _ in inputs]
-        self.solve_batch_into(inputs, outs, stream)
+        self.solve_batch_into(inputs, outs, stream, warms)
         torch.cuda.synchronize()
         res = []
         for U, S, V, info in outs:
@@ -119,8 +125,30 @@ class Plan:
             res.append((U[:, :r], S[:r], V[:, :r], inf))
         return res
 
-    def solve(self, U_f, s_f, V_f, stream=None):
-        return self.solve_batch([(U_f, s_f, V_f)], stream)[0]
+    def solve(self, U_f, s_f, V_f, stream=None, warm=None):
+        return self.solve_batch([(U_f, s_f, V_f)], stream, [warm])[0]
+
+
+class WarmRecord:
+    """Warm-start record (index sets and iterate of a previous solve) for a plan."""
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        self.handle = lrp_warm_create(plan.handle)
+
+    def reset(self) -> None:
+        lrp_warm_reset(self.handle)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            lrp_warm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(U_f, s_f, V_f, tol: float, max_rank: int, **kw):
@@ -141,4 +169,4 @@ def dst1(X: torch.Tensor, stream=None) -> torch.Tensor:
     return Y
 
 
-__all__ = ["Plan", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
+__all__ = ["Plan", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]

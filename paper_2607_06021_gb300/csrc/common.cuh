@@ -40,6 +40,8 @@ struct SolveState {
   int32_t upar;          // ping-pong parity of the FP32 iterate being stacked
   int32_t rd;            // rank of the correction
   int32_t first_converged;  // the first (FP32) solve met its stop test
+  int32_t c0;            // columns of U_{-1}, V_{-1}: r_f (cold) or the warm iterate's rank
+  int32_t warm_ok;       // this solve may load a warm-start record
   double rho;
   double eta_smin;
   double snorm;          // ||S_k||_F
@@ -62,6 +64,7 @@ enum DimSel : int32_t {
   kDimRPrev = 2,  // r_prev
   kDimRF = 3,     // rf
   kDimX = 4,      // mx[s]
+  kDimC0 = 5,     // c0
 };
 
 __host__ __device__ inline int dim_of(const SolveState& st, int side, int sel) {
@@ -70,6 +73,7 @@ __host__ __device__ inline int dim_of(const SolveState& st, int side, int sel) {
     case kDimR: return st.r;
     case kDimRPrev: return st.r_prev;
     case kDimX: return st.mx[side];
+    case kDimC0: return st.c0;
     default: return st.rf;
   }
 }
@@ -141,5 +145,15 @@ __host__ __device__ inline uint64_t splitmix64(uint64_t x) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
+
+// Device part of a warm-start record (lrp_warm_t).
+struct WarmDev {
+  int32_t valid;      // holds a result
+  int32_t cnt[2];     // |I|, |J|
+  int32_t r;          // rank of the stored iterate
+  int64_t ld;         // leading dimension of U
+  int32_t* idx;       // 2 x M index sets
+  double* U;          // 2 x (ld x M): transformed iterate Uh (side 0), Vh (side 1)
+};
 
 }  // namespace lrp

@@ -45,9 +45,16 @@ __device__ inline double dst_col_flops(int n) {
 }
 
 // Three symmetric Gram passes, two triangular applies, on side sizes m0, m1.
+// FP32 data (w == 4) accumulate passes 2 and 3 in FP32.
 __device__ inline void acct_cholqr3(double* row, double n, double m0, double m1, int NB, double w) {
   for (double m : {m0, m1}) {
-    acct_add(row, LRP_K_GRAM, 3.0 * n * m * (m + 1.0), 3.0 * (n * m * w + NB * m * (m + 1.0) / 2.0 * 8.0));
+    const double gf = n * m * (m + 1.0), gb = n * m * w + NB * m * (m + 1.0) / 2.0 * 8.0;
+    if (w == 4.0) {
+      acct_add(row, LRP_K_GRAM, gf, gb);
+      acct_add(row, LRP_K_GRAM_F32, 2.0 * gf, 2.0 * gb);
+    } else {
+      acct_add(row, LRP_K_GRAM, 3.0 * gf, 3.0 * gb);
+    }
     acct_add(row, LRP_K_REDUCE, 3.0 * NB * m * (m + 1.0) / 2.0, 3.0 * (NB + 1.0) * m * (m + 1.0) / 2.0 * 8.0);
     acct_add(row, LRP_K_GEMM, 2.0 * n * m * (m + 1.0), 2.0 * 2.0 * n * m * w);
   }
@@ -68,11 +75,12 @@ __device__ void acct_iteration(double* row, int n_, int p_, int q_, int r_, int 
   acct_cholqr3(row, n, p, q, NB, w);
   acct_add(row, LRP_K_GEMM, 2.0 * n * r * (p + q), w * n * (p + q + 2.0 * r));  // U_k = Q2 Bf
   acct_add(row, LRP_K_LEVERAGE, 2.0 * 2.0 * n * r, 2.0 * n * r * w);
+  const int gcls = (w_ == 4) ? LRP_K_GRAM_F32 : LRP_K_GRAM;
   if (rp_ > 0) {
-    acct_add(row, LRP_K_GRAM, 2.0 * 2.0 * n * r * rp, 2.0 * (n * (r + rp) * w + NB * r * rp * 8.0));
+    acct_add(row, gcls, 2.0 * 2.0 * n * r * rp, 2.0 * (n * (r + rp) * w + NB * r * rp * 8.0));
     acct_add(row, LRP_K_REDUCE, 2.0 * NB * r * rp, 2.0 * (NB + 1.0) * r * rp * 8.0);
     acct_add(row, LRP_K_GEMM, 2.0 * 2.0 * n * r * rp, 2.0 * n * (r + 2.0 * rp) * w);
-    acct_add(row, LRP_K_GRAM, 2.0 * n * rp * (rp + 1.0), 2.0 * (n * rp * w + NB * rp * (rp + 1.0) / 2.0 * 8.0));
+    acct_add(row, gcls, 2.0 * n * rp * (rp + 1.0), 2.0 * (n * rp * w + NB * rp * (rp + 1.0) / 2.0 * 8.0));
     acct_add(row, LRP_K_REDUCE, 2.0 * NB * rp * (rp + 1.0) / 2.0, 2.0 * (NB + 1.0) * rp * (rp + 1.0) / 2.0 * 8.0);
   }
 }
@@ -223,7 +231,10 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
 // R2 pinv work -> V of the core SVD -> V_k(J,:); R3 V of the pinv SVD -> U~;
 // R4 T1 -> V~; R5 core -> U_k(I,:).
 constexpr int kCoreSmemDim = 64;
-constexpr size_t kCoreSmemBytes = 6 * kCoreSmemDim * kCoreSmemDim * sizeof(double);
+template <typename TC>
+constexpr size_t core_smem_bytes() {
+  return 6 * kCoreSmemDim * kCoreSmemDim * sizeof(TC);
+}
 
 // The small core computes in the precision of the iteration (TC = T): FP64 for
 // the FP64 solve, FP32 for the inner solves of the mixed-precision path.
@@ -511,35 +522,51 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
   const int c = dim_of(*stp, side, sel_c);
   const int total = p.cand_blocks * p.cand_per_block;
   const int64_t base = (int64_t)(slot * 2 + side) * total;
-  for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
-    key[t] = (t < total) ? b.cand_score[base + t] : -1.0;
-    id[t] = (t < total) ? b.cand_idx[base + t] : -1;
-    if (id[t] < 0) {
-      key[t] = -1.0;
-      id[t] = 0x7fffffff;
-    }
-  }
-  __syncthreads();
-  // bitonic sort (score desc, index asc)
-  for (int size = 2; size <= sort_len; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
-        const int pp = t ^ stride;
-        if (pp > t) {
-          const bool up = ((t & size) == 0);
-          const bool tf = (key[t] > key[pp]) || (key[t] == key[pp] && id[t] < id[pp]);
-          if (up != tf) {
-            const double kk = key[t];
-            key[t] = key[pp];
-            key[pp] = kk;
-            const int ii = id[t];
-            id[t] = id[pp];
-            id[pp] = ii;
-          }
+  // Top-c merge of all candidates in chunks that fit the shared sort buffer: each
+  // pass sorts the current best c entries together with the next chunk.
+  const int cc0 = min(c, kMaxM);
+  const int chunk = (total <= sort_len) ? sort_len : sort_len - kMaxM;
+  int have = 0;  // best entries kept at key[0..have)
+  for (int start = 0; start < total; start += chunk) {
+    const int cnt = min(chunk, total - start);
+    for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+      if (t < have) continue;  // keep the running best list in place
+      const int src_i = t - have;
+      double kv = -1.0;
+      int iv = 0x7fffffff;
+      if (src_i < cnt) {
+        const int32_t ci = b.cand_idx[base + start + src_i];
+        if (ci >= 0) {
+          kv = b.cand_score[base + start + src_i];
+          iv = ci;
         }
       }
-      __syncthreads();
+      key[t] = kv;
+      id[t] = iv;
     }
+    __syncthreads();
+    // bitonic sort (score desc, index asc)
+    for (int size = 2; size <= sort_len; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+          const int pp = t ^ stride;
+          if (pp > t) {
+            const bool up = ((t & size) == 0);
+            const bool tf = (key[t] > key[pp]) || (key[t] == key[pp] && id[t] < id[pp]);
+            if (up != tf) {
+              const double kk = key[t];
+              key[t] = key[pp];
+              key[pp] = kk;
+              const int ii = id[t];
+              id[t] = id[pp];
+              id[pp] = ii;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    have = min(cc0, sort_len);
   }
   int32_t* set = b.idx.at(slot, side);
   __shared__ int isnew[kMaxM];
@@ -727,8 +754,65 @@ __global__ void k_setup(CoreParams p, const ProblemDev* prob, T* w, int wstride,
     st.valid = act ? 1 : 0;
     st.rf = rf;
     st.rf0 = rf;
+    st.c0 = rf;
+    st.warm_ok = (act && prob[slot].warm != nullptr) ? 1 : 0;
     *stp = st;
     if (act && acct) acct_setup(acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rf, p.g.NB, (int)sizeof(T));
+  }
+}
+
+template <typename T>
+__global__ void k_warm_load(CoreParams p, CoreBufs<T> b, Strided<T> U1) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  SolveState* stp = p.st + slot;
+  if (!stp->active || !stp->warm_ok) return;
+  const WarmDev* w = b.prob[slot].warm;
+  if (!w || !w->valid) return;
+  const int M = p.g.M;
+  const int r = min(w->r, M);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p.g.n) {
+    const double* src = w->U + (int64_t)side * w->ld * M;
+    T* dst = U1.at(slot, side);
+    for (int c = 0; c < r; ++c) dst[(int64_t)c * p.g.ld + i] = (T)src[(int64_t)c * w->ld + i];
+  }
+  if (blockIdx.x == 0) {
+    const int cnt = min(w->cnt[side], M);
+    int32_t* set = b.idx.at(slot, side);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) set[t] = w->idx[side * M + t];
+    if (threadIdx.x == 0) {
+      stp->cnt[side] = cnt;
+      if (side == 0) stp->c0 = r;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_warm_store(CoreParams p, CoreBufs<T> b, T* const* ubufs, int64_t side_stride, int64_t slot_stride) {
+  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const SolveState* stp = p.st + slot;
+  if (!stp->valid || stp->iters == 0) return;
+  WarmDev* w = b.prob[slot].warm;
+  if (!w) return;
+  const int M = p.g.M;
+  const int r = stp->r;
+  const T* src = ubufs[(stp->k - 1) & 1] + (int64_t)slot * slot_stride + (int64_t)side * side_stride;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p.g.n) {
+    double* dst = w->U + (int64_t)side * w->ld * M;
+    for (int c = 0; c < r; ++c) dst[(int64_t)c * w->ld + i] = (double)src[(int64_t)c * p.g.ld + i];
+  }
+  if (blockIdx.x == 0) {
+    const int cnt = stp->cnt[side];
+    const int32_t* set = b.idx.at(slot, side);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) w->idx[side * M + t] = set[t];
+    if (threadIdx.x == 0) {
+      w->cnt[side] = cnt;
+      if (side == 0) {
+        w->r = r;
+        w->valid = 1;
+      }
+    }
   }
 }
 
@@ -764,7 +848,7 @@ cudaError_t launch_chol(const CoreParams& p, const CoreBufs<T>& b, int sel, int 
 template <typename T>
 cudaError_t launch_core(const CoreParams& p, const CoreBufs<T>& b, int parity, cudaStream_t s) {
   auto kern = k_core<T>;
-  kern<<<p.g.nslots, CT, kCoreSmemBytes, s>>>(p, b, parity);
+  kern<<<p.g.nslots, CT, core_smem_bytes<T>(), s>>>(p, b, parity);
   return cudaGetLastError();
 }
 
@@ -772,7 +856,7 @@ template <typename T>
 cudaError_t launch_select(const CoreParams& p, const CoreBufs<T>& b, int sel_c, cudaStream_t s) {
   const int total = p.cand_blocks * p.cand_per_block;
   int len = 1;
-  while (len < total) len <<= 1;
+  while (len < total && len < 16384) len <<= 1;
   const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
   auto kern = k_select<T>;
   kern<<<p.g.nslots * 2, 512, smem, s>>>(p, b, sel_c, len);
@@ -803,9 +887,10 @@ cudaError_t core_configure() {
   cudaError_t e = cudaSuccess;
   const int sel_bytes = 16384 * (int)(sizeof(double) + sizeof(int));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
+    e = cudaFuncSetAttribute(k_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_smem_bytes<double>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
+    e = cudaFuncSetAttribute(k_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem_bytes<float>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
   if (e == cudaSuccess)
@@ -813,6 +898,19 @@ cudaError_t core_configure() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
   return e;
+}
+
+template <typename T>
+cudaError_t launch_warm_load(const CoreParams& p, const CoreBufs<T>& b, Strided<T> U1, cudaStream_t s) {
+  k_warm_load<T><<<dim3((p.g.n + 255) / 256, p.g.nslots * 2), 256, 0, s>>>(p, b, U1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_warm_store(const CoreParams& p, const CoreBufs<T>& b, T* const* ubufs, int64_t side_stride,
+                              int64_t slot_stride, cudaStream_t s) {
+  k_warm_store<T><<<dim3((p.g.n + 255) / 256, p.g.nslots * 2), 256, 0, s>>>(p, b, ubufs, side_stride, slot_stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s) {
@@ -833,7 +931,10 @@ cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, 
   template cudaError_t launch_finalize_impl<T>(const CoreParams&, const CoreBufs<T>&,                      \
                                                const DstBatch<T, double>&, T* const*, int64_t, int64_t,      \
                                                cudaStream_t);                                                 \
-  template cudaError_t launch_setup<T>(const CoreParams&, const ProblemDev*, T*, int, int, double*, cudaStream_t);
+  template cudaError_t launch_setup<T>(const CoreParams&, const ProblemDev*, T*, int, int, double*, cudaStream_t); \
+  template cudaError_t launch_warm_load<T>(const CoreParams&, const CoreBufs<T>&, Strided<T>, cudaStream_t);      \
+  template cudaError_t launch_warm_store<T>(const CoreParams&, const CoreBufs<T>&, T* const*, int64_t, int64_t,    \
+                                            cudaStream_t);
 LRP_INST(double)
 LRP_INST(float)
 #undef LRP_INST

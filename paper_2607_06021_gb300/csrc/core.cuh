@@ -24,6 +24,7 @@ struct ProblemDev {
   double* V;
   int64_t ldv;
   lrp_info* info;
+  WarmDev* warm;   // warm-start record or nullptr
 };
 
 struct CoreParams {
@@ -94,6 +95,15 @@ cudaError_t launch_setup(const CoreParams& p, const ProblemDev* prob, T* w, int 
 
 // Raises the dynamic shared-memory limits of the per-problem kernels (once per process).
 cudaError_t core_configure();
+
+// Warm start: slots whose record holds a result replace U_{-1}, V_{-1} (in U1,
+// the ping-pong buffer of iteration -1), the index sets and c0; store copies the
+// final iterate (parity from the slot's iteration count) and sets into the record.
+template <typename T>
+cudaError_t launch_warm_load(const CoreParams& p, const CoreBufs<T>& b, Strided<T> U1, cudaStream_t s);
+template <typename T>
+cudaError_t launch_warm_store(const CoreParams& p, const CoreBufs<T>& b, T* const* ubufs, int64_t side_stride,
+                              int64_t slot_stride, cudaStream_t s);
 
 // Eigenvalues lambda_k = 4 sin^2(pi k / (2(n+1))), k = 1..n, in FP64 and FP32.
 cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s);

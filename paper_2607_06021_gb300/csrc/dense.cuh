@@ -26,8 +26,22 @@ struct Eps<float> {
 // (mutually orthogonal), sig[j] = ||A(:,j)|| and, if V != nullptr,
 // A_in = A_out V^T with V orthogonal.
 template <typename TC>
+__device__ __forceinline__ TC half_warp_sum(TC v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided Jacobi SVD of the mr x nc matrix A (col-major, lda; mr >= nc is the
+// intended use) in arithmetic TC, round-robin pair ordering.  Each half-warp
+// rotates one column pair; a warp always takes two pairs of a round together so
+// that its shuffles stay warp-uniform.  On exit the columns of A are U*Sigma
+// (mutually orthogonal), sig[j] = ||A(:,j)|| and, if V != nullptr,
+// A_in = A_out V^T with V orthogonal.
+template <typename TC>
 __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv, double* sig, int* flag) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int half = (tid >> 4) & 1, hl = tid & 15;
   if (V) {
     for (int e = tid; e < nc * nc; e += blockDim.x) {
       const int i = e % nc, j = e / nc;
@@ -36,6 +50,7 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
   }
   __syncthreads();
   const int ne = nc + (nc & 1);
+  const int npairs = ne / 2;
   // Rotate while |a_i . a_j| > tol ||a_i|| ||a_j||; below mr * eps the computed
   // inner products are rounding noise.
   const TC tol = (TC)((double)(mr > 1 ? mr : 1) * Eps<TC>::value);
@@ -43,39 +58,45 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
-      for (int k = warp; k < ne / 2; k += nwarps) {
-        int a, b;
-        if (k == 0) {
-          a = rnd % (ne - 1);
-          b = ne - 1;
-        } else {
-          a = (rnd + k) % (ne - 1);
-          b = (rnd + ne - 1 - k) % (ne - 1);
+      for (int kw = warp; 2 * kw < npairs; kw += nwarps) {
+        const int k = 2 * kw + half;
+        int a = -1, b = -1;
+        if (k < npairs) {
+          if (k == 0) {
+            a = rnd % (ne - 1);
+            b = ne - 1;
+          } else {
+            a = (rnd + k) % (ne - 1);
+            b = (rnd + ne - 1 - k) % (ne - 1);
+          }
+          if (a >= nc || b >= nc) a = b = -1;
+          if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+          }
         }
-        if (a >= nc || b >= nc) continue;
-        if (a > b) {
-          const int t = a;
-          a = b;
-          b = t;
-        }
-        TC* ca = A + (int64_t)a * lda;
-        TC* cb = A + (int64_t)b * lda;
+        const bool valid = a >= 0;
+        TC* ca = A + (int64_t)(valid ? a : 0) * lda;
+        TC* cb = A + (int64_t)(valid ? b : 0) * lda;
         TC alpha = 0, beta = 0, gamma = 0;
-        for (int i = lane; i < mr; i += 32) {
-          const TC x = ca[i], y = cb[i];
-          alpha = fma(x, x, alpha);
-          beta = fma(y, y, beta);
-          gamma = fma(x, y, gamma);
+        if (valid) {
+          for (int i = hl; i < mr; i += 16) {
+            const TC x = ca[i], y = cb[i];
+            alpha = fma(x, x, alpha);
+            beta = fma(y, y, beta);
+            gamma = fma(x, y, gamma);
+          }
         }
-        alpha = warp_sum(alpha);
-        beta = warp_sum(beta);
-        gamma = warp_sum(gamma);
-        if (gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+        alpha = half_warp_sum(alpha);
+        beta = half_warp_sum(beta);
+        gamma = half_warp_sum(gamma);
+        if (!valid || gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
         const TC zeta = (beta - alpha) / ((TC)2 * gamma);
         const TC t = copysign((TC)1, zeta) / (fabs(zeta) + sqrt((TC)1 + zeta * zeta));
         const TC c = (TC)1 / sqrt((TC)1 + t * t);
         const TC s = c * t;
-        for (int i = lane; i < mr; i += 32) {
+        for (int i = hl; i < mr; i += 16) {
           const TC x = ca[i], y = cb[i];
           ca[i] = c * x - s * y;
           cb[i] = s * x + c * y;
@@ -83,13 +104,13 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
         if (V) {
           TC* va = V + (int64_t)a * ldv;
           TC* vb = V + (int64_t)b * ldv;
-          for (int i = lane; i < nc; i += 32) {
+          for (int i = hl; i < nc; i += 16) {
             const TC x = va[i], y = vb[i];
             va[i] = c * x - s * y;
             vb[i] = s * x + c * y;
           }
         }
-        if (lane == 0) *flag = 1;
+        if (hl == 0) *flag = 1;
       }
       __syncthreads();
     }
@@ -97,6 +118,7 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
     __syncthreads();
     if (!rotated) break;
   }
+  const int lane = tid & 31;
   for (int j = warp; j < nc; j += nwarps) {
     const TC* cj = A + (int64_t)j * lda;
     TC s = 0;

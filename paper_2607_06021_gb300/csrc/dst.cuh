@@ -28,9 +28,15 @@ cudaError_t dst_configure();
 void* dst_make_twiddles(int64_t N, bool fp64, cudaStream_t st);
 size_t dst_smem_bytes(int64_t n, bool fp64);
 bool dst_smem_supported(int64_t n, bool fp64);
+bool dst_supported(int64_t n);  // n+1 <= 2^21 (shared-memory or multi-pass)
 
+// Bytes of HBM staging one column needs in the multi-pass DST (0 when the
+// shared-memory kernel applies, n+1 <= 8192 in FP64 / 16384 in FP32).
+size_t dst_temp_bytes(int64_t n, bool fp64);
+
+// temp: staging of max_cols * nslots * nmats * dst_temp_bytes(n) bytes (multi-pass only).
 template <typename TIn, typename TOut, typename TC>
 cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols, int nslots, int nmats,
-                        const void* tw, cudaStream_t st);
+                        const void* tw, cudaStream_t st, void* temp = nullptr, size_t temp_bytes = 0);
 
 }  // namespace lrp

@@ -25,7 +25,25 @@ namespace lrp {
 
 namespace {
 constexpr int RT = 256;
+
+__device__ inline void racct(const RefineArgs& a, int slot, int cls, double flops, double bytes) {
+  if (!a.acct) return;
+  double* row = a.acct + (int64_t)slot * 2 * LRP_K_COUNT;
+  row[2 * cls] += flops;
+  row[2 * cls + 1] += bytes;
 }
+
+// FP64 Gram passes (symmetric) and triangular applies of one shifted CholeskyQR
+// on two n x m blocks.
+__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m) {
+  const double n = a.n;
+  racct(a, slot, LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0), 2.0 * passes * (n * m * 8.0 + a.NB * m * (m + 1.0) * 4.0));
+  racct(a, slot, LRP_K_REDUCE, 2.0 * passes * a.NB * m * (m + 1.0) / 2.0,
+        2.0 * passes * (a.NB + 1.0) * m * (m + 1.0) * 4.0);
+  if (passes > 1)
+    racct(a, slot, LRP_K_GEMM, 2.0 * (passes - 1) * n * m * (m + 1.0), 2.0 * (passes - 1) * 2.0 * n * m * 8.0);
+}
+}  // namespace
 
 
 // After the first FP32 solve: r0 = rank of the trial solution (capped so that
@@ -57,6 +75,10 @@ __global__ void k_prepare_refine(RefineArgs a) {
     st->mx[0] = st->mx[1] = rf + 2 * r0;
     st->active = 1;
     st->upar = par;
+    const double m = rf + 2.0 * r0, n = a.n;
+    // stacked blocks: read Uh_f (FP64) and Uh0 (FP32), write X and the FP64 stash
+    racct(a, slot, LRP_K_REFINE, 2.0 * n * r0, 2.0 * n * (rf * 8.0 + r0 * 4.0 + m * 8.0 + r0 * 8.0));
+    racct_cholqr(a, slot, 1, m);
   }
 }
 
@@ -172,7 +194,11 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     B1[(int64_t)t * M + i] = s1;
   }
   for (int t = tid; t < r; t += nt) sig_out[t] = sig[perm[t]];
-  if (tid == 0) st->r = r;
+  if (tid == 0) {
+    st->r = r;
+    // the tall product (Q-basis block) * Bf that follows on both sides
+    racct(a, slot, LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r, 2.0 * a.n * (m + r) * 8.0);
+  }
 }
 
 // Prepare the FP32 correction solve: its right-hand side in transformed
@@ -193,6 +219,8 @@ __global__ void k_setup_correction(RefineArgs a) {
     z.active = 1;
     z.valid = 1;
     z.rf = rR;
+    z.c0 = rR;
+    z.warm_ok = 0;
     z.rf0 = rf0;
     z.r0 = r0;
     z.total_iters = total;
@@ -237,6 +265,9 @@ __global__ void k_prepare_sum(RefineArgs a) {
     st->upar = par;
     st->rd = rd;
     st->active = 1;
+    const double n = a.n;
+    racct(a, slot, LRP_K_REFINE, 0.0, 2.0 * n * (r0 * 8.0 + rd * 4.0 + (r0 + rd) * 8.0));
+    racct_cholqr(a, slot, 2, r0 + rd);
   }
 }
 

@@ -31,6 +31,8 @@ struct RefineArgs {
   int64_t scratch_stride;
   float* w32;                  // weights of the FP32 correction solve
   int wstride;
+  double* acct;                // per slot LRP_K_COUNT x {flops, bytes} (see core.cuh)
+  int NB;                      // Gram partial blocks of the plan
 };
 
 // Raises the dynamic shared-memory limit of the recompression kernels (once per device).

@@ -232,6 +232,7 @@ static lrp_status ensure_configured(int device) {
   cudaError_t e = dst_configure();
   if (e == cudaSuccess) e = core_configure();
   if (e == cudaSuccess) e = refine_configure();
+  if (e == cudaSuccess) e = tall_configure();
   if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
   if (device >= 0 && device < 64) configured |= (1ull << device);
   return LRP_OK;
@@ -267,7 +268,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (o.selector != LRP_SEL_LEVERAGE) return set_error(LRP_EINVAL, "only the leverage-score selector is built");
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
-  if (!dst_smem_supported(n, true)) return set_error(LRP_EINVAL, "n+1 > 8192 needs the multi-pass DST (not built)");
+  if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
 
   lrp_plan_s* p = new (std::nothrow) lrp_plan_s();
   if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
@@ -294,13 +295,14 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (d.NB < 1) d.NB = 1;
   d.rows_per_block = (int)(((n + d.NB - 1) / d.NB + 31) / 32 * 32);
   d.NB = (int)((n + d.rows_per_block - 1) / d.rows_per_block);
-  // Leverage candidate blocks of at most 1024 rows.
-  d.cand_blocks = (int)((n + 1023) / 1024);
-  d.cand_per_block = M;
-  if (d.cand_blocks * d.cand_per_block > 16384) {
-    delete p;
-    return set_error(LRP_EINVAL, "candidate merge too large for this n and m_cap");
+  // Leverage candidate blocks: 1024 .. 8192 rows (sorted in shared memory), at
+  // most ~128 blocks; k_select merges their top-c lists in bounded chunks.
+  {
+    int64_t rows = 1024;
+    while (rows < 8192 && rows * 128 < n) rows <<= 1;
+    d.cand_blocks = (int)((n + rows - 1) / rows);
   }
+  d.cand_per_block = M;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     return set_error(LRP_ECUDA, "no CUDA device");
@@ -321,6 +323,13 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   p->active_dev = p->arena.get<int32_t>(4);
   p->acct = p->arena.get<double>((size_t)d.B * 2 * LRP_K_COUNT);
   p->dvec = p->arena.get<double>((size_t)d.B * d.M);
+  {
+    const size_t per_col = dst_temp_bytes(n, true);
+    const int maxc = max_rank < d.M ? max_rank : d.M;
+    const int cols = d.RF > maxc ? d.RF : maxc;
+    p->dst_temp_bytes = per_col * (size_t)cols * d.B * 2;
+    if (p->dst_temp_bytes) p->dst_temp = p->arena.get<unsigned char>(p->dst_temp_bytes);
+  }
   p->s0 = p->arena.get<double>((size_t)d.B * d.M);
   if (!p->arena.ok()) s = set_error(LRP_ENOMEM, "plan allocation failed");
   if (s == LRP_OK) s = p->w64.allocate(d, p->arena, d.RF);
@@ -348,6 +357,48 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     return s;
   }
   *out = p;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_warm_create(lrp_plan_t p, lrp_warm_t* out) {
+  if (!p || !out) return set_error(LRP_EINVAL, "NULL argument");
+  *out = nullptr;
+  lrp_warm_s* w = new (std::nothrow) lrp_warm_s();
+  if (!w) return set_error(LRP_ENOMEM, "host allocation failed");
+  w->plan = p;
+  const PlanDims& d = p->dims;
+  WarmDev h;
+  memset(&h, 0, sizeof(h));
+  h.ld = d.ld;
+  w->dev = w->arena.get<WarmDev>(1);
+  h.idx = w->arena.get<int32_t>((size_t)2 * d.M);
+  h.U = w->arena.get<double>((size_t)2 * d.ld * d.M);
+  if (!w->arena.ok()) {
+    w->arena.release();
+    delete w;
+    return set_error(LRP_ENOMEM, "warm-start record allocation failed");
+  }
+  if (cudaMemcpy(w->dev, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+    w->arena.release();
+    delete w;
+    return set_error(LRP_ECUDA, "warm-start record initialisation failed");
+  }
+  *out = w;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_warm_reset(lrp_warm_t w) {
+  if (!w) return set_error(LRP_EINVAL, "NULL record");
+  int32_t zero = 0;
+  LRP_CUDA(cudaMemcpy(&w->dev->valid, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_warm_destroy(lrp_warm_t w) {
+  if (!w) return LRP_OK;
+  cudaDeviceSynchronize();
+  w->arena.release();
+  delete w;
   return LRP_OK;
 }
 
@@ -379,8 +430,9 @@ extern "C" lrp_status lrp_plan_workspace_bytes(lrp_plan_t p, size_t* bytes) {
 namespace lrp {
 
 // Kernels launched by one tall GEMM / Gram call (narrow and wide variants).
-static inline int gemm_kernels(const lrp_plan_s* p) { return p->dims.M > 32 ? 2 : 1; }
-static inline int gram_kernels(const lrp_plan_s* p) { return p->dims.M > 64 ? 2 : 1; }
+static inline int gemm_kernels(const lrp_plan_s*) { return 1; }
+static inline int gram_kernels(const lrp_plan_s*) { return 1; }
+static inline int dst_kernels(const lrp_plan_s* p) { return dst_smem_supported(p->n, true) ? 1 : 2; }
 
 template <typename T>
 static CoreBufs<T> make_core_bufs(lrp_plan_s* p, Workspace<T>& w) {
@@ -416,7 +468,8 @@ static Strided<const T> cs(const T* base, int64_t side, int64_t slot) {
 template <typename T>
 static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T> x, int sx, Strided<const T> y,
                               int sy, double* part, Strided<double> G, bool sym, cudaStream_t s, bool acc64 = true) {
-  LRP_LAUNCH(p, LRP_K_GRAM, gram_kernels(p), s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s, acc64));
+  const int cls = (acc64 || sizeof(T) == 8) ? LRP_K_GRAM : LRP_K_GRAM_F32;
+  LRP_LAUNCH(p, cls, gram_kernels(p), s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s, acc64));
   LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, sx, sy, part, G, sym, s));
   return LRP_OK;
 }
@@ -528,7 +581,8 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   job.active_stride = 0;
   job.require_active = 0;
   const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
-  LRP_LAUNCH(p, LRP_K_DST, 1, s, (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s)));
+  LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+             (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
   return LRP_OK;
 }
 
@@ -591,8 +645,10 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
     LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
                launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
                                  kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
+    // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_warm_load<T>(cp, cb, Strided<T>{w.U[1], nm, 2 * nm}, s));
     LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-               launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimRF, w.cand_score, w.cand_idx,
+               launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimC0, w.cand_score, w.cand_idx,
                                   d.cand_blocks, d.cand_per_block, s));
     return LRP_OK;
   };
@@ -610,7 +666,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   for (int k = 0; k < p->opts.max_iter; ++k) {
     const int par = k & 1;
     auto iteration = [&](cudaStream_t s) -> lrp_status {
-      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimRF : kDimR, s));
+      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimC0 : kDimR, s));
       LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(g, p->st, ca, s));
       lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.A, nm, 2 * nm, kDimOther, s);
       if (st) return st;
@@ -673,7 +729,17 @@ static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParam
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_finalize_impl<T>(cp, cb, back, w.ubufs, nm, 2 * nm, s));
   const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   const int maxc = p->r_max < d.M ? p->r_max : d.M;
-  LRP_LAUNCH(p, LRP_K_DST, 1, s, (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s)));
+  LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+             (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
+  return LRP_OK;
+}
+
+template <typename T>
+static lrp_status warm_store(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, cudaStream_t s) {
+  if (!p->any_warm) return LRP_OK;
+  const int64_t nm = p->dims.ld * p->dims.M;
+  CoreBufs<T> cb = make_core_bufs<T>(p, w);
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_warm_store<T>(cp, cb, w.ubufs, nm, 2 * nm, s));
   return LRP_OK;
 }
 
@@ -682,6 +748,7 @@ static lrp_status run_fp64(lrp_plan_s* p, int count, cudaStream_t s) {
   lrp_status st;
   if ((st = phase_forward<double>(p, p->w64, cp, count, true, s))) return st;
   if ((st = phase_iterate<double>(p, p->w64, cp, count, s))) return st;
+  if ((st = warm_store<double>(p, p->w64, cp, s))) return st;
   return phase_finalize<double>(p, p->w64, cp, count, s);
 }
 
@@ -714,6 +781,8 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.scratch_stride = kCoreScratch * MM;
   a.w32 = p->w32.w;
   a.wstride = p->w32.rf_cap;
+  a.acct = p->acct;
+  a.NB = d.NB;
   return a;
 }
 
@@ -728,6 +797,10 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   const double tol_in = p->tol > p->mixed_inner_tol ? p->tol : p->mixed_inner_tol;
   CoreParams c32 = make_core_params<float>(p, count, tol_in, eps32, p->mixed_redundancy);
   c32.noise_floor_stop = 1;
+  // FP32 solves whose change between iterates stalls above tol_in (FP32 noise in
+  // the index updates) stop after a bounded number of iterations; the FP64
+  // residual step corrects what they leave.
+  c32.max_iter = p->opts.max_iter < p->mixed_inner_max_iter ? p->opts.max_iter : p->mixed_inner_max_iter;
   CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
   RefineArgs ra = make_refine_args(p);
@@ -737,6 +810,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   if ((st = phase_forward<float>(p, p->w32, c32, count, true, s))) return st;
   if ((st = phase_forward<double>(p, p->w64, c64, count, false, s))) return st;
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
+  if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
   for (int step = 0; step < p->opts.refine_steps; ++step) {
     // Residual of the trial solution, recompressed in FP64.
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
@@ -779,6 +853,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
 
 static lrp_status validate_problem(const lrp_plan_s* p, const lrp_problem& pr) {
   const int64_t n = p->n;
+  if (pr.warm && pr.warm->plan != p) return set_error(LRP_EINVAL, "warm-start record belongs to another plan");
   if (pr.r_f < 1 || pr.r_f > p->dims.RF) return set_error(LRP_EINVAL, "r_f out of range [1, max_rhs_rank]");
   if (!pr.d_U_f || !pr.d_V_f || !pr.d_s_f || !pr.d_U || !pr.d_S || !pr.d_V)
     return set_error(LRP_EINVAL, "NULL factor pointer");
@@ -793,6 +868,8 @@ extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_pro
   for (int i = 0; i < count; ++i) {
     lrp_status s = validate_problem(p, hp[i]);
     if (s != LRP_OK) return s;
+    for (int j = 0; j < i && hp[i].warm; ++j)
+      if (hp[j].warm == hp[i].warm) return set_error(LRP_EINVAL, "one warm-start record used twice in a batch");
   }
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < count; ++i) {
@@ -810,7 +887,10 @@ extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_pro
     d.V = hp[i].d_V;
     d.ldv = hp[i].ldv;
     d.info = hp[i].d_info;
+    d.warm = hp[i].warm ? hp[i].warm->dev : nullptr;
   }
+  p->any_warm = false;
+  for (int i = 0; i < count; ++i) p->any_warm = p->any_warm || hp[i].warm != nullptr;
   LRP_CUDA(cudaMemcpyAsync(p->prob_dev, p->prob_host, sizeof(ProblemDev) * count, cudaMemcpyHostToDevice, s));
   if (p->opts.precision == LRP_FP64) return run_fp64(p, count, s);
   return run_mixed(p, count, s);
@@ -840,7 +920,7 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
                                void* stream) {
   if (n < 1 || !is_pow2(n + 1)) return set_error(LRP_EINVAL, "n+1 must be a power of two >= 2");
   if (ncols < 0 || !X || !Y || ldx < n || ldy < n) return set_error(LRP_EINVAL, "bad DST arguments");
-  if (!dst_smem_supported(n, true)) return set_error(LRP_EINVAL, "n+1 > 8192 needs the multi-pass DST (not built)");
+  if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
   if (ncols == 0) return LRP_OK;
   cudaStream_t s = (cudaStream_t)stream;
   // Per-call job arrays: tiny device allocation kept for the lifetime of the process per n.
@@ -851,6 +931,8 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
     int dev = -1;
     void* tw = nullptr;
     void* arrays = nullptr;
+    void* temp = nullptr;
+    size_t temp_bytes = 0;
   };
   static Cache cache[8];
   int dev = 0;
@@ -872,12 +954,25 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
       c = &cache[0];
       cudaFree(c->tw);
       cudaFree(c->arrays);
+      if (c->temp) cudaFree(c->temp);
+      c->temp = nullptr;
+      c->temp_bytes = 0;
     }
     c->n = n;
     c->dev = dev;
     c->tw = dst_make_twiddles(n + 1, true, nullptr);
     LRP_CUDA(cudaMalloc(&c->arrays, 4 * sizeof(void*)));
     LRP_CUDA(cudaDeviceSynchronize());
+  }
+  {
+    const size_t need = dst_temp_bytes(n, true) * (size_t)ncols;
+    if (need > c->temp_bytes) {
+      if (c->temp) cudaFree(c->temp);
+      c->temp = nullptr;
+      c->temp_bytes = 0;
+      LRP_CUDA(cudaMalloc(&c->temp, need));
+      c->temp_bytes = need;
+    }
   }
   const void* h[4] = {X, Y, (const void*)(intptr_t)ldx, (const void*)(intptr_t)ldy};
   LRP_CUDA(cudaMemcpyAsync(c->arrays, h, sizeof(h), cudaMemcpyHostToDevice, s));
@@ -896,7 +991,7 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
   job.active_dev = nullptr;
   job.active_stride = 0;
   job.require_active = 0;
-  LRP_CUDA((dst1_launch<double, double, double>(n, job, ncols, 1, 1, c->tw, s)));
+  LRP_CUDA((dst1_launch<double, double, double>(n, job, ncols, 1, 1, c->tw, s, c->temp, c->temp_bytes)));
   return LRP_OK;
 }
 
@@ -919,4 +1014,4 @@ extern "C" const char* lrp_status_string(lrp_status s) {
 
 static_assert(sizeof(lrp_opts) == 40, "lrp_opts layout");
 static_assert(sizeof(lrp_info) == 64, "lrp_info layout");
-static_assert(sizeof(lrp_problem) == 96, "lrp_problem layout");
+static_assert(sizeof(lrp_problem) == 104, "lrp_problem layout");

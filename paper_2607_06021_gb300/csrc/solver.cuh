@@ -125,8 +125,11 @@ struct lrp_plan_s {
   int32_t* active_dev = nullptr;
   double* acct = nullptr;                // [B][LRP_K_COUNT][2] algorithmic flops / bytes
   double* dvec = nullptr;                // [B][M] weights of the stacked refinement products
+  unsigned char* dst_temp = nullptr;     // HBM staging of the multi-pass DST (n+1 > 8192)
+  size_t dst_temp_bytes = 0;
   double* s0 = nullptr;                  // [B][M] singular values of the trial solution
   double mixed_inner_tol = 1e-4;         // FP32 Cross-DEIM tolerance (relative)
+  int mixed_inner_max_iter = 12;         // iteration cap of each FP32 Cross-DEIM solve
   bool use_graphs = true;                // replay captured CUDA graphs of each iteration
   cudaStream_t cap_stream = nullptr;     // plan-owned stream used only for graph capture
   double mixed_redundancy = 1e-6;        // redundancy threshold on FP32 data
@@ -135,5 +138,12 @@ struct lrp_plan_s {
   lrp::Workspace<double> w64;
   lrp::Workspace<float> w32;
   KernelStats stats;
+  bool any_warm = false;                 // the current call has warm-start records
   std::mutex mu;
+};
+
+struct lrp_warm_s {
+  lrp_plan_s* plan = nullptr;
+  DeviceArena arena;
+  lrp::WarmDev* dev = nullptr;
 };

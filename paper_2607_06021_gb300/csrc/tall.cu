@@ -110,26 +110,15 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   }
 }
 
-// Output tile 64 rows x TN columns; TN = 32 serves mo <= 32 (it exits for wider
-// outputs) and TN = 64 the rest (it exits for mo <= 32).
+// One 64-row tile of Out = In * Bm (or Zsub - In * Bm) over output columns
+// [c0, c0 + TNW): 256 threads, each RI rows x 4 columns.
 template <typename T, int TNW>
-__global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
-                                                int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
-                                                Strided<const T> zsub, int mode) {
+__device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
+                                          T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
+                                          int r0, int c0, T (*As)[TM], T (*Bs)[64]) {
   constexpr int TX = TNW / 4;   // threads along columns
   constexpr int TY = NT / TX;   // threads along rows
   constexpr int RI = TM / TY;   // rows per thread
-  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
-  const SolveState st = st_all[slot];
-  if (!st.active) return;
-  const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
-  if (TNW == 32 ? (mo > 32) : (mo <= 32)) return;
-  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TNW;
-  if (c0 >= mo || r0 >= g.n) return;
-  const T* X = in.at(slot, side);
-  const double* Bm = bm.at(slot, side);
-  __shared__ T As[TK][TM];
-  __shared__ T Bs[TK][TNW];
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   T acc[RI][4];
 #pragma unroll
@@ -166,8 +155,6 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
     }
     __syncthreads();
   }
-  T* O = out.at(slot, side);
-  const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
 #pragma unroll
   for (int i = 0; i < RI; ++i) {
     const int row = r0 + ty + TY * i;
@@ -182,65 +169,80 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   }
 }
 
+// One launch for every output width: a CTA owns 64 rows and runs one 32-wide
+// tile when mo <= 32, else 64-wide tiles over all output columns.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_gram(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> xs,
-                                             int sel_x, Strided<const T> ys, int sel_y, double* __restrict__ part,
-                                             int tiles, bool symmetric) {
+__global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
+                                                int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
+                                                Strided<const T> zsub, int mode) {
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
-  const SolveState st = st_all[slot];
+  const SolveState& st = st_all[slot];
   if (!st.active) return;
-  const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
-  if (mx <= kSmallGram && my <= kSmallGram) return;  // handled by k_gram_small
-  const int ta = blockIdx.y / tiles, tb = blockIdx.y % tiles;
-  const int a0 = ta * TM, b0 = tb * TN;
-  if (a0 >= mx || b0 >= my) return;
-  if (symmetric && tb < ta) return;
-  const int blk = blockIdx.x;
-  const int rbeg = blk * g.rows_per_block;
-  const int rend = min(g.n, rbeg + g.rows_per_block);
-  const T* X = xs.at(slot, side);
-  const T* Y = ys.at(slot, side);
-  __shared__ T As[TKG][TM + 1];
-  __shared__ T Bs[TKG][TN + 1];
+  const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
+  const int r0 = blockIdx.x * TM;
+  if (r0 >= g.n || mo < 1) return;
+  __shared__ T As[TK][TM];
+  __shared__ T Bs[TK][64];
+  const T* X = in.at(slot, side);
+  const double* Bm = bm.at(slot, side);
+  T* O = out.at(slot, side);
+  const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
+  if (mo <= 32) {
+    gemm_tile<T, 32>(g, X, Bm, O, Z, mode, mi, mo, r0, 0, As, Bs);
+  } else {
+    for (int c0 = 0; c0 < mo; c0 += 64) gemm_tile<T, 64>(g, X, Bm, O, Z, mode, mi, mo, r0, c0, As, Bs);
+  }
+}
+
+// Tiled FP64 Gram partials for widths above kSmallGram: the CTA loops over the
+// 64 x 64 output tiles (upper tiles only when symmetric) of its row block.
+template <typename T>
+__device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* __restrict__ Y, int mx, int my,
+                           int rbeg, int rend, double* __restrict__ P, bool symmetric, unsigned char* smem) {
+  T (*As)[TM + 1] = reinterpret_cast<T (*)[TM + 1]>(smem);
+  T (*Bs)[TN + 1] = reinterpret_cast<T (*)[TN + 1]>(smem + sizeof(T) * TKG * (TM + 1));
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int r = rbeg; r < rend; r += TKG) {
-#pragma unroll
-    for (int q = 0; q < (TKG * TM) / NT; ++q) {
-      const int e = tid + NT * q;
-      const int kk = e % TKG, c = e / TKG;
-      const int row = r + kk;
-      As[kk][c] = (row < rend && a0 + c < mx) ? X[(int64_t)(a0 + c) * g.ld + row] : (T)0;
-      Bs[kk][c] = (row < rend && b0 + c < my) ? Y[(int64_t)(b0 + c) * g.ld + row] : (T)0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < TKG; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = (double)As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = (double)Bs[kk][tx + 16 * j];
+  for (int a0 = 0; a0 < mx; a0 += TM) {
+    for (int b0 = symmetric ? a0 : 0; b0 < my; b0 += TN) {
+      double acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int r = rbeg; r < rend; r += TKG) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int a = a0 + ty + 16 * i;
-    if (a >= mx) continue;
+        for (int q = 0; q < (TKG * TM) / NT; ++q) {
+          const int e = tid + NT * q;
+          const int kk = e % TKG, c = e / TKG;
+          const int row = r + kk;
+          As[kk][c] = (row < rend && a0 + c < mx) ? X[(int64_t)(a0 + c) * g.ld + row] : (T)0;
+          Bs[kk][c] = (row < rend && b0 + c < my) ? Y[(int64_t)(b0 + c) * g.ld + row] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < TKG; ++kk) {
+          double av[4], bv[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = b0 + tx + 16 * j;
-      if (b < my) P[(int64_t)b * g.M + a] = acc[i][j];
+          for (int i = 0; i < 4; ++i) av[i] = (double)As[kk][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bv[j] = (double)Bs[kk][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int a = a0 + ty + 16 * i;
+        if (a >= mx) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int b = b0 + tx + 16 * j;
+          if (b < my) P[(int64_t)b * g.M + a] = acc[i][j];
+        }
+      }
     }
   }
 }
@@ -261,14 +263,20 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
   const SolveState st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
-  if (mx > kSmallGram || my > kSmallGram || mx < 1 || my < 1) return;
+  if (mx < 1 || my < 1) return;
   const int blk = blockIdx.x;
   const int rbeg = blk * g.rows_per_block;
   const int rend = min(g.n, rbeg + g.rows_per_block);
   const T* X = xs.at(slot, side);
   const T* Y = ys.at(slot, side);
-  __shared__ TA Xs[kSmallRows][kSmallGram + 1];
-  __shared__ TA Ys[kSmallRows][kSmallGram + 1];
+  __shared__ __align__(16) unsigned char gsm[2 * kSmallRows * (kSmallGram + 1) * sizeof(double)];
+  if (mx > kSmallGram || my > kSmallGram) {
+    double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+    gram_tiled<T>(g, X, Y, mx, my, rbeg, rend, P, symmetric, gsm);
+    return;
+  }
+  TA (*Xs)[kSmallGram + 1] = reinterpret_cast<TA (*)[kSmallGram + 1]>(gsm);
+  TA (*Ys)[kSmallGram + 1] = reinterpret_cast<TA (*)[kSmallGram + 1]>(gsm + sizeof(TA) * kSmallRows * (kSmallGram + 1));
   const int tid = threadIdx.x;
   const int nent = symmetric ? mx * (mx + 1) / 2 : mx * my;
   int ea[kSmallAcc], eb[kSmallAcc];
@@ -427,12 +435,7 @@ template <typename T>
 cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
                            Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
                            cudaStream_t s) {
-  k_gemm_nn<T, 32><<<dim3(cdiv(g.n, TM), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub,
-                                                                         mode);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || g.M <= 32) return e;
-  dim3 grid(cdiv(g.n, TM), cdiv(g.M, TN), g.nslots * 2);
-  k_gemm_nn<T, 64><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
+  k_gemm_nn<T><<<dim3(cdiv(g.n, TM), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
   return cudaGetLastError();
 }
 
@@ -444,11 +447,6 @@ cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T
     k_gram_small<T, double><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
   else
     k_gram_small<T, float><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || g.M <= kSmallGram) return e;
-  const int tiles = cdiv(g.M, TM);
-  dim3 grid(g.NB, tiles * tiles, g.nslots * 2);
-  k_gram<T><<<grid, NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, tiles, symmetric);
   (void)G;
   return cudaGetLastError();
 }
@@ -471,6 +469,13 @@ cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> 
   dim3 grid(cand_blocks, g.nslots * 2);
   kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len);
   return cudaGetLastError();
+}
+
+cudaError_t tall_configure() {
+  const int bytes = 8192 * (int)(sizeof(double) + sizeof(int));  // largest leverage sort
+  cudaError_t e = cudaFuncSetAttribute(k_leverage<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leverage<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 #define LRP_INST(T)                                                                                           \

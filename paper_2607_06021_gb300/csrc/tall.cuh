@@ -47,6 +47,9 @@ cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T
 cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, int sel_y, const double* part,
                           Strided<double> G, bool symmetric, cudaStream_t s);
 
+// Raises the dynamic shared-memory limit of the leverage kernels (once per device).
+cudaError_t tall_configure();
+
 // Leverage scores of U[s](:, :c) rows (c from sel) and per-block top-c candidates.
 template <typename T>
 cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel,

@@ -50,4 +50,4 @@ def test_struct_layouts_match_header():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
     assert ctypes.sizeof(pkg.lrp_opts) == 40
     assert ctypes.sizeof(pkg.lrp_info) == 64
-    assert ctypes.sizeof(pkg.lrp_problem) == 96
+    assert ctypes.sizeof(pkg.lrp_problem) == 104
