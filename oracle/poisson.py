@@ -168,3 +168,60 @@ def rel_error_vs_exact(U, S, V, exact: SpectralSolution, block: int = 1024,
         num += float(np.sum((E - Uh[I] @ Vh.T) ** 2))
         den += float(np.sum(E ** 2))
     return float(np.sqrt(num / den))
+
+
+def rel_error_sampled(U, S, V, exact: SpectralSolution, n_low: int = 256, per_stratum: int = 32,
+                      seed: int = 0, block: int = 16):
+    """Stratified estimate of ||W - W_ex||_F / ||W_ex||_F for grids too large to sum.
+
+    Transformed space as in rel_error_vs_exact (Z orthogonal).  The transformed
+    rows are split by frequency: rows [0, n_low) (the low frequencies, which
+    hold most of the mass) are summed exactly; then geometric strata
+    [L, 2L), [2L, 4L), ... up to n, from each of which per_stratum rows are
+    drawn uniformly without replacement (all of it when smaller), each row's sums
+    exact and scaled by the stratum size over the sample size.  Returns
+    (estimate, standard error): the variance of each stratum's scaled sum from
+    its sample variance with the finite-population correction, carried through
+    rel = sqrt(num / den) to first order.  When every stratum is taken whole
+    the estimate is exact and the standard error 0.
+    """
+    Uh = dst1(U) * np.asarray(S, float)
+    Vh = dst1(V)
+    n = exact.n
+    L = max(1, min(n_low, n))
+
+    def row_sums(I):
+        e = np.empty(len(I))
+        d = np.empty(len(I))
+        for b in range(0, len(I), block):
+            Ib = np.asarray(I[b:b + block])
+            E = exact.rows(Ib)
+            e[b:b + len(Ib)] = np.sum((E - Uh[Ib] @ Vh.T) ** 2, axis=1)
+            d[b:b + len(Ib)] = np.sum(E ** 2, axis=1)
+        return e, d
+
+    e1, d1 = row_sums(np.arange(L))
+    num, den = float(e1.sum()), float(d1.sum())
+    var_num = var_den = cov = 0.0
+    rng = np.random.default_rng(seed)
+    lo = L
+    while lo < n:
+        hi = min(2 * lo, n)
+        size = hi - lo
+        m = min(per_stratum, size)
+        I = lo + (np.arange(size) if m == size else rng.choice(size, size=m, replace=False))
+        e2, d2 = row_sums(I)
+        scale = size / m
+        num += scale * float(e2.sum())
+        den += scale * float(d2.sum())
+        if 1 < m < size:
+            f = size * size / m * (1.0 - m / size)
+            var_num += f * float(np.var(e2, ddof=1))
+            var_den += f * float(np.var(d2, ddof=1))
+            cov += f * float(np.cov(e2, d2, ddof=1)[0, 1])
+        lo = hi
+    q = num / den
+    var_q = (var_num - 2 * q * cov + q * q * var_den) / (den * den)
+    rel = float(np.sqrt(q))
+    se = float(np.sqrt(max(var_q, 0.0)) / (2 * rel)) if rel > 0 else 0.0
+    return rel, se

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import lrp_inputs as li
+from oracle import cross_deim as cd
 from oracle import poisson as po
 
 
@@ -143,3 +144,26 @@ def test_error_measures_against_dense():
     err = po.rel_error_vs_exact(Uw[:, :2], Sw[:2], Vtw[:2].T, G)
     ref = np.linalg.norm(W - (Uw[:, :2] * Sw[:2]) @ Vtw[:2]) / np.linalg.norm(W)
     assert abs(err - ref) < 1e-10 * max(ref, 1e-300) + 1e-15
+
+
+def test_sampled_error_exact_when_all_rows_low():
+    rhs = li.gaussian_eigen_rhs(255, 3, 4)
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-4, 8)
+    exact = po.rel_error_vs_exact(U, S, V, G)
+    est, se = po.rel_error_sampled(U, S, V, G, n_low=255)
+    assert se == 0.0
+    assert abs(est - exact) <= 1e-12 * exact
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_sampled_error_within_standard_errors(seed):
+    # Narrow Gaussians (the large-grid recipe) on n = 4095, a loose solve so the
+    # error sits well above rounding: the stratified estimate from 16 exact
+    # rows + 32 rows per geometric stratum lands within four of its standard
+    # errors of the exact full sum, and that standard error is below 0.1%.
+    rhs = li.gaussian_eigen_rhs(4095, seed, 8, 0, s_lo=0.005, s_hi=0.05)
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-3, 24)
+    exact = po.rel_error_vs_exact(U, S, V, G)
+    est, se = po.rel_error_sampled(U, S, V, G, n_low=16, per_stratum=32, seed=seed)
+    assert abs(est - exact) <= 4 * se + 1e-9 * exact, (est, se, exact)
+    assert se < 1e-3 * exact
