@@ -234,6 +234,30 @@ typedef enum lrp_kernel_class {
 lrp_status lrp_plan_set_timing(lrp_plan_t plan, int32_t enable);
 
 /*
+ * Per-iteration trace of Algorithm Cross-DEIM (Sec. 3.1): with enable != 0 every
+ * later solve records, for each problem slot and each iteration (the mixed
+ * path's FP32 solves in order, the correction solve after the first), the
+ * quantities of the stop test.  The first call allocates
+ * batch * LRP_TRACE_LEN * LRP_TRACE_WIDTH doubles of device memory (freed with
+ * the plan).  Toggling re-captures the iteration graphs on the next solve.
+ * Errors: LRP_EINVAL (NULL plan), LRP_ENOMEM.
+ */
+#define LRP_TRACE_LEN 96
+#define LRP_TRACE_WIDTH 8
+lrp_status lrp_plan_set_trace(lrp_plan_t plan, int32_t enable);
+
+/*
+ * Copy the trace of batch slot `slot` of the last solve to host memory `out`
+ * (row-major, LRP_TRACE_WIDTH doubles per iteration: iteration index within its
+ * solve, rho, min(eta1(1+eta2), eta2(1+eta1)) S_min, |I_k|, |J_k| before
+ * redundancy removal, in-loop rank r_k, ||S_k||_F, |I_k| after removal), at
+ * most max_entries rows; *n_entries receives the rows written.  Synchronises
+ * the device.  Errors: LRP_EINVAL (NULL pointer, slot out of range, tracing
+ * never enabled), LRP_ECUDA.
+ */
+lrp_status lrp_plan_trace(lrp_plan_t plan, int32_t slot, double* out, int32_t max_entries, int32_t* n_entries);
+
+/*
  * Launches and summed event-timed milliseconds of kernel class kclass
  * (0 <= kclass < LRP_K_COUNT, or -1 for all classes) since the last reset.
  * Synchronises the device first.  *total_ms is 0 when timing was off.

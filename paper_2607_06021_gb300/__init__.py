@@ -76,6 +76,8 @@ def _load():
         "lrp_dst1": ([I64, I32, VP, I64, VP, I64, VP], I32),
         "lrp_dst1_noalloc": ([I64, I32, VP, I64, VP, I64, VP], I32),
         "lrp_plan_set_timing": ([P, I32], I32),
+        "lrp_plan_set_trace": ([P, I32], I32),
+        "lrp_plan_trace": ([P, I32, ctypes.POINTER(ctypes.c_double), I32, ctypes.POINTER(I32)], I32),
         "lrp_plan_kernel_stats": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], I32),
         "lrp_plan_reset_stats": ([P], I32),
         "lrp_plan_kernel_work": ([P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
@@ -169,6 +171,28 @@ def lrp_dst1_noalloc(n, ncols, d_X, ldx, d_Y, ldy, stream) -> int:
 
 def lrp_plan_set_timing(plan, enable: bool) -> None:
     _check(_lib.lrp_plan_set_timing(plan, 1 if enable else 0), "lrp_plan_set_timing")
+
+
+LRP_TRACE_LEN = 96
+LRP_TRACE_WIDTH = 8
+TRACE_FIELDS = ("iteration", "rho", "eta_smin", "size_I", "size_J", "rank", "snorm", "size_I_kept")
+
+
+def lrp_plan_set_trace(plan, enable: bool) -> None:
+    _check(_lib.lrp_plan_set_trace(plan, 1 if enable else 0), "lrp_plan_set_trace")
+
+
+def lrp_plan_trace(plan, slot: int):
+    """Rows of the slot's per-iteration trace, as dicts keyed by TRACE_FIELDS."""
+    buf = (ctypes.c_double * (LRP_TRACE_LEN * LRP_TRACE_WIDTH))()
+    cnt = ctypes.c_int32()
+    _check(_lib.lrp_plan_trace(plan, slot, buf, LRP_TRACE_LEN, ctypes.byref(cnt)), "lrp_plan_trace")
+    rows = []
+    for i in range(cnt.value):
+        row = buf[i * LRP_TRACE_WIDTH:(i + 1) * LRP_TRACE_WIDTH]
+        rows.append({k: (int(v) if k not in ("rho", "eta_smin", "snorm") else float(v))
+                     for k, v in zip(TRACE_FIELDS, row)})
+    return rows
 
 
 def lrp_plan_kernel_stats(plan, kclass: int):

@@ -8,6 +8,7 @@ import torch
 from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
+               lrp_plan_set_trace, lrp_plan_trace,
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
                lrp_warm_destroy, lrp_warm_reset)
 
@@ -60,6 +61,12 @@ class Plan:
 
     def set_timing(self, enable: bool) -> None:
         lrp_plan_set_timing(self.handle, enable)
+
+    def set_trace(self, enable: bool) -> None:
+        lrp_plan_set_trace(self.handle, enable)
+
+    def trace(self, slot: int = 0):
+        return lrp_plan_trace(self.handle, slot)
 
     def reset_stats(self) -> None:
         lrp_plan_reset_stats(self.handle)

@@ -14,6 +14,9 @@ namespace lrp {
 
 constexpr int kMaxM = LRP_MAX_M;
 constexpr int kMaxRF = 256;
+// Per-iteration trace (lrp_plan_set_trace): entries per slot, doubles per entry.
+constexpr int kTraceLen = 96;  // LRP_TRACE_LEN
+constexpr int kTraceWidth = 8;
 
 // Per-problem iteration state, one per batch slot, in device memory.
 // Side 0 is the row space (cross matrix C = What(:,J), factor U_k, index set
@@ -47,6 +50,7 @@ struct SolveState {
   double snorm;          // ||S_k||_F
   double snorm_prev;
   double gram_trace[2];  // trace of the pass-1 Gram (shift scale)
+  double tol;            // stop-test tolerance of the current solve
 };
 
 enum : int32_t {

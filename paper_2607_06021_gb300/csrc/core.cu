@@ -653,11 +653,24 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
   }
   if (stp->snorm == 0.0) rho = 0.0;  // zero right-hand side: W = 0 is exact
   if (threadIdx.x == 0) {
+    if (p.trace && stp->total_iters < kTraceLen) {
+      // {solve iteration, rho, eta1/eta2 S_min term, |I|, |J| (before redundancy
+      //  removal), in-loop rank, ||S_k||_F, |I| after removal}
+      double* e = p.trace + ((int64_t)slot * kTraceLen + stp->total_iters) * kTraceWidth;
+      e[0] = stp->iters;
+      e[1] = rho;
+      e[2] = stp->eta_smin;
+      e[3] = stp->cnt[0];
+      e[4] = stp->cnt[1];
+      e[5] = r;
+      e[6] = stp->snorm;
+      e[7] = stp->cnt_next[0];
+    }
     stp->rho = rho;
     stp->iters += 1;
     stp->total_iters += 1;
     stp->k += 1;
-    const bool conv = fmax(rho, stp->eta_smin) < p.tol;
+    const bool conv = fmax(rho, stp->eta_smin) < stp->tol;
     if (conv) {
       stp->flags |= kFlagConverged;
       stp->active = 0;
@@ -756,6 +769,7 @@ __global__ void k_setup(CoreParams p, const ProblemDev* prob, T* w, int wstride,
     st.rf0 = rf;
     st.c0 = rf;
     st.warm_ok = (act && prob[slot].warm != nullptr) ? 1 : 0;
+    st.tol = p.tol;
     *stp = st;
     if (act && acct) acct_setup(acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rf, p.g.NB, (int)sizeof(T));
   }

@@ -42,6 +42,7 @@ struct CoreParams {
   int noise_floor_stop;  // 1: the eta S_min term counts as met once S_min is at the data's noise floor
   int cand_blocks;     // leverage candidate blocks per side
   int cand_per_block;
+  double* trace;       // [nslots][kTraceLen][kTraceWidth] per-iteration record, or nullptr
 };
 
 // Per-slot buffers used by the core kernels (all FP64 unless noted, M x M col-major).

@@ -226,6 +226,7 @@ __global__ void k_setup_correction(RefineArgs a) {
     z.total_iters = total;
     z.flags = st->flags & ~kFlagConverged;
     z.first_converged = (st->flags & kFlagConverged) ? 1 : 0;
+    z.tol = a.corr_tol;
     *st = z;
   }
 }

@@ -33,6 +33,7 @@ struct RefineArgs {
   int wstride;
   double* acct;                // per slot LRP_K_COUNT x {flops, bytes} (see core.cuh)
   int NB;                      // Gram partial blocks of the plan
+  double corr_tol;             // stop-test tolerance of the FP32 correction solve
 };
 
 // Raises the dynamic shared-memory limit of the recompression kernels (once per device).

@@ -145,6 +145,46 @@ extern "C" lrp_status lrp_plan_set_timing(lrp_plan_t p, int32_t enable) {
   return LRP_OK;
 }
 
+extern "C" lrp_status lrp_plan_set_trace(lrp_plan_t p, int32_t enable) {
+  if (!p) return set_error(LRP_EINVAL, "NULL plan");
+  std::lock_guard<std::mutex> lock(p->mu);
+  const bool on = enable != 0;
+  if (on && !p->trace_dev) {
+    const size_t bytes = sizeof(double) * (size_t)p->dims.B * kTraceLen * kTraceWidth;
+    if (cudaMalloc((void**)&p->trace_dev, bytes) != cudaSuccess) {
+      p->trace_dev = nullptr;
+      return set_error(LRP_ENOMEM, "trace allocation failed");
+    }
+    LRP_CUDA(cudaMemset(p->trace_dev, 0, bytes));
+  }
+  if (on != p->trace_on) {
+    // captured iteration graphs hold the kernel parameters, trace pointer included
+    p->w64.release_graphs();
+    p->w32.release_graphs();
+  }
+  p->trace_on = on;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_plan_trace(lrp_plan_t p, int32_t slot, double* out, int32_t max_entries,
+                                     int32_t* n_entries) {
+  if (!p || !out || !n_entries) return set_error(LRP_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= p->dims.B || max_entries < 0) return set_error(LRP_EINVAL, "slot out of range");
+  std::lock_guard<std::mutex> lock(p->mu);
+  *n_entries = 0;
+  if (!p->trace_dev) return set_error(LRP_EINVAL, "tracing was never enabled on this plan");
+  LRP_CUDA(cudaDeviceSynchronize());
+  SolveState h;
+  LRP_CUDA(cudaMemcpy(&h, p->st + slot, sizeof(h), cudaMemcpyDeviceToHost));
+  int cnt = h.total_iters < kTraceLen ? h.total_iters : kTraceLen;
+  if (cnt > max_entries) cnt = max_entries;
+  if (cnt > 0)
+    LRP_CUDA(cudaMemcpy(out, p->trace_dev + (size_t)slot * kTraceLen * kTraceWidth,
+                        sizeof(double) * kTraceWidth * cnt, cudaMemcpyDeviceToHost));
+  *n_entries = cnt;
+  return LRP_OK;
+}
+
 extern "C" lrp_status lrp_plan_kernel_stats(lrp_plan_t p, int32_t kclass, int64_t* launches, double* total_ms) {
   if (!p || !launches || !total_ms) return set_error(LRP_EINVAL, "NULL argument");
   if (kclass < -1 || kclass >= LRP_K_COUNT) return set_error(LRP_EINVAL, "kernel class out of range");
@@ -405,6 +445,7 @@ extern "C" lrp_status lrp_warm_destroy(lrp_warm_t w) {
 extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
   if (!p) return LRP_OK;
   cudaDeviceSynchronize();
+  if (p->trace_dev) cudaFree(p->trace_dev);
   p->arena.release();
   if (p->tw64) cudaFree(p->tw64);
   if (p->tw32) cudaFree(p->tw32);
@@ -537,6 +578,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   cp.selector = p->opts.selector;
   cp.cand_blocks = d.cand_blocks;
   cp.cand_per_block = d.cand_per_block;
+  cp.trace = p->trace_on ? p->trace_dev : nullptr;
   return cp;
 }
 
@@ -783,6 +825,7 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.wstride = p->w32.rf_cap;
   a.acct = p->acct;
   a.NB = d.NB;
+  a.corr_tol = p->tol;
   return a;
 }
 
@@ -804,6 +847,15 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
   RefineArgs ra = make_refine_args(p);
+  // The trial solution carries a relative error of about tol_in, so the
+  // correction dW needs relative accuracy tol / tol_in only (its error enters
+  // the sum scaled by ||dW|| ~ tol_in ||W||); FP32 offers no better than tol_in.
+  {
+    double ct = p->tol / tol_in;
+    if (ct < tol_in) ct = tol_in;
+    if (ct > 0.1) ct = 0.1;
+    ra.corr_tol = ct;
+  }
   const TallGeom& g = c64.g;
   const Strided<const double> none{nullptr, 0, 0};
   lrp_status st;

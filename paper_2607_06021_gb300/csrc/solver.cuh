@@ -139,6 +139,8 @@ struct lrp_plan_s {
   lrp::Workspace<float> w32;
   KernelStats stats;
   bool any_warm = false;                 // the current call has warm-start records
+  double* trace_dev = nullptr;           // [B][kTraceLen][kTraceWidth], allocated on first use
+  bool trace_on = false;
   std::mutex mu;
 };
 

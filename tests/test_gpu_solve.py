@@ -81,3 +81,38 @@ def test_batch_equals_individual_solves():
         Ua, Sa, Va, _ = _gpu_solve(rhs, 1e-10, 32, m_cap=0)
         assert po.lowrank_rel_diff(to_np(U), to_np(S), to_np(V), Ua, Sa, Va) < 1e-12
     plan.close()
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_trace_matches_oracle_iteration_by_iteration(seed):
+    # Every iteration of Algorithm Cross-DEIM: the sizes of I_k, J_k after the
+    # union and the growth index, the in-loop rank, rho and the eta S_min term of
+    # the stop test agree with the oracle's (same reading of the paper).
+    import paper_2607_06021_gb300 as lrp
+    from tests.gpu_util import rhs_dev
+    rhs = li.workload_single_small(seed)
+    tol, r_max, m_cap = 1e-10, 32, 68
+    plan = lrp.Plan(rhs.n, tol, r_max, max_rhs_rank=rhs.rank, m_cap=m_cap, seed=seed)
+    plan.set_trace(True)
+    plan.solve(*rhs_dev(rhs))
+    tr = plan.trace(0)
+    plan.close()
+    _, _, _, oinfo, _ = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, r_max, seed=seed, m_cap=m_cap)
+    assert len(tr) == oinfo.iterations
+    for k, row in enumerate(tr):
+        assert row["iteration"] == k
+        assert (row["size_I"], row["size_J"]) == tuple(oinfo.sizes[k]), (k, row, oinfo.sizes[k])
+        assert row["rank"] == oinfo.ranks[k], (k, row)
+        rho_o, eta_o = oinfo.rho[k], oinfo.eta_smin[k]
+        # rho is a difference of nearly equal iterates: agree to 1e-6 relative or
+        # 1e-13 absolute (its rounding floor).
+        assert abs(row["rho"] - rho_o) <= 1e-6 * rho_o + 1e-13, (k, row["rho"], rho_o)
+        # eta = 1/sigma_min(U_k(I,:)): the GPU takes it from the Gram of U_k(I,:)
+        # (Cholesky + power iteration on the inverse), the oracle from an SVD.
+        # Where the term is <= 1 (the range that decides the stop test) they agree
+        # to 1e-3; above it kappa(U_k(I,:))^2 nears 1/eps, the Gram value keeps only
+        # its magnitude, and both sides just stay far above any tolerance.
+        if eta_o <= 1.0:
+            assert abs(row["eta_smin"] - eta_o) <= 1e-3 * eta_o + 1e-15, (k, row["eta_smin"], eta_o)
+        else:
+            assert row["eta_smin"] > 0.5, (k, row["eta_smin"], eta_o)
