@@ -42,7 +42,7 @@ typedef enum lrp_status {
   LRP_ETIMEDOUT = 4,       /* a bounded wait gave up (server drain, device flag) */
   LRP_NOT_CONVERGED = 5,   /* max_iter reached; a valid result was still written */
   LRP_RANK_CAPPED = 6,     /* tolerance needs rank > max_rank; result truncated */
-  LRP_EAGAIN = 7,          /* lrp_poll: the request has not finished yet */
+  LRP_EAGAIN = 7,          /* lrp_poll: not finished yet; lrp_submit: server full, retry */
   LRP_ECAPACITY = 8        /* server admission: request larger than the memory cap */
 } lrp_status;
 
@@ -139,6 +139,14 @@ lrp_status lrp_default_opts(lrp_opts* opts);
  */
 lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank,
                     const lrp_opts* opts);
+
+/*
+ * Device bytes that lrp_plan(n, tol, max_rank, opts) would allocate in its
+ * workspace arena (the figure lrp_plan_workspace_bytes reports for the plan),
+ * computed on the host without touching a device.  Same argument checks and
+ * errors as lrp_plan (LRP_EINVAL), plus LRP_EINVAL for NULL bytes.
+ */
+lrp_status lrp_plan_estimate_bytes(int64_t n, double tol, int32_t max_rank, const lrp_opts* opts, size_t* bytes);
 
 /*
  * Create an empty warm-start record for problems of `plan` (device memory of
@@ -274,6 +282,111 @@ lrp_status lrp_plan_kernel_work(lrp_plan_t plan, int32_t kclass, double* flops, 
 
 /* Clear the launch counts, timings and work totals of a plan. */
 lrp_status lrp_plan_reset_stats(lrp_plan_t plan);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A request server over the batched solver for streams of independent
+ * problems of varying n, precision and tolerance (one GPU, one process).
+ * Admission: each request's working set is estimated as
+ * 8 n (2 r_f + 4 m_cap + 2 max_rank) bytes (m_cap = min(2 max_rank + r_f', 256),
+ * r_f' = r_f rounded up to a multiple of 8); a request is refused with
+ * LRP_ECAPACITY when it alone exceeds the memory cap, and with LRP_EAGAIN when
+ * the queued and running requests' estimates plus its own would exceed the cap
+ * or the queue is full (retry later).  Scheduling: worker lanes (one host thread
+ * and one CUDA stream each) take the oldest waiting request whose bucket
+ * (n, precision, tol, max_rank, r_f') has no batch running and solve it with up
+ * to a plan's batch of waiting requests of that bucket, in arrival order
+ * (continuous batching: later arrivals join the next batch).  One plan per
+ * bucket is created on first use with as many batch slots as fit a quarter of
+ * the cap, and idle plans are destroyed least recently used when a new plan or
+ * warm-start record would not fit.  Warm start: requests that name the same
+ * nonzero warm_key share a warm-start record of their bucket's plan (created
+ * by the first, reused by later ones; at most warm_capacity records per plan,
+ * least recently used dropped); a batch holds at most one request per key.
+ */
+typedef struct lrp_server_s* lrp_server_t;
+
+typedef struct lrp_server_opts {
+  int64_t memory_cap_bytes;  /* device bytes for plans and warm records, and the admission cap (40 GiB) */
+  int32_t lanes;             /* concurrent batches, 1..16 (2) */
+  int32_t max_batch;         /* upper bound of a plan's batch slots (64) */
+  int32_t max_queue;         /* waiting requests before LRP_EAGAIN (65536) */
+  int32_t warm_capacity;     /* warm-start records per plan (64) */
+} lrp_server_opts;
+
+typedef struct lrp_request {
+  int64_t n;            /* interior points per dimension, n+1 a power of two */
+  int32_t r_f;          /* right-hand-side rank */
+  int32_t max_rank;     /* output rank cap (r_max) */
+  double tol;           /* relative tolerance of Algorithm Cross-DEIM */
+  int32_t precision;    /* lrp_precision */
+  int32_t reserved;
+  uint64_t warm_key;    /* 0, or the key of a warm-start record (see above) */
+  const double* U_f;    /* host, n x r_f column-major (ld n); copied by lrp_submit */
+  const double* s_f;    /* host, r_f; copied */
+  const double* V_f;    /* host, n x r_f; copied */
+  double* U;            /* host out, n x max_rank (ld n): first rank columns written */
+  double* S;            /* host out, max_rank singular values */
+  double* V;            /* host out, n x max_rank */
+} lrp_request;
+
+typedef struct lrp_result {
+  int32_t status;       /* the solve's lrp_status (OK, NOT_CONVERGED, RANK_CAPPED) or the error */
+  int32_t rank;         /* columns written to U, V */
+  int32_t iterations;   /* Cross-DEIM iterations, all solves of the request */
+  int32_t warm_used;    /* 1 if the solve started from a filled warm-start record */
+  double latency_us;    /* lrp_submit to completion */
+  double queue_us;      /* lrp_submit to the start of its batch */
+} lrp_result;
+
+typedef struct lrp_server_stats {
+  int64_t submitted, completed, rejected;  /* since creation or the last reset */
+  int64_t queued, running, plans;
+  int64_t device_bytes;                    /* plans + warm records held */
+  int64_t admitted_bytes;                  /* estimates of queued + running requests */
+  double p50_us, p99_us, mean_us, max_us;  /* latency of completed requests (nearest rank) */
+} lrp_server_stats;
+
+/* Fill *opts with the defaults.  Returns LRP_EINVAL for NULL. */
+lrp_status lrp_server_default_opts(lrp_server_opts* opts);
+
+/* The admission estimate above in bytes (0 for out-of-range arguments). */
+size_t lrp_request_footprint(int64_t n, int32_t r_f, int32_t max_rank);
+
+/*
+ * Start a server on the current device (opts may be NULL).  Errors:
+ * LRP_EINVAL (options out of range), LRP_ECUDA (no device), LRP_ENOMEM.
+ */
+lrp_status lrp_server_create(lrp_server_t* out, const lrp_server_opts* opts);
+
+/*
+ * Admit one request without blocking on the GPU: the inputs are copied, the
+ * output buffers must stay valid until the request's result has been taken.
+ * *ticket identifies it.  Errors: LRP_EINVAL (bad request), LRP_ECAPACITY,
+ * LRP_EAGAIN (see above), LRP_ENOMEM.
+ */
+lrp_status lrp_submit(lrp_server_t server, const lrp_request* req, uint64_t* ticket);
+
+/*
+ * LRP_EAGAIN while the request runs or waits; once it has finished, LRP_OK with
+ * *out filled, after which the ticket is released (a second poll is LRP_EINVAL).
+ */
+lrp_status lrp_poll(lrp_server_t server, uint64_t ticket, lrp_result* out);
+
+/* As lrp_poll, but waits up to timeout_us; LRP_ETIMEDOUT if still unfinished. */
+lrp_status lrp_wait(lrp_server_t server, uint64_t ticket, lrp_result* out, int64_t timeout_us);
+
+/* Counters and latency percentiles (microseconds). */
+lrp_status lrp_server_get_stats(lrp_server_t server, lrp_server_stats* out);
+
+/* Clear the counters and the latency record. */
+lrp_status lrp_server_reset_stats(lrp_server_t server);
+
+/*
+ * Finish every admitted request, stop the lanes and free all device memory.
+ * Results not yet taken are discarded.
+ */
+lrp_status lrp_server_destroy(lrp_server_t server);
 
 /* Thread-local text of the last error (empty string if none). */
 const char* lrp_last_error(void);

@@ -54,6 +54,33 @@ class lrp_problem(ctypes.Structure):
                 ("d_info", ctypes.c_void_p), ("warm", ctypes.c_void_p)]
 
 
+class lrp_server_opts(ctypes.Structure):
+    _fields_ = [("memory_cap_bytes", ctypes.c_int64), ("lanes", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("warm_capacity", ctypes.c_int32)]
+
+
+class lrp_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("r_f", ctypes.c_int32), ("max_rank", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("warm_key", ctypes.c_uint64), ("U_f", ctypes.c_void_p), ("s_f", ctypes.c_void_p),
+                ("V_f", ctypes.c_void_p), ("U", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("V", ctypes.c_void_p)]
+
+
+class lrp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("rank", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("warm_used", ctypes.c_int32), ("latency_us", ctypes.c_double), ("queue_us", ctypes.c_double)]
+
+
+class lrp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("plans", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("admitted_bytes", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double)]
+
+
 INFO_BYTES = ctypes.sizeof(lrp_info)
 
 
@@ -81,6 +108,16 @@ def _load():
         "lrp_plan_kernel_stats": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], I32),
         "lrp_plan_reset_stats": ([P], I32),
         "lrp_plan_kernel_work": ([P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+        "lrp_plan_estimate_bytes": ([I64, D, I32, ctypes.POINTER(lrp_opts), ctypes.POINTER(ctypes.c_size_t)], I32),
+        "lrp_server_default_opts": ([ctypes.POINTER(lrp_server_opts)], I32),
+        "lrp_request_footprint": ([I64, I32, I32], ctypes.c_size_t),
+        "lrp_server_create": ([ctypes.POINTER(P), ctypes.POINTER(lrp_server_opts)], I32),
+        "lrp_submit": ([P, ctypes.POINTER(lrp_request), ctypes.POINTER(ctypes.c_uint64)], I32),
+        "lrp_poll": ([P, ctypes.c_uint64, ctypes.POINTER(lrp_result)], I32),
+        "lrp_wait": ([P, ctypes.c_uint64, ctypes.POINTER(lrp_result), I64], I32),
+        "lrp_server_get_stats": ([P, ctypes.POINTER(lrp_server_stats)], I32),
+        "lrp_server_reset_stats": ([P], I32),
+        "lrp_server_destroy": ([P], I32),
         "lrp_last_error": ([], ctypes.c_char_p),
         "lrp_status_string": ([I32], ctypes.c_char_p),
     }
@@ -123,6 +160,66 @@ def lrp_plan(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None):
     _check(_lib.lrp_plan(ctypes.byref(h), int(n), float(tol), int(max_rank),
                          ctypes.byref(opts) if opts is not None else None), "lrp_plan")
     return h
+
+
+def lrp_plan_estimate_bytes(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None) -> int:
+    v = ctypes.c_size_t()
+    _check(_lib.lrp_plan_estimate_bytes(int(n), float(tol), int(max_rank),
+                                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(v)),
+           "lrp_plan_estimate_bytes")
+    return int(v.value)
+
+
+def lrp_server_default_opts() -> lrp_server_opts:
+    o = lrp_server_opts()
+    _check(_lib.lrp_server_default_opts(ctypes.byref(o)), "lrp_server_default_opts")
+    return o
+
+
+def lrp_request_footprint(n: int, r_f: int, max_rank: int) -> int:
+    return int(_lib.lrp_request_footprint(int(n), int(r_f), int(max_rank)))
+
+
+def lrp_server_create(opts: lrp_server_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_server_create(ctypes.byref(h), ctypes.byref(opts) if opts is not None else None),
+           "lrp_server_create")
+    return h
+
+
+def lrp_submit(server, req: lrp_request):
+    """Ticket, or None when the server answers LRP_EAGAIN (full: retry later)."""
+    t = ctypes.c_uint64()
+    s = _check(_lib.lrp_submit(server, ctypes.byref(req), ctypes.byref(t)), "lrp_submit", (LRP_OK, LRP_EAGAIN))
+    return int(t.value) if s == LRP_OK else None
+
+
+def lrp_poll(server, ticket: int):
+    """lrp_result once finished, else None."""
+    r = lrp_result()
+    s = _check(_lib.lrp_poll(server, ctypes.c_uint64(ticket), ctypes.byref(r)), "lrp_poll", (LRP_OK, LRP_EAGAIN))
+    return r if s == LRP_OK else None
+
+
+def lrp_wait(server, ticket: int, timeout_us: int):
+    r = lrp_result()
+    s = _check(_lib.lrp_wait(server, ctypes.c_uint64(ticket), ctypes.byref(r), int(timeout_us)), "lrp_wait",
+               (LRP_OK, LRP_ETIMEDOUT))
+    return r if s == LRP_OK else None
+
+
+def lrp_server_get_stats(server) -> lrp_server_stats:
+    st = lrp_server_stats()
+    _check(_lib.lrp_server_get_stats(server, ctypes.byref(st)), "lrp_server_get_stats")
+    return st
+
+
+def lrp_server_reset_stats(server) -> None:
+    _check(_lib.lrp_server_reset_stats(server), "lrp_server_reset_stats")
+
+
+def lrp_server_destroy(server) -> None:
+    _check(_lib.lrp_server_destroy(server), "lrp_server_destroy")
 
 
 def lrp_warm_create(plan):
@@ -214,4 +311,4 @@ def lrp_plan_reset_stats(plan) -> None:
     _check(_lib.lrp_plan_reset_stats(plan), "lrp_plan_reset_stats")
 
 
-from .api import Plan, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401
+from .api import Plan, Server, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401

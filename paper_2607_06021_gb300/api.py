@@ -10,7 +10,9 @@ from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGE
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
                lrp_plan_set_trace, lrp_plan_trace,
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
-               lrp_warm_destroy, lrp_warm_reset)
+               lrp_warm_destroy, lrp_warm_reset, lrp_poll, lrp_request, lrp_server_create,
+               lrp_server_default_opts, lrp_server_destroy, lrp_server_get_stats, lrp_server_reset_stats,
+               lrp_submit, lrp_wait)
 
 
 def colmajor(x: torch.Tensor) -> torch.Tensor:
@@ -176,4 +178,70 @@ def dst1(X: torch.Tensor, stream=None) -> torch.Tensor:
     return Y
 
 
-__all__ = ["Plan", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
+__all__ = ["Plan", "Server", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
+
+
+class Server:
+    """Request server (host factors in, host factors out); see lrp_server_create."""
+
+    def __init__(self, memory_cap_bytes: int | None = None, lanes: int = 2, max_batch: int = 64,
+                 max_queue: int = 65536, warm_capacity: int = 64):
+        o = lrp_server_default_opts()
+        if memory_cap_bytes is not None:
+            o.memory_cap_bytes = int(memory_cap_bytes)
+        o.lanes, o.max_batch, o.max_queue, o.warm_capacity = lanes, max_batch, max_queue, warm_capacity
+        self.handle = lrp_server_create(o)
+        self._outputs = {}
+
+    def submit(self, U_f, s_f, V_f, tol: float, max_rank: int, precision: str = "mixed", warm_key: int = 0):
+        """Ticket, or None when the server is full.  U_f, V_f: n x r_f host arrays."""
+        import numpy as np
+        U_f = np.asfortranarray(U_f, dtype=np.float64)
+        V_f = np.asfortranarray(V_f, dtype=np.float64)
+        s_f = np.ascontiguousarray(s_f, dtype=np.float64)
+        n, r_f = U_f.shape
+        U = np.empty((n, max_rank), order="F")
+        S = np.empty(max_rank)
+        V = np.empty((n, max_rank), order="F")
+        req = lrp_request()
+        req.n, req.r_f, req.max_rank, req.tol = n, r_f, max_rank, float(tol)
+        req.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
+        req.warm_key = int(warm_key)
+        req.U_f, req.s_f, req.V_f = U_f.ctypes.data, s_f.ctypes.data, V_f.ctypes.data
+        req.U, req.S, req.V = U.ctypes.data, S.ctypes.data, V.ctypes.data
+        t = lrp_submit(self.handle, req)
+        if t is not None:
+            self._outputs[t] = (U, S, V)
+        return t
+
+    def _take(self, t, r):
+        U, S, V = self._outputs.pop(t)
+        k = r.rank
+        return U[:, :k], S[:k], V[:, :k], {f: getattr(r, f) for f, _ in r._fields_}
+
+    def poll(self, ticket: int):
+        r = lrp_poll(self.handle, ticket)
+        return None if r is None else self._take(ticket, r)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        r = lrp_wait(self.handle, ticket, int(timeout_s * 1e6))
+        return None if r is None else self._take(ticket, r)
+
+    def stats(self) -> dict:
+        st = lrp_server_get_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def reset_stats(self) -> None:
+        lrp_server_reset_stats(self.handle)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            lrp_server_destroy(self.handle)
+            self.handle = None
+            self._outputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dst.cu", "tall.cu", "core.cu", "refine.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["dst.cu", "tall.cu", "core.cu", "refine.cu", "solver.cu", "noalloc.cu", "server.cu"]
 
 
 def nvcc() -> str:
@@ -40,7 +40,7 @@ def build(verbose: bool = False, extra=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-cudart", "shared",
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-cudart", "shared", "-lpthread",
            "-Xlinker", "-rpath", "-Xlinker", cudalib]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:

@@ -86,6 +86,7 @@ lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc
   fwd_ldi = arena.get<int64_t>((size_t)2 * d.B);
   fwd_ldo = arena.get<int64_t>((size_t)2 * d.B);
   if (!arena.ok()) return set_error(LRP_ENOMEM, "workspace allocation failed");
+  if (arena.measure) return LRP_OK;
   T* ub[2] = {U[0], U[1]};
   LRP_CUDA(cudaMemcpy(ubufs, ub, sizeof(ub), cudaMemcpyHostToDevice));
   return LRP_OK;
@@ -240,6 +241,11 @@ extern "C" lrp_status lrp_plan_reset_stats(lrp_plan_t p) {
 void* DeviceArena::raw(size_t bytes) {
   if (failed) return nullptr;
   bytes = (bytes + 255) & ~(size_t)255;
+  if (measure) {
+    // sizing pass: count the bytes, hand out a placeholder that is never used
+    total += bytes;
+    return reinterpret_cast<void*>((uintptr_t)256);
+  }
   void* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     failed = true;
@@ -292,9 +298,8 @@ extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   return LRP_OK;
 }
 
-extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts) {
-  if (!out) return set_error(LRP_EINVAL, "out is NULL");
-  *out = nullptr;
+// Validated options and every size of the plan (no device work).
+static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts) {
   lrp_opts o;
   lrp_default_opts(&o);
   if (opts) o = *opts;
@@ -309,9 +314,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
   if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
-
-  lrp_plan_s* p = new (std::nothrow) lrp_plan_s();
-  if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
+  if (!fp64 && o.refine_steps != 1) return set_error(LRP_EINVAL, "refine_steps must be 1 (one refinement step is built)");
   p->n = n;
   p->tol = tol;
   p->mixed_inner_tol = 1e-4;
@@ -343,19 +346,18 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     d.cand_blocks = (int)((n + rows - 1) / rows);
   }
   d.cand_per_block = M;
-  if (cudaGetDevice(&p->device) != cudaSuccess) {
-    delete p;
-    return set_error(LRP_ECUDA, "no CUDA device");
-  }
-  {
-    lrp_status cs_ = ensure_configured(p->device);
-    if (cs_ != LRP_OK) {
-      delete p;
-      return cs_;
-    }
-  }
+  if (!fp64 && d.M < d.RF + 2) return set_error(LRP_EINVAL, "mixed precision needs m_cap >= max_rhs_rank + 2");
+  return LRP_OK;
+}
+
+// Every arena allocation of the plan, in one fixed order (also run as a
+// sizing pass by lrp_plan_estimate_bytes).
+static lrp_status plan_layout(lrp_plan_s* p) {
+  const PlanDims& d = p->dims;
+  const bool fp64 = (p->opts.precision == LRP_FP64);
+  const int64_t n = p->n;
+  const int max_rank = p->r_max;
   lrp_status s = LRP_OK;
-  cudaStream_t st0 = nullptr;
   p->st = p->arena.get<SolveState>((size_t)d.B);
   p->lam64 = p->arena.get<double>((size_t)d.n);
   p->lam32 = p->arena.get<float>((size_t)d.n);
@@ -375,9 +377,45 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (s == LRP_OK) s = p->w64.allocate(d, p->arena, d.RF);
   // the FP32 workspace also holds the recompressed residual (up to m_cap columns)
   if (s == LRP_OK && !fp64) s = p->w32.allocate(d, p->arena, d.RF > d.M ? d.RF : d.M);
-  if (s == LRP_OK && !fp64 && d.M < d.RF + 2) s = set_error(LRP_EINVAL, "mixed precision needs m_cap >= max_rhs_rank + 2");
-  if (s == LRP_OK && !fp64 && o.refine_steps != 1)
-    s = set_error(LRP_EINVAL, "refine_steps must be 1 (one refinement step is built)");
+  return s;
+}
+
+extern "C" lrp_status lrp_plan_estimate_bytes(int64_t n, double tol, int32_t max_rank, const lrp_opts* opts,
+                                              size_t* bytes) {
+  if (!bytes) return set_error(LRP_EINVAL, "bytes is NULL");
+  *bytes = 0;
+  lrp_plan_s* p = new (std::nothrow) lrp_plan_s();
+  if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
+  p->arena.measure = true;
+  lrp_status s = plan_setup_host(p, n, tol, max_rank, opts);
+  if (s == LRP_OK) s = plan_layout(p);
+  if (s == LRP_OK) *bytes = p->arena.total;
+  delete p;
+  return s;
+}
+
+extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts) {
+  if (!out) return set_error(LRP_EINVAL, "out is NULL");
+  *out = nullptr;
+  lrp_plan_s* p = new (std::nothrow) lrp_plan_s();
+  if (!p) return set_error(LRP_ENOMEM, "host allocation failed");
+  lrp_status s = plan_setup_host(p, n, tol, max_rank, opts);
+  if (s != LRP_OK) {
+    delete p;
+    return s;
+  }
+  const PlanDims& d = p->dims;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return set_error(LRP_ECUDA, "no CUDA device");
+  }
+  s = ensure_configured(p->device);
+  if (s != LRP_OK) {
+    delete p;
+    return s;
+  }
+  cudaStream_t st0 = nullptr;
+  s = plan_layout(p);
   if (s == LRP_OK) {
     p->tw64 = dst_make_twiddles(n + 1, true, st0);
     p->tw32 = dst_make_twiddles(n + 1, false, st0);

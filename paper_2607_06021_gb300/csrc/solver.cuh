@@ -16,6 +16,7 @@ struct DeviceArena {
   std::vector<void*> blocks;
   size_t total = 0;
   bool failed = false;
+  bool measure = false;  // sizing pass: count bytes, allocate nothing
   void* raw(size_t bytes);
   template <typename T>
   T* get(size_t count) {

@@ -51,3 +51,37 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(pkg.lrp_opts) == 40
     assert ctypes.sizeof(pkg.lrp_info) == 64
     assert ctypes.sizeof(pkg.lrp_problem) == 104
+    assert ctypes.sizeof(pkg.lrp_server_opts) == 24
+    assert ctypes.sizeof(pkg.lrp_request) == 88
+    assert ctypes.sizeof(pkg.lrp_result) == 32
+    assert ctypes.sizeof(pkg.lrp_server_stats) == 96
+
+
+def test_plan_estimate_is_host_only_and_linear_in_batch():
+    # Sizing runs without a device: the arena grows by the same amount per
+    # batch slot, and mixed precision adds an FP32 workspace.
+    pkg = pytest.importorskip("paper_2607_06021_gb300")
+    o = pkg.lrp_default_opts()
+    o.max_rhs_rank, o.m_cap = 20, 64
+    sizes = []
+    for b in (1, 2, 3, 8):
+        o.batch = b
+        sizes.append(pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o))
+    per = sizes[1] - sizes[0]
+    # linear up to the 256-byte alignment of each of the arena's allocations
+    assert per > 0 and abs((sizes[2] - sizes[1]) - per) <= 64 * 256
+    assert abs((sizes[3] - sizes[0]) - 7 * per) <= 64 * 256
+    # the five n x m_cap FP64 blocks per side dominate one slot
+    assert per >= 2 * 5 * 4096 * 64 * 8
+    o.batch, o.precision = 1, pkg.LRP_MIXED
+    assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) > sizes[0]
+    with pytest.raises(pkg.LrpError):
+        pkg.lrp_plan_estimate_bytes(4000, 1e-8, 64, o)
+
+
+def test_request_footprint_formula():
+    pkg = pytest.importorskip("paper_2607_06021_gb300")
+    # 8 n (2 r_f + 4 m_cap + 2 max_rank), m_cap = min(2 max_rank + ceil8(r_f), 256)
+    assert pkg.lrp_request_footprint(4095, 20, 64) == 8 * 4095 * (40 + 4 * 152 + 128)
+    assert pkg.lrp_request_footprint(262143, 48, 128) == 8 * 262143 * (96 + 4 * 256 + 256)
+    assert pkg.lrp_request_footprint(255, 0, 8) == 0
