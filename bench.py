@@ -35,7 +35,11 @@ M_CAP = 64  # index-set capacity; sets reach at most ~35 on this workload (DESIG
 WORKLOAD = ("n=4095 (h=1/4096), RHS rank 20 = 16 seeded Gaussians + 4 eigenfunctions "
             "(p,q in 1..64), tol 1e-8, max rank 64, index-set capacity 64")
 METRIC = "Poisson solves/s & p50/p99 latency at rel err<=1e-6, mixed vs plain FP64"
-FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA throughput of this GB300 pool ("Peaks")
+# ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
+# FP64 4 flop/clk/SM (2 FMA), FP32 256 flop/clk/SM (128 lanes x FMA).
+SMS, SM_GHZ = 152, 2.070
+FP64_PEAK_TFLOPS = SMS * 4 * SM_GHZ / 1e3
+FP32_PEAK_TFLOPS = SMS * 256 * SM_GHZ / 1e3
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -50,6 +54,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="requests of the serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-kmax", type=int, default=14, help="largest n = 2^k - 1 of the stream")
+    ap.add_argument("--mixed-sizes", type=int, default=512, help="solves of the mixed-size batch (0: skip)")
     return ap.parse_args()
 
 
@@ -256,10 +265,13 @@ def gpu_arm(args, rank, world, local_rank, precisions):
     return results, rhss, hbm_peak, peak_src
 
 
-# Kernel classes whose time is bounded by arithmetic rather than HBM: in the FP64
-# path every tall product runs on the FP64 pipe; in the mixed path the Gram
-# partials of the ill-conditioned first CholeskyQR pass and the refinement stay FP64.
-ALU_CLASSES = {"fp64": {"gram", "gemm", "cross", "reduce"}, "mixed": {"gram"}}
+# Kernel classes whose time is bounded by arithmetic rather than HBM, with the
+# pipe that bounds them.  FP64 path: every tall product on the FP64 pipe.  Mixed
+# path: the FP32 iterations' products on the FP32 pipe, the ill-conditioned first
+# CholeskyQR pass (FP64 accumulation) and the refinement's products on FP64.
+ALU_CLASSES = {"fp64": {"gram": "fp64", "gemm": "fp64", "cross": "fp64", "reduce": "fp64"},
+               "mixed": {"gram": "fp64", "gemm": "fp64", "gram_f32": "fp32", "gemm_f32": "fp32", "cross": "fp32"}}
+ALU_PEAKS = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS}
 
 
 def roofline(res, prec, hbm_peak, peak_src):
@@ -273,9 +285,12 @@ def roofline(res, prec, hbm_peak, peak_src):
     if ms <= 0 or launches <= 0:
         return None
     if name in ALU_CLASSES[prec]:
+        pipe = ALU_CLASSES[prec][name]
+        peak = ALU_PEAKS[pipe]
         achieved = flops / (ms / 1e3) / 1e12
-        out = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "measured FP64 FMA probe (DESIGN.md)"}
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "peak_source": f"{pipe.upper()} pipe: 152 SMs x 2070 MHz x "
+                              f"{'4' if pipe == 'fp64' else '256'} flop/clk/SM"}
     else:
         achieved = nbytes / (ms / 1e3) / 1e9
         out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -284,6 +299,129 @@ def roofline(res, prec, hbm_peak, peak_src):
                 "algorithmic_per_launch": (flops if out["bound"] == "alu" else nbytes) / launches,
                 "traffic": None})
     return out
+
+
+def class_rooflines(res, prec, hbm_peak):
+    """Every kernel class with algorithmic work, against its own bound."""
+    out = {}
+    for name, (launches, ms, flops, nbytes) in res["kernels"].items():
+        if name == "all" or ms <= 0 or flops + nbytes <= 0:
+            continue
+        if name in ALU_CLASSES[prec]:
+            peak = ALU_PEAKS[ALU_CLASSES[prec][name]]
+            out[name] = {"bound": "alu_" + ALU_CLASSES[prec][name], "ms": round(ms, 3),
+                         "frac": round(flops / (ms / 1e3) / 1e12 / peak, 4)}
+        else:
+            out[name] = {"bound": "hbm", "ms": round(ms, 3), "frac": round(nbytes / (ms / 1e3) / 1e9 / hbm_peak, 4)}
+    return out
+
+
+def serving_stream(args, rank):
+    """Poisson arrivals of independent requests through the request server:
+    n = 2^k - 1 with k uniform in 8..kmax, r_f uniform in 2..48 Gaussians, 80%
+    mixed precision at tol 1e-6 and 20% FP64 at tol 1e-10 (rank cap 64), 10% of
+    requests perturbed repeats of an earlier one that reuse its warm-start key.
+    Latency runs from the request's arrival time to its completion."""
+    import numpy as np
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+    rng = np.random.default_rng(7 + rank)
+    R = args.serve_requests
+    specs = []
+    for i in range(R):
+        if i > 0 and rng.random() < 0.10:
+            j = int(rng.integers(0, i))
+            while specs[j]["repeat_of"] >= 0:
+                j = specs[j]["repeat_of"]
+            specs[j]["warm_key"] = j + 1
+            s = dict(specs[j], repeat_of=j, warm_key=j + 1, pert=int(rng.integers(1 << 30)))
+        else:
+            k = int(rng.integers(8, args.serve_kmax + 1))
+            mixed = rng.random() < 0.8
+            s = {"n": (1 << k) - 1, "r_f": int(rng.integers(2, 49)), "seed": int(rng.integers(1 << 30)),
+                 "prec": "mixed" if mixed else "fp64", "tol": 1e-6 if mixed else 1e-10, "repeat_of": -1,
+                 "warm_key": 0, "pert": 0}
+        specs.append(s)
+    rhss = []
+    for s in specs:
+        base = li.gaussian_eigen_rhs(s["n"], s["seed"], s["r_f"])
+        rhss.append(li.perturb_amplitudes(base, s["pert"]) if s["repeat_of"] >= 0 else base)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=R)
+    arrivals = np.cumsum(gaps)
+    sv = lrp.Server(lanes=2, max_batch=32, warm_capacity=64)
+    # warm the server's plans on one request per bucket (untimed)
+    seen = set()
+    for s, r in zip(specs, rhss):
+        key = (s["n"], s["prec"], (s["r_f"] + 63) // 64)
+        if key in seen:
+            continue
+        seen.add(key)
+        sv.wait(sv.submit(r.U, r.s, r.V, s["tol"], 64, s["prec"]), 600.0)
+    sv.reset_stats()
+    tickets = [None] * R
+    delay_us = np.zeros(R)
+    t0 = time.perf_counter()
+    for i, (s, r) in enumerate(zip(specs, rhss)):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        while True:
+            t = sv.submit(r.U, r.s, r.V, s["tol"], 64, s["prec"], warm_key=s["warm_key"])
+            if t is not None:
+                break
+            time.sleep(1e-4)  # server full: retry
+        tickets[i] = t
+        delay_us[i] = max(0.0, (time.perf_counter() - t0 - arrivals[i]) * 1e6)
+    lat, warm_hits, statuses = np.zeros(R), 0, {}
+    for i, t in enumerate(tickets):
+        res = sv.wait(t, 600.0)
+        info = res[3]
+        lat[i] = info["latency_us"] + delay_us[i]
+        warm_hits += info["warm_used"]
+        statuses[info["status"]] = statuses.get(info["status"], 0) + 1
+    wall = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    return {"requests": R, "rate_per_s": args.serve_rate, "wall_s": round(wall, 3),
+            "throughput_solves_per_s": R / wall,
+            "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+            "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,
+            "status_counts": {lrp.status_string(k): v for k, v in statuses.items()},
+            "workload": f"n=2^k-1, k~U{{8..{args.serve_kmax}}}, r_f~U{{2..48}} Gaussians, 80% mixed/1e-6, "
+                        "20% FP64/1e-10, rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
+                        "latency from arrival to completion, plans warmed per bucket beforehand"}
+
+
+def mixed_sizes_batch(args, rank):
+    """One batch of independent solves of mixed sizes through the request server:
+    n uniform over {511, 1023, 2047, 4095, 8191}, r_f uniform in 2..24
+    Gaussians, mixed precision at tol 1e-6, all submitted at once."""
+    import numpy as np
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+    rhss = li.batch_mixed_sizes(args.mixed_sizes, seed=11 + rank)
+    sv = lrp.Server(lanes=2, max_batch=128)
+
+    def run():
+        t0 = time.perf_counter()
+        ts = [sv.submit(r.U, r.s, r.V, 1e-6, 64, "mixed") for r in rhss]
+        out = [sv.wait(t, 600.0) for t in ts]
+        return time.perf_counter() - t0, out
+
+    run()  # plans created and graphs captured (untimed)
+    walls = []
+    for _ in range(3):
+        w, out = run()
+        walls.append(w)
+    sv.close()
+    w = statistics.median(walls)
+    ns = sorted({r.n for r in rhss})
+    return {"solves": len(rhss), "wall_s": round(w, 4), "solves_per_s": len(rhss) / w,
+            "iterations_mean": float(np.mean([o[3]["iterations"] for o in out])),
+            "workload": f"n uniform over {ns}, r_f~U{{2..24}} Gaussians, mixed precision, tol 1e-6, rank cap 64; "
+                        "host factors in, host factors out, median of 3 runs"}
 
 
 def cpu_baseline(rhss, seconds, gpu_results=None):
@@ -391,9 +529,14 @@ def main():
     if "e2e" in res:
         line["e2e"] = res["e2e"]
     line["roofline"] = roofline(res, head, hbm_peak, peak_src)
+    line["class_roofline"] = class_rooflines(res, head, hbm_peak)
     line["kernel_ms"] = {k: round(v[1], 3) for k, v in res["kernels"].items()}
     line["latency_bound_ms"] = {k: round(v[1], 3) for k, v in res["kernels"].items()
                                 if k != "all" and v[2] + v[3] == 0 and v[1] > 0}
+    if args.mixed_sizes > 0:
+        line["mixed_sizes_batch"] = mixed_sizes_batch(args, rank)
+    if args.serve_requests > 0:
+        line["serving"] = serving_stream(args, rank)
     if not args.no_cpu and world == 1:
         cb, errs = cpu_baseline(rhss, args.cpu_seconds, results)
         line["cpu_baseline"] = cb

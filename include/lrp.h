@@ -222,7 +222,7 @@ typedef enum lrp_kernel_class {
   LRP_K_CROSS = 1,     /* sampled columns/rows of the transformed solution */
   LRP_K_GRAM = 2,      /* per-block partial Gram / cross-Gram products, FP64 accumulation */
   LRP_K_REDUCE = 3,    /* reduction of the Gram partials */
-  LRP_K_GEMM = 4,      /* tall-skinny n x m times m x m' products */
+  LRP_K_GEMM = 4,      /* tall-skinny n x m times m x m' products on FP64 data */
   LRP_K_LEVERAGE = 5,  /* leverage scores and block top-c */
   LRP_K_CHOL = 6,      /* small Cholesky / triangular inverse per problem */
   LRP_K_CORE = 7,      /* small pseudoinverse / SVD core per problem */
@@ -231,7 +231,8 @@ typedef enum lrp_kernel_class {
   LRP_K_OTHER = 10,    /* setup, finalize, counters */
   LRP_K_REFINE = 11,   /* mixed precision: residual/sum assembly and recompression cores */
   LRP_K_GRAM_F32 = 12, /* partial Gram products with FP32 accumulation (FP32 iterations) */
-  LRP_K_COUNT = 13
+  LRP_K_GEMM_F32 = 13, /* tall-skinny products on FP32 data (FP32 iterations) */
+  LRP_K_COUNT = 14
 } lrp_kernel_class;
 
 /*
@@ -289,7 +290,7 @@ lrp_status lrp_plan_reset_stats(lrp_plan_t plan);
  * problems of varying n, precision and tolerance (one GPU, one process).
  * Admission: each request's working set is estimated as
  * 8 n (2 r_f + 4 m_cap + 2 max_rank) bytes (m_cap = min(2 max_rank + r_f', 256),
- * r_f' = r_f rounded up to a multiple of 8); a request is refused with
+ * r_f' = r_f rounded up to a multiple of 64); a request is refused with
  * LRP_ECAPACITY when it alone exceeds the memory cap, and with LRP_EAGAIN when
  * the queued and running requests' estimates plus its own would exceed the cap
  * or the queue is full (retry later).  Scheduling: worker lanes (one host thread

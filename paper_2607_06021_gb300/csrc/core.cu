@@ -56,7 +56,7 @@ __device__ inline void acct_cholqr3(double* row, double n, double m0, double m1,
       acct_add(row, LRP_K_GRAM, 3.0 * gf, 3.0 * gb);
     }
     acct_add(row, LRP_K_REDUCE, 3.0 * NB * m * (m + 1.0) / 2.0, 3.0 * (NB + 1.0) * m * (m + 1.0) / 2.0 * 8.0);
-    acct_add(row, LRP_K_GEMM, 2.0 * n * m * (m + 1.0), 2.0 * 2.0 * n * m * w);
+    acct_add(row, w == 4.0 ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * n * m * (m + 1.0), 2.0 * 2.0 * n * m * w);
   }
 }
 
@@ -64,7 +64,7 @@ __device__ void acct_setup(double* row, int n_, int rf_, int NB, int w_) {
   const double n = n_, rf = rf_, w = w_;
   acct_add(row, LRP_K_DST, 2.0 * rf * dst_col_flops(n_), 2.0 * rf * n * (8.0 + w));
   acct_cholqr3(row, n, rf, rf, NB, w);
-  acct_add(row, LRP_K_GEMM, 2.0 * n * rf * (rf + 1.0), 2.0 * 2.0 * n * rf * w);  // U_{-1} = Q2 P3
+  acct_add(row, w_ == 4 ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * n * rf * (rf + 1.0), 2.0 * 2.0 * n * rf * w);  // U_{-1}
   acct_add(row, LRP_K_LEVERAGE, 2.0 * 2.0 * n * rf, 2.0 * n * rf * w);
 }
 
@@ -73,13 +73,14 @@ __device__ void acct_iteration(double* row, int n_, int p_, int q_, int r_, int 
   // side 0 columns: p = |J|; side 1 columns: q = |I|
   acct_add(row, LRP_K_CROSS, 2.0 * n * rf * (p + q), w * (2.0 * n * rf + n * (p + q) + n));
   acct_cholqr3(row, n, p, q, NB, w);
-  acct_add(row, LRP_K_GEMM, 2.0 * n * r * (p + q), w * n * (p + q + 2.0 * r));  // U_k = Q2 Bf
+  const int mcls = (w_ == 4) ? LRP_K_GEMM_F32 : LRP_K_GEMM;
+  acct_add(row, mcls, 2.0 * n * r * (p + q), w * n * (p + q + 2.0 * r));  // U_k = Q2 Bf
   acct_add(row, LRP_K_LEVERAGE, 2.0 * 2.0 * n * r, 2.0 * n * r * w);
   const int gcls = (w_ == 4) ? LRP_K_GRAM_F32 : LRP_K_GRAM;
   if (rp_ > 0) {
     acct_add(row, gcls, 2.0 * 2.0 * n * r * rp, 2.0 * (n * (r + rp) * w + NB * r * rp * 8.0));
     acct_add(row, LRP_K_REDUCE, 2.0 * NB * r * rp, 2.0 * (NB + 1.0) * r * rp * 8.0);
-    acct_add(row, LRP_K_GEMM, 2.0 * 2.0 * n * r * rp, 2.0 * n * (r + 2.0 * rp) * w);
+    acct_add(row, mcls, 2.0 * 2.0 * n * r * rp, 2.0 * n * (r + 2.0 * rp) * w);
     acct_add(row, gcls, 2.0 * n * rp * (rp + 1.0), 2.0 * (n * rp * w + NB * rp * (rp + 1.0) / 2.0 * 8.0));
     acct_add(row, LRP_K_REDUCE, 2.0 * NB * rp * (rp + 1.0) / 2.0, 2.0 * (NB + 1.0) * rp * (rp + 1.0) / 2.0 * 8.0);
   }

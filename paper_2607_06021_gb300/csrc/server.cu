@@ -58,7 +58,9 @@ struct BucketKey {
   }
 };
 
-int rf_class(int r_f) { return (r_f + 7) / 8 * 8; }
+// Right-hand-side rank class of a bucket: coarse, so that a stream of mixed
+// ranks shares few plans (the class only sizes the plan's r_f capacity).
+int rf_class(int r_f) { return (r_f + 63) / 64 * 64; }
 
 int m_cap_of(int max_rank, int rf_cap) { return std::min(2 * max_rank + rf_cap, 256); }
 

@@ -52,6 +52,12 @@ lrp_status set_error(lrp_status s, const std::string& msg) {
     if (ev0_ >= 0) (P)->stats.pending.push_back({(CLS), ev0_, (P)->stats.take(S)});                 \
   } while (0)
 
+// Kernel class of a tall product on data of type T.
+template <typename T>
+static constexpr int gemm_class() {
+  return sizeof(T) == 4 ? LRP_K_GEMM_F32 : LRP_K_GEMM;
+}
+
 template <typename T>
 lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc) {
   const int64_t nm = d.ld * d.M;
@@ -332,8 +338,8 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (M < o.max_rhs_rank) M = o.max_rhs_rank;  // the initial bases have r_f columns
   if (M < 2) M = 2;
   d.M = M;
-  // Gram partial blocks: at least 256 rows each, at most 64 blocks.
-  d.NB = (int)((n + 255) / 256);
+  // Gram partial blocks: at least 512 rows each, at most 64 blocks.
+  d.NB = (int)((n + 511) / 512);
   if (d.NB > 64) d.NB = 64;
   if (d.NB < 1) d.NB = 1;
   d.rows_per_block = (int)(((n + d.NB - 1) / d.NB + 31) / 32 * 32);
@@ -571,7 +577,7 @@ static lrp_status cholqr(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, cons
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 0, s));
   if (passes < 2) return LRP_OK;
-  LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs(X, side_stride, slot_stride), sel, P, sel, Strided<T>{w.Q1, nm, 2 * nm},
                                none, 0, s));
   // Later passes see a well-conditioned basis: FP32 data keep an FP32 Gram.
@@ -581,7 +587,7 @@ static lrp_status cholqr(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, cons
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 1, s));
   if (passes < 3) return LRP_OK;
-  LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
              launch_gemm_nn<T>(g, p->st, cs<T>(w.Q1, nm, 2 * nm), sel, P, sel, Strided<T>{w.Q2, nm, 2 * nm}, none, 0,
                                s));
   if ((st = gram_reduce<T>(p, g, cs<T>(w.Q2, nm, 2 * nm), sel, cs<T>(w.Q2, nm, 2 * nm), sel, w.part, G, true, s,
@@ -722,7 +728,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   auto init = [&](cudaStream_t s) -> lrp_status {
     lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.Fh, fm, 2 * fm, kDimRF, s);
     if (st) return st;
-    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
                launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
                                  kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
     // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
@@ -751,7 +757,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
       lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.A, nm, 2 * nm, kDimOther, s);
       if (st) return st;
       LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cp, cb, par, s));
-      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+      LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
                  launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
                                    Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
                                    none, 0, s));
@@ -763,7 +769,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
         st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
                             w.part, Gx, false, s, sizeof(T) == 8);
         if (st) return st;
-        LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+        LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
                    launch_gemm_nn<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
                                      Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
                                      Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));

@@ -31,13 +31,12 @@ constexpr int NT = 256;
 }  // namespace
 
 constexpr int kSmallGram = 64;
-constexpr int kSmallAcc = 16;
 constexpr int kSmallRows = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __restrict__ st_all, CrossArgs<T> a) {
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
-  const SolveState st = st_all[slot];
+  const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int m = st.cnt[1 - side];
   const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
@@ -110,15 +109,38 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   }
 }
 
-// One 64-row tile of Out = In * Bm (or Zsub - In * Bm) over output columns
-// [c0, c0 + TNW): 256 threads, each RI rows x 4 columns.
+// Rows of one GEMM CTA.
+constexpr int kGemmRows = 128;
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void ld(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void ld(const double* p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+};
+
+// One kGemmRows-row tile of Out = In * Bm (or Zsub - In * Bm) over output
+// columns [c0, c0 + TNW): 256 threads, each RI consecutive rows x 4
+// consecutive columns, operands read from shared memory as 4-vectors.
 template <typename T, int TNW>
 __device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
                                           T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
-                                          int r0, int c0, T (*As)[TM], T (*Bs)[64]) {
-  constexpr int TX = TNW / 4;   // threads along columns
-  constexpr int TY = NT / TX;   // threads along rows
-  constexpr int RI = TM / TY;   // rows per thread
+                                          int r0, int c0, T (*As)[kGemmRows + 4], T (*Bs)[64 + 4]) {
+  constexpr int TX = TNW / 4;           // threads along columns
+  constexpr int TY = NT / TX;           // threads along rows
+  constexpr int RI = kGemmRows / TY;    // rows per thread
+  static_assert(RI % 4 == 0, "rows per thread: whole 4-vectors");
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   T acc[RI][4];
 #pragma unroll
@@ -127,15 +149,13 @@ __device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict
     for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
   for (int k0 = 0; k0 < mi; k0 += TK) {
 #pragma unroll
-    for (int q = 0; q < (TK * TM) / NT; ++q) {
+    for (int q = 0; q < (TK * kGemmRows) / NT; ++q) {
       const int e = tid + NT * q;
-      const int kk = e / TM, i = e % TM;
+      const int kk = e / kGemmRows, i = e % kGemmRows;
       const int row = r0 + i, k = k0 + kk;
       As[kk][i] = (row < g.n && k < mi) ? X[(int64_t)k * g.ld + row] : (T)0;
     }
-#pragma unroll
-    for (int q = 0; q < (TK * TNW) / NT; ++q) {
-      const int e = tid + NT * q;
+    for (int e = tid; e < TK * TNW; e += NT) {
       const int kk = e % TK, c = e / TK;
       const int k = k0 + kk, col = c0 + c;
       Bs[kk][c] = (k < mi && col < mo) ? (T)Bm[(int64_t)col * g.M + k] : (T)0;
@@ -145,9 +165,13 @@ __device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict
     for (int kk = 0; kk < TK; ++kk) {
       T av[RI], bv[4];
 #pragma unroll
-      for (int i = 0; i < RI; ++i) av[i] = As[kk][ty + TY * i];
+      for (int i = 0; i < RI; i += 4) {
+        T v[4];
+        Vec4<T>::ld(&As[kk][ty * RI + i], v);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TX * j];
+        for (int u = 0; u < 4; ++u) av[i + u] = v[u];
+      }
+      Vec4<T>::ld(&Bs[kk][tx * 4], bv);
 #pragma unroll
       for (int i = 0; i < RI; ++i)
 #pragma unroll
@@ -156,21 +180,21 @@ __device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < RI; ++i) {
-    const int row = r0 + ty + TY * i;
-    if (row >= g.n) continue;
+  for (int j = 0; j < 4; ++j) {
+    const int col = c0 + tx * 4 + j;
+    if (col >= mo) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int col = c0 + tx + TX * j;
-      if (col >= mo) continue;
+    for (int i = 0; i < RI; ++i) {
+      const int row = r0 + ty * RI + i;
+      if (row >= g.n) continue;
       const int64_t o = (int64_t)col * g.ld + row;
       O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
     }
   }
 }
 
-// One launch for every output width: a CTA owns 64 rows and runs one 32-wide
-// tile when mo <= 32, else 64-wide tiles over all output columns.
+// One launch for every output width: a CTA owns kGemmRows rows and runs one
+// 32-wide tile when mo <= 32, else 64-wide tiles over all output columns.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
@@ -179,10 +203,10 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
-  const int r0 = blockIdx.x * TM;
+  const int r0 = blockIdx.x * kGemmRows;
   if (r0 >= g.n || mo < 1) return;
-  __shared__ T As[TK][TM];
-  __shared__ T Bs[TK][64];
+  __shared__ __align__(16) T As[TK][kGemmRows + 4];
+  __shared__ __align__(16) T Bs[TK][64 + 4];
   const T* X = in.at(slot, side);
   const double* Bm = bm.at(slot, side);
   T* O = out.at(slot, side);
@@ -194,9 +218,10 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   }
 }
 
-// Tiled FP64 Gram partials for widths above kSmallGram: the CTA loops over the
-// 64 x 64 output tiles (upper tiles only when symmetric) of its row block.
-template <typename T>
+// Tiled Gram partials for widths above kSmallGram: the CTA loops over the
+// 64 x 64 output tiles (upper tiles only when symmetric) of its row block,
+// accumulating in TA.
+template <typename T, typename TA>
 __device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* __restrict__ Y, int mx, int my,
                            int rbeg, int rend, double* __restrict__ P, bool symmetric, unsigned char* smem) {
   T (*As)[TM + 1] = reinterpret_cast<T (*)[TM + 1]>(smem);
@@ -204,11 +229,11 @@ __device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int a0 = 0; a0 < mx; a0 += TM) {
     for (int b0 = symmetric ? a0 : 0; b0 < my; b0 += TN) {
-      double acc[4][4];
+      TA acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = (TA)0;
       for (int r = rbeg; r < rend; r += TKG) {
 #pragma unroll
         for (int q = 0; q < (TKG * TM) / NT; ++q) {
@@ -221,11 +246,11 @@ __device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* 
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < TKG; ++kk) {
-          double av[4], bv[4];
+          TA av[4], bv[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) av[i] = (double)As[kk][ty + 16 * i];
+          for (int i = 0; i < 4; ++i) av[i] = (TA)As[kk][ty + 16 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) bv[j] = (double)Bs[kk][tx + 16 * j];
+          for (int j = 0; j < 4; ++j) bv[j] = (TA)Bs[kk][tx + 16 * j];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -240,27 +265,63 @@ __device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int b = b0 + tx + 16 * j;
-          if (b < my) P[(int64_t)b * g.M + a] = acc[i][j];
+          if (b < my) P[(int64_t)b * g.M + a] = (double)acc[i][j];
         }
       }
     }
   }
 }
 
-// Gram partials for small column counts (mx, my <= kSmallGram): each thread
-// owns up to kSmallAcc output entries (upper triangle only when symmetric) and
-// accumulates them in FP64 over the row block, read through shared memory in
-// chunks of 32 rows.  Exits when either count exceeds kSmallGram (the tiled
-// kernel then does the work).
-// TA is the accumulation type: FP64 for every Gram of the FP64 path and for the
-// first (ill-conditioned) CholeskyQR pass of the FP32 iterations, FP32 for the
-// FP32 iterations' later passes and cross-Grams.
-template <typename T, typename TA>
+// TS consecutive elements of a shared-memory row (16-byte aligned for TS = 4
+// floats or 2 doubles, 32-byte for 4 doubles).
+template <typename TA, int TS>
+__device__ __forceinline__ void load_ts(const TA* p, TA (&v)[TS]) {
+  if constexpr (sizeof(TA) == 4 && TS == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else if constexpr (sizeof(TA) == 8 && TS == 2) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x, v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < TS; ++u) v[u] = p[u];
+  }
+}
+
+// Output tile t -> (ia, ib): upper tiles column by column when symmetric.
+__device__ __forceinline__ void tile_coords(int t, bool symmetric, int tx, int& ia, int& ib) {
+  if (symmetric) {
+    ib = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((ib + 1) * (ib + 2) / 2 <= t) ++ib;
+    while (ib * (ib + 1) / 2 > t) --ib;
+    ia = t - ib * (ib + 1) / 2;
+  } else {
+    ia = t % tx;
+    ib = t / tx;
+  }
+}
+
+// Gram partials for small column counts (mx, my <= kSmallGram), register
+// tiled: the output is cut into TS x TS tiles (upper tiles only when
+// symmetric).  With at most NT tiles, every tile has one thread in each of
+// NT / ntile row groups, which split the rows of each shared-memory chunk and
+// add their sums in shared memory at the end; with more tiles than threads a
+// thread owns up to TPT tiles over all rows.  Exits to the tiled kernel when
+// either count exceeds kSmallGram.  TS = 4 for FP32 accumulation (16 FMAs per
+// two 16-byte loads); TS = 2 with four tiles per thread for FP64 accumulation,
+// whose pipe is the bound and which wastes fewer FMAs on diagonal and padding
+// entries.  TA is the accumulation type: FP64 for every Gram of the FP64 path
+// and for the first (ill-conditioned) CholeskyQR pass of the FP32 iterations,
+// FP32 for the FP32 iterations' later passes and cross-Grams.
+template <typename T, typename TA, int TS, int TPT>
 __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState* __restrict__ st_all,
                                                    Strided<const T> xs, int sel_x, Strided<const T> ys, int sel_y,
                                                    double* __restrict__ part, bool symmetric) {
+  constexpr int KC = kSmallRows;          // rows per shared-memory chunk
+  constexpr int LDS = kSmallGram + 4;     // padded row length (keeps 16-byte alignment)
+  static_assert((kSmallGram / TS) * (kSmallGram / TS) <= NT * TPT, "tiles per thread");
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
-  const SolveState st = st_all[slot];
+  const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
   if (mx < 1 || my < 1) return;
@@ -269,69 +330,107 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
   const int rend = min(g.n, rbeg + g.rows_per_block);
   const T* X = xs.at(slot, side);
   const T* Y = ys.at(slot, side);
-  __shared__ __align__(16) unsigned char gsm[2 * kSmallRows * (kSmallGram + 1) * sizeof(double)];
+  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+  // the chunk is staged in the accumulation type: each element is converted once
+  constexpr size_t kTileBytes = 2 * KC * LDS * sizeof(TA);
+  constexpr size_t kRedBytes = (size_t)NT * TS * TS * sizeof(TA);
+  constexpr size_t kFallBytes = (size_t)TKG * (TM + 1 + TN + 1) * sizeof(T);
+  constexpr size_t kSmem = kTileBytes > kRedBytes ? (kTileBytes > kFallBytes ? kTileBytes : kFallBytes)
+                                                  : (kRedBytes > kFallBytes ? kRedBytes : kFallBytes);
+  __shared__ __align__(16) unsigned char gsm[kSmem];
   if (mx > kSmallGram || my > kSmallGram) {
-    double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
-    gram_tiled<T>(g, X, Y, mx, my, rbeg, rend, P, symmetric, gsm);
+    gram_tiled<T, TA>(g, X, Y, mx, my, rbeg, rend, P, symmetric, gsm);
     return;
   }
-  TA (*Xs)[kSmallGram + 1] = reinterpret_cast<TA (*)[kSmallGram + 1]>(gsm);
-  TA (*Ys)[kSmallGram + 1] = reinterpret_cast<TA (*)[kSmallGram + 1]>(gsm + sizeof(TA) * kSmallRows * (kSmallGram + 1));
-  const int tid = threadIdx.x;
-  const int nent = symmetric ? mx * (mx + 1) / 2 : mx * my;
-  int ea[kSmallAcc], eb[kSmallAcc];
-  TA acc[kSmallAcc];
-#pragma unroll
-  for (int k = 0; k < kSmallAcc; ++k) {
-    const int e = tid + NT * k;
-    int a = 0, b = 0;
-    if (e < nent) {
-      if (symmetric) {
-        b = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-        while ((b + 1) * (b + 2) / 2 <= e) ++b;
-        while (b * (b + 1) / 2 > e) --b;
-        a = e - b * (b + 1) / 2;
-      } else {
-        a = e % mx;
-        b = e / mx;
-      }
-    } else {
-      a = -1;
-    }
-    ea[k] = a;
-    eb[k] = b;
-    acc[k] = (TA)0;
-  }
+  TA (*Xs)[LDS] = reinterpret_cast<TA (*)[LDS]>(gsm);
+  TA (*Ys)[LDS] = reinterpret_cast<TA (*)[LDS]>(gsm + (size_t)KC * LDS * sizeof(TA));
   const bool same = symmetric;
-  for (int r = rbeg; r < rend; r += kSmallRows) {
-    for (int e = tid; e < kSmallRows * mx; e += NT) {
-      const int kk = e % kSmallRows, c = e / kSmallRows;
+  const int tx = (mx + TS - 1) / TS, ty = (my + TS - 1) / TS;
+  const int ntile = same ? tx * (tx + 1) / 2 : tx * ty;
+  const int G = ntile <= NT ? NT / ntile : 1;  // row groups
+  const int tid = threadIdx.x;
+  const int grp = ntile <= NT ? tid / ntile : 0;
+  const int t0 = ntile <= NT ? tid - grp * ntile : tid;
+  int ia[TPT], ib[TPT];
+  bool own[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int t = t0 + q * NT;
+    own[q] = grp < G && t < ntile && (q == 0 || ntile > NT);
+    ia[q] = ib[q] = 0;
+    if (own[q]) tile_coords(t, same, tx, ia[q], ib[q]);
+  }
+  TA acc[TPT][TS][TS];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q)
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) acc[q][i][j] = (TA)0;
+  const int wx = tx * TS, wy = ty * TS;  // padded widths (zero columns beyond mx, my)
+  for (int r = rbeg; r < rend; r += KC) {
+    for (int e = tid; e < KC * wx; e += NT) {
+      const int kk = e % KC, c = e / KC;
       const int row = r + kk;
-      Xs[kk][c] = (row < rend) ? (TA)X[(int64_t)c * g.ld + row] : (TA)0;
+      Xs[kk][c] = (row < rend && c < mx) ? (TA)X[(int64_t)c * g.ld + row] : (TA)0;
     }
     if (!same) {
-      for (int e = tid; e < kSmallRows * my; e += NT) {
-        const int kk = e % kSmallRows, c = e / kSmallRows;
+      for (int e = tid; e < KC * wy; e += NT) {
+        const int kk = e % KC, c = e / KC;
         const int row = r + kk;
-        Ys[kk][c] = (row < rend) ? (TA)Y[(int64_t)c * g.ld + row] : (TA)0;
+        Ys[kk][c] = (row < rend && c < my) ? (TA)Y[(int64_t)c * g.ld + row] : (TA)0;
       }
     }
     __syncthreads();
+    const TA(*Bsrc)[LDS] = same ? Xs : Ys;
 #pragma unroll
-    for (int k = 0; k < kSmallAcc; ++k) {
-      if (ea[k] < 0) continue;
-      const int a = ea[k], b = eb[k];
-      TA s = acc[k];
-#pragma unroll 8
-      for (int kk = 0; kk < kSmallRows; ++kk) s = fma(Xs[kk][a], same ? Xs[kk][b] : Ys[kk][b], s);
-      acc[k] = s;
+    for (int q = 0; q < TPT; ++q) {
+      if (!own[q]) continue;
+      for (int kk = grp; kk < KC; kk += G) {
+        TA av[TS], bv[TS];
+        load_ts<TA, TS>(&Xs[kk][TS * ia[q]], av);
+        load_ts<TA, TS>(&Bsrc[kk][TS * ib[q]], bv);
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+#pragma unroll
+          for (int j = 0; j < TS; ++j) acc[q][i][j] = fma(av[i], bv[j], acc[q][i][j]);
+      }
     }
     __syncthreads();
   }
-  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+  if (G == 1) {
+    // one thread per tile: write directly
 #pragma unroll
-  for (int k = 0; k < kSmallAcc; ++k)
-    if (ea[k] >= 0) P[(int64_t)eb[k] * g.M + ea[k]] = (double)acc[k];
+    for (int q = 0; q < TPT; ++q) {
+      if (!own[q]) continue;
+#pragma unroll
+      for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < TS; ++j) {
+          const int a = TS * ia[q] + i, b = TS * ib[q] + j;
+          if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = (double)acc[q][i][j];
+        }
+    }
+    return;
+  }
+  // sum the row groups' tiles (one tile per thread here): red[grp][t][TS*TS]
+  TA* red = reinterpret_cast<TA*>(gsm);
+  if (own[0]) {
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) red[((size_t)grp * ntile + t0) * TS * TS + i * TS + j] = acc[0][i][j];
+  }
+  __syncthreads();
+  for (int e = tid; e < ntile * TS * TS; e += NT) {
+    const int tt = e / (TS * TS), ij = e % (TS * TS), i = ij / TS, j = ij % TS;
+    TA v = (TA)0;
+    for (int q = 0; q < G; ++q) v += red[((size_t)q * ntile + tt) * TS * TS + ij];
+    int ta, tb;
+    tile_coords(tt, same, tx, ta, tb);
+    const int a = TS * ta + i, b = TS * tb + j;
+    if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = (double)v;
+  }
 }
 
 __global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int sel_x, int sel_y,
@@ -388,7 +487,7 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
   double* key = reinterpret_cast<double*>(smem_raw);
   int* id = reinterpret_cast<int*>(key + sort_len);
   const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
-  const SolveState st = st_all[slot];
+  const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);
   const int blk = blockIdx.x;
@@ -435,7 +534,8 @@ template <typename T>
 cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
                            Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
                            cudaStream_t s) {
-  k_gemm_nn<T><<<dim3(cdiv(g.n, TM), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
+  k_gemm_nn<T><<<dim3(cdiv(g.n, kGemmRows), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub,
+                                                                          mode);
   return cudaGetLastError();
 }
 
@@ -444,9 +544,11 @@ cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T
                         Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
                         cudaStream_t s, bool acc64) {
   if (acc64 || sizeof(T) == 8)
-    k_gram_small<T, double><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
+    k_gram_small<T, double, 2, 4><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part,
+                                                                             symmetric);
   else
-    k_gram_small<T, float><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part, symmetric);
+    k_gram_small<T, float, 4, 1><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part,
+                                                                            symmetric);
   (void)G;
   return cudaGetLastError();
 }

@@ -81,7 +81,7 @@ def test_plan_estimate_is_host_only_and_linear_in_batch():
 
 def test_request_footprint_formula():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
-    # 8 n (2 r_f + 4 m_cap + 2 max_rank), m_cap = min(2 max_rank + ceil8(r_f), 256)
-    assert pkg.lrp_request_footprint(4095, 20, 64) == 8 * 4095 * (40 + 4 * 152 + 128)
+    # 8 n (2 r_f + 4 m_cap + 2 max_rank), m_cap = min(2 max_rank + r_f rounded up to 64, 256)
+    assert pkg.lrp_request_footprint(4095, 20, 64) == 8 * 4095 * (40 + 4 * 192 + 128)
     assert pkg.lrp_request_footprint(262143, 48, 128) == 8 * 262143 * (96 + 4 * 256 + 256)
     assert pkg.lrp_request_footprint(255, 0, 8) == 0

@@ -13,8 +13,8 @@ pytestmark = pytest.mark.gpu
 
 def _bucket_plan(lrp, n, r_f, tol, max_rank, precision):
     # the server's plan for this request's bucket: r_f rounded up to a multiple
-    # of 8, m_cap = min(2 max_rank + that, 256)
-    rfc = (r_f + 7) // 8 * 8
+    # of 64, m_cap = min(2 max_rank + that, 256)
+    rfc = (r_f + 63) // 64 * 64
     return lrp.Plan(n, tol, max_rank, max_rhs_rank=rfc, m_cap=min(2 * max_rank + rfc, 256), precision=precision)
 
 
