@@ -62,7 +62,7 @@ typedef struct lrp_opts {
   int32_t precision;     /* lrp_precision, default LRP_FP64 */
   int32_t selector;      /* lrp_selector, default LRP_SEL_LEVERAGE */
   int32_t max_iter;      /* Cross-DEIM iterations, default 30 */
-  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps, default 1 */
+  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps, 1 (default) or 0 (FP32 result) */
   int32_t max_rhs_rank;  /* capacity for r_f, default 64 (<= 256) */
   int32_t batch;         /* max problems per lrp_solve_batch call, default 1 */
   int32_t m_cap;         /* index-set capacity, default min(2*max_rank + max_rhs_rank, 256) */
@@ -72,6 +72,13 @@ typedef struct lrp_opts {
 } lrp_opts;
 
 /* Per-problem report, written by the device into caller memory. */
+/* lrp_info.flags */
+#define LRP_FLAG_CONVERGED 1   /* the stop test passed (mixed: in every solve, or a stall below) */
+#define LRP_FLAG_RANK_CAPPED 2 /* r* > max_rank */
+#define LRP_FLAG_CAPACITY 4    /* an index set reached m_cap */
+#define LRP_FLAG_BAD_INPUT 8   /* non-finite data met */
+#define LRP_FLAG_STALLED 16    /* an FP32 solve stopped at its noise floor: the change stopped halving */
+
 typedef struct lrp_info {
   int32_t rank;          /* r = max(min(r*, max_rank), 1) columns written to U, V, S */
   int32_t iterations;    /* Cross-DEIM iterations taken (last solve of a refinement) */
@@ -80,7 +87,7 @@ typedef struct lrp_info {
   int32_t size_I;        /* |I| at exit */
   int32_t size_J;        /* |J| at exit */
   int32_t total_iterations; /* summed over the initial solve and refinement solves */
-  int32_t reserved0;
+  int32_t flags;         /* LRP_FLAG_* bits */
   double rho;            /* last relative change ||A_k - A_{k-1}||_F / ||A_k||_F */
   double eta_smin;       /* last min(eta1(1+eta2), eta2(1+eta1)) * S_min / ||S||_F */
   double sigma_max;      /* largest singular value of the result */

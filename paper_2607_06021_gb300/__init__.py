@@ -40,7 +40,7 @@ class lrp_info(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("r_star", ctypes.c_int32),
                 ("size_I", ctypes.c_int32), ("size_J", ctypes.c_int32),
-                ("total_iterations", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("total_iterations", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("rho", ctypes.c_double), ("eta_smin", ctypes.c_double),
                 ("sigma_max", ctypes.c_double), ("reserved1", ctypes.c_double)]
 

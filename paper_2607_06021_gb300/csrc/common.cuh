@@ -50,7 +50,10 @@ struct SolveState {
   double snorm;          // ||S_k||_F
   double snorm_prev;
   double gram_trace[2];  // trace of the pass-1 Gram (shift scale)
-  double tol;            // stop-test tolerance of the current solve
+  double tol;            // stop-test tolerance of the current solve (relative to ||S_k||)
+  double tol_abs;        // > 0: also accept changes below tol_abs in absolute terms (correction solves)
+  double rho_best;       // smallest rho of this solve after its first iteration (0: none yet)
+  int32_t stall;         // iterations since rho last fell below half of rho_best
 };
 
 enum : int32_t {
@@ -58,6 +61,7 @@ enum : int32_t {
   kFlagRankCapped = 2,
   kFlagCapacity = 4,   // index set hit m_cap
   kFlagBadInput = 8,
+  kFlagStalled = 16,   // FP32 solve stopped at its noise floor (change stopped halving)
 };
 
 // Size selectors for the generic tall kernels: which per-side dimension of

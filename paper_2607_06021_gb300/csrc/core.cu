@@ -671,9 +671,26 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
     stp->iters += 1;
     stp->total_iters += 1;
     stp->k += 1;
-    const bool conv = fmax(rho, stp->eta_smin) < stp->tol;
+    // A correction solve is done once its change is small against the solution
+    // it corrects: tol_abs / ||S_k|| (clamped to [tol, 0.1]) relative to itself.
+    double tol_eff = stp->tol;
+    if (stp->tol_abs > 0.0 && stp->snorm > 0.0) tol_eff = fmax(tol_eff, fmin(0.1, stp->tol_abs / stp->snorm));
+    const bool conv = fmax(rho, stp->eta_smin) < tol_eff;
+    // FP32 solves: once the change has failed twice in a row to halve its best
+    // value, the iteration moves only within the data's rounding noise.
+    if (p.noise_floor_stop && stp->iters >= 2) {
+      if (stp->rho_best == 0.0 || rho < 0.5 * stp->rho_best) {
+        stp->rho_best = rho;
+        stp->stall = 0;
+      } else {
+        stp->stall += 1;
+      }
+    }
     if (conv) {
       stp->flags |= kFlagConverged;
+      stp->active = 0;
+    } else if (p.noise_floor_stop && stp->stall >= 2) {
+      stp->flags |= kFlagStalled;
       stp->active = 0;
     } else if (stp->k >= p.max_iter) {
       stp->active = 0;
@@ -744,7 +761,7 @@ __global__ void k_finalize(CoreParams p, CoreBufs<T> b, DstBatch<T, double> back
     inf.size_I = stp->cnt[0];
     inf.size_J = stp->cnt[1];
     inf.total_iterations = stp->total_iters;
-    inf.reserved0 = stp->flags;
+    inf.flags = stp->flags;
     inf.rho = stp->rho;
     inf.eta_smin = stp->eta_smin;
     inf.sigma_max = s[0];

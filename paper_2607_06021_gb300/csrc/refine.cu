@@ -214,6 +214,8 @@ __global__ void k_setup_correction(RefineArgs a) {
   if (threadIdx.x == 0) {
     const int total = st->total_iters;
     const int r0 = st->r0, rf0 = st->rf0;
+    double s0n = 0.0;  // ||S0||_F = ||What0||_F of the trial solution
+    for (int t = 0; t < r0; ++t) s0n += a.s0[(int64_t)slot * a.M + t] * a.s0[(int64_t)slot * a.M + t];
     SolveState z;
     memset(&z, 0, sizeof(z));
     z.active = 1;
@@ -225,8 +227,9 @@ __global__ void k_setup_correction(RefineArgs a) {
     z.r0 = r0;
     z.total_iters = total;
     z.flags = st->flags & ~kFlagConverged;
-    z.first_converged = (st->flags & kFlagConverged) ? 1 : 0;
+    z.first_converged = (st->flags & (kFlagConverged | kFlagStalled)) ? 1 : 0;
     z.tol = a.corr_tol;
+    z.tol_abs = a.final_tol * sqrt(s0n);
     *st = z;
   }
 }
@@ -293,7 +296,7 @@ __global__ void k_final_state(RefineArgs a) {
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
   if (!st->valid || threadIdx.x != 0) return;
-  const bool conv = st->first_converged && (st->flags & kFlagConverged);
+  const bool conv = st->first_converged && (st->flags & (kFlagConverged | kFlagStalled));
   st->k = 1;
   st->iters = st->total_iters;
   st->flags = conv ? (st->flags | kFlagConverged) : (st->flags & ~kFlagConverged);

@@ -33,7 +33,8 @@ struct RefineArgs {
   int wstride;
   double* acct;                // per slot LRP_K_COUNT x {flops, bytes} (see core.cuh)
   int NB;                      // Gram partial blocks of the plan
-  double corr_tol;             // stop-test tolerance of the FP32 correction solve
+  double corr_tol;             // stop-test tolerance floor of the FP32 correction solve
+  double final_tol;            // the solve's tolerance: the correction's absolute target is final_tol ||S0||
 };
 
 // Raises the dynamic shared-memory limit of the recompression kernels (once per device).

@@ -320,7 +320,8 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
   if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
-  if (!fp64 && o.refine_steps != 1) return set_error(LRP_EINVAL, "refine_steps must be 1 (one refinement step is built)");
+  if (!fp64 && o.refine_steps != 0 && o.refine_steps != 1)
+    return set_error(LRP_EINVAL, "refine_steps must be 0 or 1 (one refinement step is built)");
   p->n = n;
   p->tol = tol;
   p->mixed_inner_tol = 1e-4;
@@ -870,6 +871,7 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.acct = p->acct;
   a.NB = d.NB;
   a.corr_tol = p->tol;
+  a.final_tol = p->tol;
   return a;
 }
 
@@ -891,15 +893,11 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
   RefineArgs ra = make_refine_args(p);
-  // The trial solution carries a relative error of about tol_in, so the
-  // correction dW needs relative accuracy tol / tol_in only (its error enters
-  // the sum scaled by ||dW|| ~ tol_in ||W||); FP32 offers no better than tol_in.
-  {
-    double ct = p->tol / tol_in;
-    if (ct < tol_in) ct = tol_in;
-    if (ct > 0.1) ct = 0.1;
-    ra.corr_tol = ct;
-  }
+  // The correction dW enters the sum at its own size ||dW|| ~ ||W - W0||, so
+  // it is done once its change is below tol ||W0|| in absolute terms (the stop
+  // test then uses tol ||S0|| / ||S_k||); FP32 resolves no better than tol_in.
+  ra.corr_tol = tol_in;
+  ra.final_tol = p->tol;
   const TallGeom& g = c64.g;
   const Strided<const double> none{nullptr, 0, 0};
   lrp_status st;
@@ -907,6 +905,8 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   if ((st = phase_forward<double>(p, p->w64, c64, count, false, s))) return st;
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
   if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
+  // Without refinement the FP32 solution is the result (truncated at tol_in).
+  if (p->opts.refine_steps == 0) return phase_finalize<float>(p, p->w32, c32, count, s);
   for (int step = 0; step < p->opts.refine_steps; ++step) {
     // Residual of the trial solution, recompressed in FP64.
     LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   }
 }
 
-// Rows of one GEMM CTA.
+// Rows of one GEMM row tile, and row tiles per CTA.
 constexpr int kGemmRows = 128;
+constexpr int kGemmTiles = 4;
 
 template <typename T>
 struct Vec4;
@@ -130,71 +131,87 @@ struct Vec4<double> {
   }
 };
 
-// One kGemmRows-row tile of Out = In * Bm (or Zsub - In * Bm) over output
-// columns [c0, c0 + TNW): 256 threads, each RI consecutive rows x 4
-// consecutive columns, operands read from shared memory as 4-vectors.
+// Out = In * Bm (or Zsub - In * Bm) for the CTA's kGemmTiles row tiles of
+// kGemmRows rows, output columns [c0, c0 + TNW).  Bm is staged in shared
+// memory in blocks of 64 rows of K (converted to T once per staging): with
+// K <= 64 one staging serves all row tiles.  Each row tile streams In through
+// shared memory in TK-deep slices: 256 threads, each RI consecutive rows x 4
+// consecutive columns, operands read as 4-vectors.
 template <typename T, int TNW>
-__device__ __forceinline__ void gemm_tile(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
-                                          T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
-                                          int r0, int c0, T (*As)[kGemmRows + 4], T (*Bs)[64 + 4]) {
+__device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
+                                           T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
+                                           int rbase, int c0, T (*As)[kGemmRows], T (*Bs)[64]) {
   constexpr int TX = TNW / 4;           // threads along columns
   constexpr int TY = NT / TX;           // threads along rows
   constexpr int RI = kGemmRows / TY;    // rows per thread
   static_assert(RI % 4 == 0, "rows per thread: whole 4-vectors");
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  T acc[RI][4];
+  const int nkb = (mi + 63) / 64;
+  for (int tile = 0; tile < kGemmTiles; ++tile) {
+    const int r0 = rbase + tile * kGemmRows;
+    if (r0 >= g.n) break;
+    T acc[RI][4];
 #pragma unroll
-  for (int i = 0; i < RI; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-  for (int k0 = 0; k0 < mi; k0 += TK) {
-#pragma unroll
-    for (int q = 0; q < (TK * kGemmRows) / NT; ++q) {
-      const int e = tid + NT * q;
-      const int kk = e / kGemmRows, i = e % kGemmRows;
-      const int row = r0 + i, k = k0 + kk;
-      As[kk][i] = (row < g.n && k < mi) ? X[(int64_t)k * g.ld + row] : (T)0;
-    }
-    for (int e = tid; e < TK * TNW; e += NT) {
-      const int kk = e % TK, c = e / TK;
-      const int k = k0 + kk, col = c0 + c;
-      Bs[kk][c] = (k < mi && col < mo) ? (T)Bm[(int64_t)col * g.M + k] : (T)0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-      T av[RI], bv[4];
-#pragma unroll
-      for (int i = 0; i < RI; i += 4) {
-        T v[4];
-        Vec4<T>::ld(&As[kk][ty * RI + i], v);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) av[i + u] = v[u];
+      for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int kb = 0; kb < mi; kb += 64) {
+      const int kend = min(mi, kb + 64);
+      if (tile == 0 || nkb > 1) {
+        __syncthreads();  // previous readers of Bs are done
+        const int kpad = (kend - kb + TK - 1) / TK * TK;
+        for (int e = tid; e < kpad * TNW; e += NT) {
+          const int k = e % kpad, c = e / kpad;
+          const int col = c0 + c;
+          Bs[k][c] = (kb + k < kend && col < mo) ? (T)Bm[(int64_t)col * g.M + kb + k] : (T)0;
+        }
       }
-      Vec4<T>::ld(&Bs[kk][tx * 4], bv);
+      for (int k0 = kb; k0 < kend; k0 += TK) {
 #pragma unroll
-      for (int i = 0; i < RI; ++i)
+        for (int q = 0; q < (TK * kGemmRows) / NT; ++q) {
+          const int e = tid + NT * q;
+          const int kk = e / kGemmRows, i = e % kGemmRows;
+          const int row = r0 + i, k = k0 + kk;
+          As[kk][i] = (row < g.n && k < kend) ? X[(int64_t)k * g.ld + row] : (T)0;
+        }
+        __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int kk = 0; kk < TK; ++kk) {
+          T av[RI], bv[4];
+#pragma unroll
+          for (int i = 0; i < RI; i += 4) {
+            T v[4];
+            Vec4<T>::ld(&As[kk][ty * RI + i], v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[i + u] = v[u];
+          }
+          Vec4<T>::ld(&Bs[k0 - kb + kk][tx * 4], bv);
+#pragma unroll
+          for (int i = 0; i < RI; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
-  }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int col = c0 + tx * 4 + j;
-    if (col >= mo) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tx * 4 + j;
+      if (col >= mo) continue;
 #pragma unroll
-    for (int i = 0; i < RI; ++i) {
-      const int row = r0 + ty * RI + i;
-      if (row >= g.n) continue;
-      const int64_t o = (int64_t)col * g.ld + row;
-      O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
+      for (int i = 0; i < RI; ++i) {
+        const int row = r0 + ty * RI + i;
+        if (row >= g.n) continue;
+        const int64_t o = (int64_t)col * g.ld + row;
+        O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
+      }
     }
   }
+  __syncthreads();  // the next column block restages Bs
 }
 
-// One launch for every output width: a CTA owns kGemmRows rows and runs one
-// 32-wide tile when mo <= 32, else 64-wide tiles over all output columns.
+// One launch for every output width: a CTA owns kGemmTiles x kGemmRows rows
+// and runs one 32-wide column block when mo <= 32, else 64-wide blocks.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
@@ -203,18 +220,18 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
-  const int r0 = blockIdx.x * kGemmRows;
-  if (r0 >= g.n || mo < 1) return;
-  __shared__ __align__(16) T As[TK][kGemmRows + 4];
-  __shared__ __align__(16) T Bs[TK][64 + 4];
+  const int rbase = blockIdx.x * kGemmRows * kGemmTiles;
+  if (rbase >= g.n || mo < 1) return;
+  __shared__ __align__(16) T As[TK][kGemmRows];
+  __shared__ __align__(16) T Bs[64][64];
   const T* X = in.at(slot, side);
   const double* Bm = bm.at(slot, side);
   T* O = out.at(slot, side);
   const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
   if (mo <= 32) {
-    gemm_tile<T, 32>(g, X, Bm, O, Z, mode, mi, mo, r0, 0, As, Bs);
+    gemm_block<T, 32>(g, X, Bm, O, Z, mode, mi, mo, rbase, 0, As, Bs);
   } else {
-    for (int c0 = 0; c0 < mo; c0 += 64) gemm_tile<T, 64>(g, X, Bm, O, Z, mode, mi, mo, r0, c0, As, Bs);
+    for (int c0 = 0; c0 < mo; c0 += 64) gemm_block<T, 64>(g, X, Bm, O, Z, mode, mi, mo, rbase, c0, As, Bs);
   }
 }
 
@@ -534,8 +551,8 @@ template <typename T>
 cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
                            Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
                            cudaStream_t s) {
-  k_gemm_nn<T><<<dim3(cdiv(g.n, kGemmRows), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub,
-                                                                          mode);
+  k_gemm_nn<T><<<dim3(cdiv(g.n, kGemmRows * kGemmTiles), 1, g.nslots * 2), NT, 0, s>>>(g, st, in, sel_in, bm, sel_out,
+                                                                                       out, zsub, mode);
   return cudaGetLastError();
 }
 
