@@ -54,9 +54,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1500,
+    ap.add_argument("--serve-requests", type=int, default=800,
                     help="requests of the serving stream (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-kmax", type=int, default=14, help="largest n = 2^k - 1 of the stream")
     ap.add_argument("--mixed-sizes", type=int, default=512, help="solves of the mixed-size batch (0: skip)")
     return ap.parse_args()
@@ -272,9 +272,13 @@ def gpu_arm(args, rank, world, local_rank, precisions):
 ALU_CLASSES = {"fp64": {"gram": "fp64", "gemm": "fp64", "cross": "fp64", "reduce": "fp64"},
                "mixed": {"gram": "fp64", "gemm": "fp64", "gram_f32": "fp32", "gemm_f32": "fp32", "cross": "fp32"}}
 ALU_PEAKS = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS}
+# DRAM bytes (read + write) per launch from ncu captures of the mixed bench at
+# batch 128, scaled by batch / 128 (the launches' data grow with the slots);
+# a class whose kernel changed since its capture has no entry.
+TRAFFIC_B128 = {("mixed", "gemm"): (577.1e6, "profiles/k_gemm_nn_double_mixed_n4095_batch128.md")}
 
 
-def roofline(res, prec, hbm_peak, peak_src):
+def roofline(res, prec, hbm_peak, peak_src, batch):
     """Dominant kernel class (most event-timed time, among classes with
     algorithmic work) against its bound."""
     ks = {k: v for k, v in res["kernels"].items() if k != "all" and v[2] + v[3] > 0}
@@ -298,6 +302,10 @@ def roofline(res, prec, hbm_peak, peak_src):
     out.update({"kernel": name, "launches": launches, "avg_launch_us": 1e3 * ms / launches,
                 "algorithmic_per_launch": (flops if out["bound"] == "alu" else nbytes) / launches,
                 "traffic": None})
+    tr = TRAFFIC_B128.get((prec, name))
+    if tr is not None:
+        out["traffic"] = tr[0] * batch / 128
+        out["traffic_source"] = f"{tr[1]} (dram bytes per launch at batch 128, scaled to batch {batch})"
     return out
 
 
@@ -528,7 +536,7 @@ def main():
         line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
     if "e2e" in res:
         line["e2e"] = res["e2e"]
-    line["roofline"] = roofline(res, head, hbm_peak, peak_src)
+    line["roofline"] = roofline(res, head, hbm_peak, peak_src, args.batch)
     line["class_roofline"] = class_rooflines(res, head, hbm_peak)
     line["kernel_ms"] = {k: round(v[1], 3) for k, v in res["kernels"].items()}
     line["latency_bound_ms"] = {k: round(v[1], 3) for k, v in res["kernels"].items()
