@@ -390,8 +390,11 @@ def serving_stream(args, rank):
         statuses[info["status"]] = statuses.get(info["status"], 0) + 1
     wall = time.perf_counter() - t0
     st = sv.stats()
+    last_error = sv.last_error()
     sv.close()
-    return {"requests": R, "rate_per_s": args.serve_rate, "wall_s": round(wall, 3),
+    failed = sum(v for k, v in statuses.items() if k not in (lrp.LRP_OK, lrp.LRP_NOT_CONVERGED, lrp.LRP_RANK_CAPPED))
+    return {"requests": R, "rate_per_s": args.serve_rate, "wall_s": round(wall, 3), "failed": failed,
+            "last_error": last_error or None,
             "throughput_solves_per_s": R / wall,
             "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
             "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,

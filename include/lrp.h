@@ -387,6 +387,9 @@ lrp_status lrp_wait(lrp_server_t server, uint64_t ticket, lrp_result* out, int64
 /* Counters and latency percentiles (microseconds). */
 lrp_status lrp_server_get_stats(lrp_server_t server, lrp_server_stats* out);
 
+/* Copy the message of the most recent failed batch (empty if none) into buf (len bytes, NUL-terminated). */
+lrp_status lrp_server_last_error(lrp_server_t server, char* buf, size_t len);
+
 /* Clear the counters and the latency record. */
 lrp_status lrp_server_reset_stats(lrp_server_t server);
 

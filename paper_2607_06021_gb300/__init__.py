@@ -117,6 +117,7 @@ def _load():
         "lrp_wait": ([P, ctypes.c_uint64, ctypes.POINTER(lrp_result), I64], I32),
         "lrp_server_get_stats": ([P, ctypes.POINTER(lrp_server_stats)], I32),
         "lrp_server_reset_stats": ([P], I32),
+        "lrp_server_last_error": ([P, ctypes.c_char_p, ctypes.c_size_t], I32),
         "lrp_server_destroy": ([P], I32),
         "lrp_last_error": ([], ctypes.c_char_p),
         "lrp_status_string": ([I32], ctypes.c_char_p),
@@ -212,6 +213,12 @@ def lrp_server_get_stats(server) -> lrp_server_stats:
     st = lrp_server_stats()
     _check(_lib.lrp_server_get_stats(server, ctypes.byref(st)), "lrp_server_get_stats")
     return st
+
+
+def lrp_server_last_error(server) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _check(_lib.lrp_server_last_error(server, buf, 1024), "lrp_server_last_error")
+    return buf.value.decode()
 
 
 def lrp_server_reset_stats(server) -> None:

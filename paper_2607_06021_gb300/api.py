@@ -5,14 +5,15 @@ import ctypes
 
 import torch
 
-from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK,
+from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK, LRP_SEL_LEVERAGE,
+               LRP_SEL_QDEIM,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
                lrp_plan_set_trace, lrp_plan_trace,
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
                lrp_warm_destroy, lrp_warm_reset, lrp_poll, lrp_request, lrp_server_create,
                lrp_server_default_opts, lrp_server_destroy, lrp_server_get_stats, lrp_server_reset_stats,
-               lrp_submit, lrp_wait)
+               lrp_server_last_error, lrp_submit, lrp_wait)
 
 
 def colmajor(x: torch.Tensor) -> torch.Tensor:
@@ -44,7 +45,7 @@ class Plan:
 
     def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
-                 check_every: int = 1, refine_steps: int = 1):
+                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls"):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch = batch
@@ -54,6 +55,7 @@ class Plan:
         o.seed = seed
         o.check_every = check_every
         o.refine_steps = refine_steps
+        o.selector = LRP_SEL_QDEIM if selector == "qdeim" else LRP_SEL_LEVERAGE
         self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
         self.handle = lrp_plan(n, tol, max_rank, o)
 
@@ -233,6 +235,9 @@ class Server:
 
     def reset_stats(self) -> None:
         lrp_server_reset_stats(self.handle)
+
+    def last_error(self) -> str:
+        return lrp_server_last_error(self.handle)
 
     def close(self) -> None:
         if self.handle is not None:

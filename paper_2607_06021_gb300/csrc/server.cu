@@ -32,6 +32,7 @@
 namespace lrp {
 lrp_status set_error(lrp_status s, const std::string& msg);
 }
+extern "C" const char* lrp_last_error(void);
 
 static_assert(sizeof(lrp_server_opts) == 24, "lrp_server_opts layout");
 static_assert(sizeof(lrp_request) == 88, "lrp_request layout");
@@ -121,6 +122,7 @@ struct lrp_server_s {
   int64_t submitted = 0, completed = 0, rejected = 0;
   std::vector<double> latencies;    // microseconds, completed requests
   std::vector<std::thread> lanes;
+  std::string last_error;           // message of the most recent failed batch
 };
 
 namespace {
@@ -438,7 +440,9 @@ void lane_main(lrp_server_s* sv) {
     for (size_t i = 0; i < warms.size(); ++i)
       if (warms[i] && !warms[i]->rec) warms[i] = nullptr;
     if (st == LRP_OK) st = run_batch(sv, e, batch, warms, s, lb);
+    const std::string err = (st != LRP_OK) ? std::string(lrp_last_error()) : std::string();
     lk.lock();
+    if (st != LRP_OK) sv->last_error = err;
     for (size_t i = 0; i < batch.size(); ++i) {
       if (st == LRP_OK && warms[i]) warms[i]->filled = true;
       finish(sv, batch[i], st == LRP_OK ? batch[i]->solve_status : st);
@@ -634,6 +638,15 @@ extern "C" lrp_status lrp_server_get_stats(lrp_server_t sv, lrp_server_stats* ou
     out->p50_us = percentile(lat, 0.50);
     out->p99_us = percentile(lat, 0.99);
   }
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_server_last_error(lrp_server_t sv, char* buf, size_t len) {
+  if (!sv || !buf || len == 0) return set_error(LRP_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  const size_t k = std::min(len - 1, sv->last_error.size());
+  memcpy(buf, sv->last_error.data(), k);
+  buf[k] = 0;
   return LRP_OK;
 }
 

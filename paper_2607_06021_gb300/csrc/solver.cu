@@ -82,6 +82,15 @@ lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc
   idx = arena.get<int32_t>((size_t)d.B * 2 * d.M);
   cand_score = arena.get<double>((size_t)d.B * 2 * d.cand_blocks * d.cand_per_block);
   cand_idx = arena.get<int32_t>((size_t)d.B * 2 * d.cand_blocks * d.cand_per_block);
+  if (d.qdeim_chunks > 0) {
+    qd.nchunk = d.qdeim_chunks;
+    qd.chunk_rows = d.qdeim_rows;
+    qd.qn = arena.get<double>((size_t)d.B * 2 * d.ld);
+    qd.qv = arena.get<double>((size_t)d.B * 2 * MM);
+    qd.cs = arena.get<double>((size_t)d.B * 2 * 2 * d.qdeim_chunks);
+    qd.ci = arena.get<int32_t>((size_t)d.B * 2 * 2 * d.qdeim_chunks);
+    qd.piv = arena.get<int32_t>((size_t)d.B * 2 * d.M);
+  }
   back_in = arena.get<T*>((size_t)2 * d.B);
   back_out = arena.get<double*>((size_t)2 * d.B);
   back_ldi = arena.get<int64_t>((size_t)2 * d.B);
@@ -316,7 +325,7 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.max_rhs_rank < 1 || o.max_rhs_rank > kMaxRF) return set_error(LRP_EINVAL, "max_rhs_rank out of range");
   if (o.batch < 1 || o.batch > 65535) return set_error(LRP_EINVAL, "batch out of range");
   if (o.precision != LRP_FP64 && o.precision != LRP_MIXED) return set_error(LRP_EINVAL, "unknown precision");
-  if (o.selector != LRP_SEL_LEVERAGE) return set_error(LRP_EINVAL, "only the leverage-score selector is built");
+  if (o.selector != LRP_SEL_LEVERAGE && o.selector != LRP_SEL_QDEIM) return set_error(LRP_EINVAL, "unknown selector");
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
   if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
@@ -353,6 +362,8 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
     d.cand_blocks = (int)((n + rows - 1) / rows);
   }
   d.cand_per_block = M;
+  d.qdeim_rows = 1024;
+  d.qdeim_chunks = (o.selector == LRP_SEL_QDEIM) ? (int)((n + d.qdeim_rows - 1) / d.qdeim_rows) : 0;
   if (!fp64 && d.M < d.RF + 2) return set_error(LRP_EINVAL, "mixed precision needs m_cap >= max_rhs_rank + 2");
   return LRP_OK;
 }
@@ -673,6 +684,24 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   return LRP_OK;
 }
 
+// Row candidates for the next index-set enrichment from the current factors:
+// leverage scores (Algorithm LeverageScores, the default) or QDEIM pivots
+// (Algorithm IS), both read by k_select.
+template <typename T>
+static lrp_status select_rows(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, Strided<const T> U, int sel,
+                              cudaStream_t s) {
+  const PlanDims& d = p->dims;
+  if (p->opts.selector == LRP_SEL_QDEIM) {
+    LRP_LAUNCH(p, LRP_K_LEVERAGE, 2 * d.M + 1, s,
+               launch_qdeim<T>(g, p->st, U, sel, w.qd, w.cand_score, w.cand_idx, d.cand_blocks, d.cand_per_block,
+                               d.M, s));
+  } else {
+    LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
+               launch_leverage<T>(g, p->st, U, sel, w.cand_score, w.cand_idx, d.cand_blocks, d.cand_per_block, s));
+  }
+  return LRP_OK;
+}
+
 // Cross-DEIM (Algorithm Cross-DEIM) on the transformed right-hand side held in
 // w.Fh / w.w: initial bases orth(Fh), then iterations until every slot stops.
 // Runs `body` directly, or (when graphs are enabled and timing is off) replays
@@ -734,10 +763,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
                                  kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
     // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
     LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_warm_load<T>(cp, cb, Strided<T>{w.U[1], nm, 2 * nm}, s));
-    LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-               launch_leverage<T>(g, p->st, cs<T>(w.U[1], nm, 2 * nm), kDimC0, w.cand_score, w.cand_idx,
-                                  d.cand_blocks, d.cand_per_block, s));
-    return LRP_OK;
+    return select_rows<T>(p, w, g, cs<T>(w.U[1], nm, 2 * nm), kDimC0, s);
   };
   lrp_status st0 = run_captured<T>(p, w, count, 3, s, init);
   if (st0) return st0;
@@ -762,9 +788,8 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
                  launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
                                    Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
                                    none, 0, s));
-      LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-                 launch_leverage<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR, w.cand_score, w.cand_idx,
-                                    d.cand_blocks, d.cand_per_block, s));
+      st = select_rows<T>(p, w, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, s);
+      if (st) return st;
       if (k > 0) {
         // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
         st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,

@@ -40,6 +40,8 @@ struct PlanDims {
   int rows_per_block;
   int cand_blocks;     // leverage candidate blocks (<= 1024 rows each)
   int cand_per_block;
+  int qdeim_chunks;    // QDEIM row chunks (0: leverage selection)
+  int qdeim_rows;      // rows per QDEIM chunk
 };
 
 // HBM layout per batch slot b and side s (0 = rows/U/I, 1 = columns/V/J); every
@@ -78,6 +80,7 @@ struct Workspace {
   T** fwd_out = nullptr;
   int64_t* fwd_ldi = nullptr;
   int64_t* fwd_ldo = nullptr;
+  QdeimBufs qd{};  // QDEIM selection buffers (plans with the QDEIM selector only)
   int rf_cap = 0;  // columns of Fh (and entries of w) per slot and side
   // Captured CUDA graphs of one Cross-DEIM iteration: [0] the first iteration,
   // [1] odd iterations, [2] even iterations >= 2, [3] the initial bases; valid for

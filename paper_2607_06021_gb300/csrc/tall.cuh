@@ -50,6 +50,26 @@ cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, in
 // Raises the dynamic shared-memory limit of the leverage kernels (once per device).
 cudaError_t tall_configure();
 
+// Work buffers of the QDEIM selection (per problem and side).
+struct QdeimBufs {
+  double* qn;        // [slots x 2][ld] residual row norms^2 (-1 once picked)
+  double* qv;        // [slots x 2][M][M] row l: orthonormal direction q_l of the picked rows
+  double* cs;        // [slots x 2][2][nchunk] best residual norm per row chunk (two step parities)
+  int32_t* ci;       // [slots x 2][2][nchunk] its row
+  int32_t* piv;      // [slots x 2][M] pivots in order (-1: none)
+  int nchunk;        // row chunks of chunk_rows rows
+  int chunk_rows;
+};
+
+// QDEIM (Algorithm IS): the first c = dim(sel) pivots of the column-pivoted QR of
+// U[s](:, :c)^T, handed to the index-set merge as ranked candidates (block 0 of
+// cand_score / cand_idx, in pivot order).  max_c bounds c over the batch (the
+// plan's m_cap): 2 max_c + 1 launches.
+template <typename T>
+cudaError_t launch_qdeim(const TallGeom& g, const SolveState* st, Strided<const T> us, int sel, const QdeimBufs& q,
+                         double* cscore, int32_t* cidx, int cand_blocks, int cand_per_block, int max_c,
+                         cudaStream_t s);
+
 // Leverage scores of U[s](:, :c) rows (c from sel) and per-block top-c candidates.
 template <typename T>
 cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel,
