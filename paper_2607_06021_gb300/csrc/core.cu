@@ -45,13 +45,12 @@ __device__ inline double dst_col_flops(int n) {
 }
 
 // Three symmetric Gram passes, two triangular applies, on side sizes m0, m1.
-// FP32 data (w == 4) accumulate passes 2 and 3 in FP32.
+// FP32 data (w == 4) run every pass on the FP32 pipe (pass 1 in double-float).
 __device__ inline void acct_cholqr3(double* row, double n, double m0, double m1, int NB, double w) {
   for (double m : {m0, m1}) {
     const double gf = n * m * (m + 1.0), gb = n * m * w + NB * m * (m + 1.0) / 2.0 * 8.0;
     if (w == 4.0) {
-      acct_add(row, LRP_K_GRAM, gf, gb);
-      acct_add(row, LRP_K_GRAM_F32, 2.0 * gf, 2.0 * gb);
+      acct_add(row, LRP_K_GRAM_F32, 3.0 * gf, 3.0 * gb);
     } else {
       acct_add(row, LRP_K_GRAM, 3.0 * gf, 3.0 * gb);
     }

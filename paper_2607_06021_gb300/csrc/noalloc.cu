@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "dst.cuh"
+#include "guard.cuh"
 
 namespace lrp {
 lrp_status set_error(lrp_status s, const std::string& msg);
@@ -85,6 +86,7 @@ extern "C" lrp_status lrp_dst1_noalloc(int64_t n, int32_t ncols, const double* d
     // device current (host code may not use the symbol itself as a pointer).
     std::lock_guard<std::mutex> lock(g_addr.mu);
     if (!g_addr.ptr[dev]) {
+      SetupGuard guard;
       cudaError_t e = cudaGetSymbolAddress(&g_addr.ptr[dev], g_noalloc_scratch);
       if (e != cudaSuccess) {
         g_addr.ptr[dev] = nullptr;

@@ -27,6 +27,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "guard.cuh"
 #include "lrp.h"
 
 namespace lrp {
@@ -39,6 +40,7 @@ static_assert(sizeof(lrp_request) == 88, "lrp_request layout");
 static_assert(sizeof(lrp_result) == 32, "lrp_result layout");
 static_assert(sizeof(lrp_server_stats) == 96, "lrp_server_stats layout");
 using lrp::set_error;
+using lrp::SetupGuard;
 
 namespace {
 
@@ -184,9 +186,12 @@ void destroy_entry(lrp_server_s* sv, PlanEntry* e) {
   }
   e->warm.clear();
   if (e->plan) lrp_plan_destroy(e->plan);
-  if (e->d_in) cudaFree(e->d_in);
-  if (e->d_out) cudaFree(e->d_out);
-  if (e->d_info) cudaFree(e->d_info);
+  {
+    SetupGuard guard;
+    if (e->d_in) cudaFree(e->d_in);
+    if (e->d_out) cudaFree(e->d_out);
+    if (e->d_info) cudaFree(e->d_info);
+  }
   sv->device_bytes -= e->bytes;
   delete e;
 }
@@ -238,6 +243,7 @@ lrp_status build_entry(lrp_server_s* sv, PlanEntry* e) {
   if (s != LRP_OK) return s;
   e->in_stride = (size_t)(2 * e->key.n + 1) * e->key.rf_cap;
   e->out_stride = (size_t)(2 * e->key.n + 1) * e->key.max_rank;
+  SetupGuard guard;
   if (cudaMalloc((void**)&e->d_in, sizeof(double) * e->in_stride * e->B) != cudaSuccess ||
       cudaMalloc((void**)&e->d_out, sizeof(double) * e->out_stride * e->B) != cudaSuccess ||
       cudaMalloc((void**)&e->d_info, sizeof(lrp_info) * e->B) != cudaSuccess) {
@@ -252,6 +258,7 @@ struct LaneBuffers {
   size_t cap = 0;
   double* need(size_t count) {
     if (count <= cap) return pinned;
+    SetupGuard guard;
     if (pinned) cudaFreeHost(pinned);
     pinned = nullptr;
     cap = 0;
@@ -263,6 +270,7 @@ struct LaneBuffers {
     return pinned;
   }
   ~LaneBuffers() {
+    SetupGuard guard;
     if (pinned) cudaFreeHost(pinned);
   }
 };
@@ -334,7 +342,10 @@ lrp_status run_batch(lrp_server_s* sv, PlanEntry* e, std::vector<Request*>& batc
 void lane_main(lrp_server_s* sv) {
   cudaSetDevice(sv->device);
   cudaStream_t s = nullptr;
-  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  {
+    SetupGuard guard;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  }
   LaneBuffers lb;
   std::unique_lock<std::mutex> lk(sv->mu);
   for (;;) {
@@ -468,6 +479,7 @@ void lane_main(lrp_server_s* sv) {
   }
   lk.unlock();
   cudaStreamSynchronize(s);
+  SetupGuard guard;
   cudaStreamDestroy(s);
 }
 
@@ -667,7 +679,10 @@ extern "C" lrp_status lrp_server_destroy(lrp_server_t sv) {
   sv->cv.notify_all();
   for (auto& t : sv->lanes) t.join();
   cudaSetDevice(sv->device);
-  cudaDeviceSynchronize();
+  {
+    SetupGuard guard;
+    cudaDeviceSynchronize();
+  }
   for (PlanEntry* e : sv->plans) destroy_entry(sv, e);
   sv->plans.clear();
   for (auto& kv : sv->tickets) delete kv.second;

@@ -27,6 +27,11 @@ namespace lrp {
 
 thread_local std::string g_last_error;
 
+std::shared_mutex& setup_mutex() {
+  static std::shared_mutex m;
+  return m;
+}
+
 lrp_status set_error(lrp_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
@@ -129,6 +134,7 @@ using namespace lrp;
 int KernelStats::take(cudaStream_t s) {
   if (next_event >= (int)pool.size()) {
     cudaEvent_t e;
+    SetupGuard guard;
     if (cudaEventCreate(&e) != cudaSuccess) return -1;
     pool.push_back(e);
   }
@@ -164,6 +170,7 @@ extern "C" lrp_status lrp_plan_set_timing(lrp_plan_t p, int32_t enable) {
 extern "C" lrp_status lrp_plan_set_trace(lrp_plan_t p, int32_t enable) {
   if (!p) return set_error(LRP_EINVAL, "NULL plan");
   std::lock_guard<std::mutex> lock(p->mu);
+  SetupGuard guard;
   const bool on = enable != 0;
   if (on && !p->trace_dev) {
     const size_t bytes = sizeof(double) * (size_t)p->dims.B * kTraceLen * kTraceWidth;
@@ -187,6 +194,7 @@ extern "C" lrp_status lrp_plan_trace(lrp_plan_t p, int32_t slot, double* out, in
   if (!p || !out || !n_entries) return set_error(LRP_EINVAL, "NULL argument");
   if (slot < 0 || slot >= p->dims.B || max_entries < 0) return set_error(LRP_EINVAL, "slot out of range");
   std::lock_guard<std::mutex> lock(p->mu);
+  SetupGuard guard;
   *n_entries = 0;
   if (!p->trace_dev) return set_error(LRP_EINVAL, "tracing was never enabled on this plan");
   LRP_CUDA(cudaDeviceSynchronize());
@@ -205,6 +213,7 @@ extern "C" lrp_status lrp_plan_kernel_stats(lrp_plan_t p, int32_t kclass, int64_
   if (!p || !launches || !total_ms) return set_error(LRP_EINVAL, "NULL argument");
   if (kclass < -1 || kclass >= LRP_K_COUNT) return set_error(LRP_EINVAL, "kernel class out of range");
   std::lock_guard<std::mutex> lock(p->mu);
+  SetupGuard guard;
   if (cudaDeviceSynchronize() != cudaSuccess) return set_error(LRP_ECUDA, "synchronize failed");
   p->stats.drain();
   int64_t l = 0;
@@ -223,6 +232,7 @@ extern "C" lrp_status lrp_plan_kernel_work(lrp_plan_t p, int32_t kclass, double*
   if (!p || !flops || !bytes) return set_error(LRP_EINVAL, "NULL argument");
   if (kclass < -1 || kclass >= LRP_K_COUNT) return set_error(LRP_EINVAL, "kernel class out of range");
   std::lock_guard<std::mutex> lock(p->mu);
+  SetupGuard guard;
   std::vector<double> h((size_t)p->dims.B * 2 * LRP_K_COUNT);
   LRP_CUDA(cudaDeviceSynchronize());
   LRP_CUDA(cudaMemcpy(h.data(), p->acct, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
@@ -241,6 +251,7 @@ extern "C" lrp_status lrp_plan_kernel_work(lrp_plan_t p, int32_t kclass, double*
 extern "C" lrp_status lrp_plan_reset_stats(lrp_plan_t p) {
   if (!p) return set_error(LRP_EINVAL, "NULL plan");
   std::lock_guard<std::mutex> lock(p->mu);
+  SetupGuard guard;
   cudaDeviceSynchronize();
   cudaMemset(p->acct, 0, sizeof(double) * (size_t)p->dims.B * 2 * LRP_K_COUNT);
   p->stats.drain();
@@ -412,6 +423,8 @@ extern "C" lrp_status lrp_plan_estimate_bytes(int64_t n, double tol, int32_t max
   return s;
 }
 
+static void plan_free(lrp_plan_s* p);
+
 extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts) {
   if (!out) return set_error(LRP_EINVAL, "out is NULL");
   *out = nullptr;
@@ -423,6 +436,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     return s;
   }
   const PlanDims& d = p->dims;
+  SetupGuard guard;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     return set_error(LRP_ECUDA, "no CUDA device");
@@ -449,7 +463,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     if (e != cudaSuccess) s = set_error(LRP_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
   }
   if (s != LRP_OK) {
-    lrp_plan_destroy(p);
+    plan_free(p);
     return s;
   }
   *out = p;
@@ -463,6 +477,7 @@ extern "C" lrp_status lrp_warm_create(lrp_plan_t p, lrp_warm_t* out) {
   if (!w) return set_error(LRP_ENOMEM, "host allocation failed");
   w->plan = p;
   const PlanDims& d = p->dims;
+  SetupGuard guard;
   WarmDev h;
   memset(&h, 0, sizeof(h));
   h.ld = d.ld;
@@ -485,6 +500,7 @@ extern "C" lrp_status lrp_warm_create(lrp_plan_t p, lrp_warm_t* out) {
 
 extern "C" lrp_status lrp_warm_reset(lrp_warm_t w) {
   if (!w) return set_error(LRP_EINVAL, "NULL record");
+  SetupGuard guard;
   int32_t zero = 0;
   LRP_CUDA(cudaMemcpy(&w->dev->valid, &zero, sizeof(zero), cudaMemcpyHostToDevice));
   return LRP_OK;
@@ -492,14 +508,15 @@ extern "C" lrp_status lrp_warm_reset(lrp_warm_t w) {
 
 extern "C" lrp_status lrp_warm_destroy(lrp_warm_t w) {
   if (!w) return LRP_OK;
+  SetupGuard guard;
   cudaDeviceSynchronize();
   w->arena.release();
   delete w;
   return LRP_OK;
 }
 
-extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
-  if (!p) return LRP_OK;
+// Frees everything a plan holds; the caller holds the setup mutex.
+static void plan_free(lrp_plan_s* p) {
   cudaDeviceSynchronize();
   if (p->trace_dev) cudaFree(p->trace_dev);
   p->arena.release();
@@ -513,6 +530,12 @@ extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
   p->w32.release_graphs();
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
+}
+
+extern "C" lrp_status lrp_plan_destroy(lrp_plan_t p) {
+  if (!p) return LRP_OK;
+  SetupGuard guard;
+  plan_free(p);
   return LRP_OK;
 }
 
@@ -565,7 +588,8 @@ static Strided<const T> cs(const T* base, int64_t side, int64_t slot) {
 template <typename T>
 static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T> x, int sx, Strided<const T> y,
                               int sy, double* part, Strided<double> G, bool sym, cudaStream_t s, bool acc64 = true) {
-  const int cls = (acc64 || sizeof(T) == 8) ? LRP_K_GRAM : LRP_K_GRAM_F32;
+  // FP32 data run on the FP32 pipe (FP32 or double-float accumulation)
+  const int cls = (sizeof(T) == 8) ? LRP_K_GRAM : LRP_K_GRAM_F32;
   LRP_LAUNCH(p, cls, gram_kernels(p), s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s, acc64));
   LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, sx, sy, part, G, sym, s));
   return LRP_OK;
@@ -710,10 +734,12 @@ template <typename T, typename Body>
 static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int kind, cudaStream_t s, Body body) {
   if (!p->use_graphs || p->stats.timing || !p->cap_stream) return body(s);
   if (w.graph_count != count) {
+    SetupGuard guard;
     w.release_graphs();
     w.graph_count = count;
   }
   if (!w.graphs[kind]) {
+    CaptureGuard capture;
     int64_t before[LRP_K_COUNT];
     for (int c = 0; c < LRP_K_COUNT; ++c) before[c] = p->stats.launches[c];
     // Captured on the plan's own stream (the caller's may be the legacy default
@@ -911,6 +937,9 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   const double tol_in = p->tol > p->mixed_inner_tol ? p->tol : p->mixed_inner_tol;
   CoreParams c32 = make_core_params<float>(p, count, tol_in, eps32, p->mixed_redundancy);
   c32.noise_floor_stop = 1;
+  // the first pass's Gram is double-float (relative error ~1e-13, at worst
+  // ~5e-10): its shift dominates that error
+  c32.shift_rel = 1e-12;
   // FP32 solves whose change between iterates stalls above tol_in (FP32 noise in
   // the index updates) stop after a bounded number of iterations; the FP64
   // residual step corrects what they leave.
@@ -1056,6 +1085,7 @@ extern "C" lrp_status lrp_dst1(int64_t n, int32_t ncols, const double* X, int64_
     size_t temp_bytes = 0;
   };
   static Cache cache[8];
+  SetupGuard guard;  // the cache may allocate, free and synchronise
   int dev = 0;
   LRP_CUDA(cudaGetDevice(&dev));
   {

@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "core.cuh"
+#include "guard.cuh"
 
 // Device allocations of one plan (released together).
 struct DeviceArena {

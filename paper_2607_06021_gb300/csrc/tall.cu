@@ -450,6 +450,134 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
   }
 }
 
+// hi + lo += a * b without rounding the product: a*b = p + pe exactly (one FMA),
+// p is added to hi by TwoSum (Knuth) and every rounding error goes to lo.  The
+// _rn intrinsics keep the compiler from contracting or reordering the steps.
+__device__ __forceinline__ void df_add_product(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+// Gram partials of FP32 data with near-FP64 accuracy on the FP32 pipe (the first,
+// ill-conditioned CholeskyQR pass of the FP32 iterations).  Same tiling as
+// k_gram_small<float, float, 4, 1>, but each entry is a double-float (hi, lo)
+// sum of exact products, folded into an FP64 total every kDfFold chunks
+// (128 rows): the relative error stays below ~2 (128)^2 eps32^2 ~ 5e-10 in the
+// worst case (~1e-13 typically), against 64x the FP64 pipe's rate.
+constexpr int kDfFold = 4;
+
+__global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __restrict__ st_all,
+                                                Strided<const float> xs, int sel_x, double* __restrict__ part) {
+  constexpr int KC = kSmallRows;
+  constexpr int LDS = kSmallGram + 4;
+  constexpr int TS = 4;
+  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const SolveState& st = st_all[slot];
+  if (!st.active) return;
+  const int mx = dim_of(st, side, sel_x);
+  if (mx < 1) return;
+  const int blk = blockIdx.x;
+  const int rbeg = blk * g.rows_per_block;
+  const int rend = min(g.n, rbeg + g.rows_per_block);
+  const float* X = xs.at(slot, side);
+  double* P = part + ((int64_t)(slot * 2 + side) * g.NB + blk) * (int64_t)g.M * g.M;
+  constexpr size_t kTileBytes = KC * LDS * sizeof(float);
+  constexpr size_t kRedBytes = (size_t)NT * TS * TS * sizeof(double);
+  constexpr size_t kFallBytes = (size_t)TKG * (TM + 1 + TN + 1) * sizeof(float);
+  constexpr size_t kSmem = kRedBytes > kTileBytes ? (kRedBytes > kFallBytes ? kRedBytes : kFallBytes)
+                                                  : (kTileBytes > kFallBytes ? kTileBytes : kFallBytes);
+  __shared__ __align__(16) unsigned char gsm[kSmem];
+  if (mx > kSmallGram) {
+    gram_tiled<float, double>(g, X, X, mx, mx, rbeg, rend, P, true, gsm);
+    return;
+  }
+  float (*Xs)[LDS] = reinterpret_cast<float (*)[LDS]>(gsm);
+  const int tx = (mx + TS - 1) / TS;
+  const int ntile = tx * (tx + 1) / 2;  // <= 136
+  const int G = NT / ntile;
+  const int tid = threadIdx.x;
+  const int grp = tid / ntile, t0 = tid - grp * ntile;
+  const bool own = grp < G;
+  int ia = 0, ib = 0;
+  if (own) tile_coords(t0, true, tx, ia, ib);
+  float hi[TS][TS], lo[TS][TS];
+  double tot[TS][TS];
+#pragma unroll
+  for (int i = 0; i < TS; ++i)
+#pragma unroll
+    for (int j = 0; j < TS; ++j) {
+      hi[i][j] = 0.f;
+      lo[i][j] = 0.f;
+      tot[i][j] = 0.0;
+    }
+  const int wx = tx * TS;
+  int chunk = 0;
+  for (int r = rbeg; r < rend; r += KC, ++chunk) {
+    for (int e = tid; e < KC * wx; e += NT) {
+      const int kk = e % KC, c = e / KC;
+      const int row = r + kk;
+      Xs[kk][c] = (row < rend && c < mx) ? X[(int64_t)c * g.ld + row] : 0.f;
+    }
+    __syncthreads();
+    if (own) {
+      for (int kk = grp; kk < KC; kk += G) {
+        float av[TS], bv[TS];
+        load_ts<float, TS>(&Xs[kk][TS * ia], av);
+        load_ts<float, TS>(&Xs[kk][TS * ib], bv);
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+#pragma unroll
+          for (int j = 0; j < TS; ++j) df_add_product(av[i], bv[j], hi[i][j], lo[i][j]);
+      }
+      if ((chunk % kDfFold) == kDfFold - 1 || r + KC >= rend) {
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+#pragma unroll
+          for (int j = 0; j < TS; ++j) {
+            tot[i][j] += (double)hi[i][j] + (double)lo[i][j];
+            hi[i][j] = 0.f;
+            lo[i][j] = 0.f;
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (G == 1) {
+    if (own) {
+#pragma unroll
+      for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < TS; ++j) {
+          const int a = TS * ia + i, b = TS * ib + j;
+          if (a < mx && b < mx && a <= b) P[(int64_t)b * g.M + a] = tot[i][j];
+        }
+    }
+    return;
+  }
+  double* red = reinterpret_cast<double*>(gsm);
+  if (own) {
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) red[((size_t)grp * ntile + t0) * TS * TS + i * TS + j] = tot[i][j];
+  }
+  __syncthreads();
+  for (int e = tid; e < ntile * TS * TS; e += NT) {
+    const int tt = e / (TS * TS), ij = e % (TS * TS), i = ij / TS, j = ij % TS;
+    double v = 0.0;
+    for (int q = 0; q < G; ++q) v += red[((size_t)q * ntile + tt) * TS * TS + ij];
+    int ta, tb;
+    tile_coords(tt, true, tx, ta, tb);
+    const int a = TS * ta + i, b = TS * tb + j;
+    if (a < mx && b < mx && a <= b) P[(int64_t)b * g.M + a] = v;
+  }
+}
+
 __global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int sel_x, int sel_y,
                          const double* __restrict__ part, Strided<double> G, bool symmetric) {
   const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
@@ -560,7 +688,11 @@ template <typename T>
 cudaError_t launch_gram(const TallGeom& g, const SolveState* st, Strided<const T> x, int sel_x,
                         Strided<const T> y, int sel_y, double* part, Strided<double> G, bool symmetric,
                         cudaStream_t s, bool acc64) {
-  if (acc64 || sizeof(T) == 8)
+  if (sizeof(T) == 4 && acc64 && symmetric && x.base == y.base)
+    k_gram_df<<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, Strided<const float>{(const float*)x.base,
+                                                                                   x.side_stride, x.slot_stride},
+                                                         sel_x, part);
+  else if (acc64 || sizeof(T) == 8)
     k_gram_small<T, double, 2, 4><<<dim3(g.NB, 1, g.nslots * 2), NT, 0, s>>>(g, st, x, sel_x, y, sel_y, part,
                                                                              symmetric);
   else
