@@ -385,20 +385,27 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
 #pragma unroll
       for (int j = 0; j < TS; ++j) acc[q][i][j] = (TA)0;
   const int wx = tx * TS, wy = ty * TS;  // padded widths (zero columns beyond mx, my)
-  for (int r = rbeg; r < rend; r += KC) {
-    for (int e = tid; e < KC * wx; e += NT) {
-      const int kk = e % KC, c = e / KC;
-      const int row = r + kk;
-      Xs[kk][c] = (row < rend && c < mx) ? (TA)X[(int64_t)c * g.ld + row] : (TA)0;
+  // The next chunk is fetched into registers while the current one is used.
+  constexpr int PF = KC * kSmallGram / NT;  // elements per thread and chunk (8)
+  T px[PF], py[PF];
+  auto fetch = [&](int r) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + NT * q, kk = e % KC, c = e / KC, row = r + kk;
+      px[q] = (c < mx && row < rend) ? X[(int64_t)c * g.ld + row] : (T)0;
+      if (!same) py[q] = (c < my && row < rend) ? Y[(int64_t)c * g.ld + row] : (T)0;
     }
-    if (!same) {
-      for (int e = tid; e < KC * wy; e += NT) {
-        const int kk = e % KC, c = e / KC;
-        const int row = r + kk;
-        Ys[kk][c] = (row < rend && c < my) ? (TA)Y[(int64_t)c * g.ld + row] : (TA)0;
-      }
+  };
+  fetch(rbeg);
+  for (int r = rbeg; r < rend; r += KC) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + NT * q, kk = e % KC, c = e / KC;
+      if (c < wx) Xs[kk][c] = (TA)px[q];
+      if (!same && c < wy) Ys[kk][c] = (TA)py[q];
     }
     __syncthreads();
+    if (r + KC < rend) fetch(r + KC);
     const TA(*Bsrc)[LDS] = same ? Xs : Ys;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
@@ -516,14 +523,25 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
       tot[i][j] = 0.0;
     }
   const int wx = tx * TS;
+  constexpr int PF = KC * kSmallGram / NT;  // elements per thread and chunk (8)
+  float px[PF];
+  auto fetch = [&](int r) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + NT * q, kk = e % KC, c = e / KC, row = r + kk;
+      px[q] = (c < mx && row < rend) ? X[(int64_t)c * g.ld + row] : 0.f;
+    }
+  };
+  fetch(rbeg);
   int chunk = 0;
   for (int r = rbeg; r < rend; r += KC, ++chunk) {
-    for (int e = tid; e < KC * wx; e += NT) {
-      const int kk = e % KC, c = e / KC;
-      const int row = r + kk;
-      Xs[kk][c] = (row < rend && c < mx) ? X[(int64_t)c * g.ld + row] : 0.f;
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + NT * q, kk = e % KC, c = e / KC;
+      if (c < wx) Xs[kk][c] = px[q];
     }
     __syncthreads();
+    if (r + KC < rend) fetch(r + KC);
     if (own) {
       for (int kk = grp; kk < KC; kk += G) {
         float av[TS], bv[TS];
