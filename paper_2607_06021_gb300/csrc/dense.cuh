@@ -38,6 +38,13 @@ __device__ __forceinline__ TC half_warp_sum(TC v) {
 // that its shuffles stay warp-uniform.  On exit the columns of A are U*Sigma
 // (mutually orthogonal), sig[j] = ||A(:,j)|| and, if V != nullptr,
 // A_in = A_out V^T with V orthogonal.
+// A is scaled by a power of two to ||A||_F in [1/2, 1) for the sweeps (exact;
+// undone on exit), so that squared column norms cannot underflow in FP32.  A
+// pair is left alone once |a_i . a_j| <= mr eps ||a_i|| ||a_j|| (rounding noise)
+// or one of its columns is below eps ||A||_F: such columns lie below every
+// cutoff applied to the singular values (the pseudoinverse's
+// max(|I|,|J|) eps sigma_1, the tail rules), and rotating them only chases
+// rounding noise.
 template <typename TC>
 __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv, double* sig, int* flag) {
   const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -48,12 +55,32 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
       V[(int64_t)j * ldv + i] = (i == j) ? (TC)1 : (TC)0;
     }
   }
+  __shared__ double jac_red[32];
+  double f2 = 0.0;
+  for (int e = tid; e < mr * nc; e += blockDim.x) {
+    const double v = (double)A[(int64_t)(e / mr) * lda + (e % mr)];
+    f2 = fma(v, v, f2);
+  }
+  f2 = warp_sum(f2);
+  if ((tid & 31) == 0) jac_red[warp] = f2;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < nwarps ? jac_red[tid] : 0.0;
+    v = warp_sum(v);
+    if (tid == 0) jac_red[0] = v;
+  }
+  __syncthreads();
+  const double fro2 = jac_red[0];
+  int ex = 0;
+  if (fro2 > 0.0) frexp(sqrt(fro2), &ex);
+  const TC down = (TC)ldexp(1.0, -ex);
+  if (ex != 0)
+    for (int e = tid; e < mr * nc; e += blockDim.x) A[(int64_t)(e / mr) * lda + (e % mr)] *= down;
   __syncthreads();
   const int ne = nc + (nc & 1);
   const int npairs = ne / 2;
-  // Rotate while |a_i . a_j| > tol ||a_i|| ||a_j||; below mr * eps the computed
-  // inner products are rounding noise.
   const TC tol = (TC)((double)(mr > 1 ? mr : 1) * Eps<TC>::value);
+  const TC nu = (TC)(Eps<TC>::value * Eps<TC>::value);
   for (int sweep = 0; sweep < kJacobiSweeps && ne >= 2; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
@@ -91,7 +118,8 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
         alpha = half_warp_sum(alpha);
         beta = half_warp_sum(beta);
         gamma = half_warp_sum(gamma);
-        if (!valid || gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+        if (!valid || gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta) || fmin(alpha, beta) <= nu)
+          continue;
         const TC zeta = (beta - alpha) / ((TC)2 * gamma);
         const TC t = copysign((TC)1, zeta) / (fabs(zeta) + sqrt((TC)1 + zeta * zeta));
         const TC c = (TC)1 / sqrt((TC)1 + t * t);
@@ -117,6 +145,11 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
     const int rotated = *flag;
     __syncthreads();
     if (!rotated) break;
+  }
+  if (ex != 0) {
+    const TC up = (TC)ldexp(1.0, ex);
+    for (int e = tid; e < mr * nc; e += blockDim.x) A[(int64_t)(e / mr) * lda + (e % mr)] *= up;
+    __syncthreads();
   }
   const int lane = tid & 31;
   for (int j = warp; j < nc; j += nwarps) {

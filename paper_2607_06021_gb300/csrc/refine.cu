@@ -48,18 +48,35 @@ __device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, d
 
 // After the first FP32 solve: r0 = rank of the trial solution (capped so that
 // r_f + 2 r0 <= M), d = [h^2 s_f, -S0, -S0], mx = r_f + 2 r0.
+// Tail-rule rank of the descending values s[0..r): the smallest t >= 1 with
+// sum_{l >= t} s_l^2 < tol^2 sum_l s_l^2 (the final truncation's rule).
+__device__ int tail_rank_dev(const double* s, int r, double tol) {
+  double tot = 0.0;
+  for (int t = 0; t < r; ++t) tot += s[t] * s[t];
+  int rs = r;
+  double tail = 0.0;
+  for (int t = r - 1; t >= 1; --t) {
+    tail += s[t] * s[t];
+    if (tail < tol * tol * tot) rs = t;
+    else break;
+  }
+  return rs < 1 ? 1 : rs;
+}
+
 __global__ void k_prepare_refine(RefineArgs a) {
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
   if (!st->valid) return;
   const int M = a.M;
   const int rf = st->rf0;
-  int r0 = st->r;
+  const int par = (st->k - 1) & 1;
+  const double* sig = a.sig32 + (int64_t)slot * 2 * M + (int64_t)par * M;
+  // The trial solution enters at its tail-rule rank at the FP32 solve's own
+  // tolerance; the part it drops is left to the correction.
+  int r0 = tail_rank_dev(sig, st->r, st->tol);
   const int cap = (M - rf) / 2;
   if (r0 > cap) r0 = cap;
   if (r0 < 1) r0 = 1;
-  const int par = (st->k - 1) & 1;
-  const double* sig = a.sig32 + (int64_t)slot * 2 * M + (int64_t)par * M;
   double* d = a.dvec + (int64_t)slot * M;
   double* s0 = a.s0 + (int64_t)slot * M;
   const double h = 1.0 / (double)(a.n + 1);
@@ -256,10 +273,14 @@ __global__ void k_prepare_sum(RefineArgs a) {
   if (!st->valid) return;
   const int M = a.M;
   const int r0 = st->r0;
-  int rd = st->r;
-  if (rd > M - r0) rd = M - r0;
   const int par = (st->k - 1) & 1;
   const double* sig = a.sig32 + (int64_t)slot * 2 * M + (int64_t)par * M;
+  // The correction enters at its tail-rule rank at the tolerance its stop test
+  // used (relative to itself: tol ||S0|| / ||S_k||, within [tol_in, 0.1]).
+  double tol_c = st->tol;
+  if (st->tol_abs > 0.0 && st->snorm > 0.0) tol_c = fmax(tol_c, fmin(0.1, st->tol_abs / st->snorm));
+  int rd = tail_rank_dev(sig, st->r, tol_c);
+  if (rd > M - r0) rd = M - r0;
   double* d = a.dvec + (int64_t)slot * M;
   const double* s0 = a.s0 + (int64_t)slot * M;
   for (int t = threadIdx.x; t < r0; t += blockDim.x) d[t] = s0[t];
