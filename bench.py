@@ -214,6 +214,11 @@ def gpu_arm(args, rank, world, local_rank, precisions):
             with torch.cuda.stream(stream):
                 plan.solve_batch_into(batch.inputs, batch.outputs, stream)
 
+        # The clock sampler starts before the warm-up steps: its start-up (NVML
+        # initialisation) stays out of the timed region; it samples through it.
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        time.sleep(0.5)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 step()
@@ -221,8 +226,6 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         plan.reset_stats()
         barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local_rank)
-        clocks.start()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             ms = time_steps(step, args.steps, stream, torch, flush)
