@@ -148,6 +148,19 @@ lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t max_rank,
                     const lrp_opts* opts);
 
 /*
+ * Pack the results of the plan's most recent solve (lrp_solve / lrp_solve_batch)
+ * compactly: for each problem i of that batch, in order, the block
+ * [U (n x r_i) | S (r_i) | V (n x r_i)] (column-major, ld n; r_i the problem's
+ * rank) into d_packed, starting d_offsets[i] doubles in; d_offsets[count]
+ * receives the total.  d_offsets (device, count + 1 int64) and d_packed
+ * (device, capacity doubles) are the caller's.  Asynchronous on `stream`, which
+ * must be ordered after the solve; a block that would end beyond capacity is not
+ * written (detect it from d_offsets[count] > capacity).  Errors: LRP_EINVAL (NULL
+ * plan or offsets, no solve yet), LRP_ECUDA.
+ */
+lrp_status lrp_plan_pack(lrp_plan_t plan, double* d_packed, int64_t capacity, int64_t* d_offsets, void* stream);
+
+/*
  * Device bytes that lrp_plan(n, tol, max_rank, opts) would allocate in its
  * workspace arena (the figure lrp_plan_workspace_bytes reports for the plan),
  * computed on the host without touching a device.  Same argument checks and

@@ -108,6 +108,7 @@ def _load():
         "lrp_plan_kernel_stats": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], I32),
         "lrp_plan_reset_stats": ([P], I32),
         "lrp_plan_kernel_work": ([P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+        "lrp_plan_pack": ([P, VP, I64, VP, VP], I32),
         "lrp_plan_estimate_bytes": ([I64, D, I32, ctypes.POINTER(lrp_opts), ctypes.POINTER(ctypes.c_size_t)], I32),
         "lrp_server_default_opts": ([ctypes.POINTER(lrp_server_opts)], I32),
         "lrp_request_footprint": ([I64, I32, I32], ctypes.c_size_t),
@@ -161,6 +162,10 @@ def lrp_plan(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None):
     _check(_lib.lrp_plan(ctypes.byref(h), int(n), float(tol), int(max_rank),
                          ctypes.byref(opts) if opts is not None else None), "lrp_plan")
     return h
+
+
+def lrp_plan_pack(plan, d_packed, capacity: int, d_offsets, stream) -> None:
+    _check(_lib.lrp_plan_pack(plan, d_packed, int(capacity), d_offsets, stream), "lrp_plan_pack")
 
 
 def lrp_plan_estimate_bytes(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None) -> int:

@@ -9,7 +9,7 @@ from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGE
                LRP_SEL_QDEIM,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
-               lrp_plan_set_trace, lrp_plan_trace,
+               lrp_plan_set_trace, lrp_plan_trace, lrp_plan_pack,
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
                lrp_warm_destroy, lrp_warm_reset, lrp_poll, lrp_request, lrp_server_create,
                lrp_server_default_opts, lrp_server_destroy, lrp_server_get_stats, lrp_server_reset_stats,
@@ -65,6 +65,13 @@ class Plan:
 
     def set_timing(self, enable: bool) -> None:
         lrp_plan_set_timing(self.handle, enable)
+
+    def pack(self, packed: torch.Tensor, offsets: torch.Tensor, stream=None) -> None:
+        """Compact results of the last solve into packed (float64) and offsets (int64, count + 1)."""
+        if packed.dtype != torch.float64 or offsets.dtype != torch.int64 or not packed.is_cuda or not offsets.is_cuda:
+            raise ValueError("packed: CUDA float64, offsets: CUDA int64")
+        lrp_plan_pack(self.handle, ctypes.c_void_p(packed.data_ptr()), packed.numel(),
+                      ctypes.c_void_p(offsets.data_ptr()), _stream(stream))
 
     def set_trace(self, enable: bool) -> None:
         lrp_plan_set_trace(self.handle, enable)

@@ -93,7 +93,7 @@ __device__ void acct_back(double* row, int n_, int r_out, int w_) {
 // ------------------------------------------------------------------- kernels
 
 constexpr int kCholSmemDim = 64;
-constexpr size_t kCholSmemBytes = 3 * kCholSmemDim * kCholSmemDim * sizeof(double);
+constexpr size_t kCholSmemBytes = kCholSmemDim * kCholSmemDim * sizeof(double);
 
 template <typename T>
 __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int sel, int pass) {
@@ -104,15 +104,15 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   const int M = p.g.M;
   const int m = dim_of(*stp, side, sel);
   const double* G = b.G.at(slot, side);
-  // Working triangle W, R^{-1} / product buffer Tm and a copy of R_acc: shared
-  // memory (leading dimension kCholSmemDim) when m <= kCholSmemDim, else the
-  // slot's global scratch (leading dimension M).
+  // Working triangle W: shared memory (leading dimension kCholSmemDim) when
+  // m <= kCholSmemDim, else the slot's global scratch (leading dimension M).
+  // The R^{-1} / product buffer Tm is always in the slot's scratch (L2-resident),
+  // which keeps the CTA's shared memory at one m_cap^2 block.
   const bool in_smem = m <= kCholSmemDim;
   const int Lc = in_smem ? kCholSmemDim : M;
   double* base = b.scratch + (int64_t)slot * b.scratch_stride;
   double* W = in_smem ? chol_smem : base + (int64_t)(8 + side) * M * M;
-  double* Tm = in_smem ? chol_smem + kCholSmemDim * kCholSmemDim : base + (int64_t)(10 + side) * M * M;
-  double* Rc = in_smem ? chol_smem + 2 * kCholSmemDim * kCholSmemDim : nullptr;
+  double* Tm = base + (int64_t)(10 + side) * M * M;  // leading dimension M
   double* P = b.P.at(slot, side);
   double* Racc = b.Racc.at(slot, side);
   __shared__ double red[32];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
 
   // P = R^{-1}: column l by back substitution (dropped rows give zeros).
   for (int l = tid; l < m; l += nt) {
-    double* x = Tm + (int64_t)l * Lc;
+    double* x = Tm + (int64_t)l * M;
     for (int i = m - 1; i > l; --i) x[i] = 0.0;
     for (int i = l; i >= 0; --i) {
       if (dropped[i]) {
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
-    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * Lc + i];
+    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * M + i];
   }
   __syncthreads();
   // Racc <- R (pass 0, undoing the equilibration) or R * Racc.
@@ -199,28 +199,17 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
       Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? W[(int64_t)j * Lc + i] / dsc[j] : 0.0;
     }
   } else {
-    const double* Ro = Racc;
-    int ldr = M;
-    if (in_smem) {
-      for (int e = tid; e < m * m; e += nt) {
-        const int i = e % m, j = e / m;
-        Rc[(int64_t)j * Lc + i] = Racc[(int64_t)j * M + i];
-      }
-      __syncthreads();
-      Ro = Rc;
-      ldr = Lc;
-    }
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, l = e / m;
       double s = 0.0;
       if (i <= l)
-        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * Ro[(int64_t)l * ldr + k];
-      Tm[(int64_t)l * Lc + i] = s;
+        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * Racc[(int64_t)l * M + k];
+      Tm[(int64_t)l * M + i] = s;
     }
     __syncthreads();
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * Lc + i];
+      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * M + i];
     }
   }
 }

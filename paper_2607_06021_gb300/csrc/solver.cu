@@ -1042,6 +1042,7 @@ extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_pro
   p->any_warm = false;
   for (int i = 0; i < count; ++i) p->any_warm = p->any_warm || hp[i].warm != nullptr;
   LRP_CUDA(cudaMemcpyAsync(p->prob_dev, p->prob_host, sizeof(ProblemDev) * count, cudaMemcpyHostToDevice, s));
+  p->last_count = count;
   if (p->opts.precision == LRP_FP64) return run_fp64(p, count, s);
   return run_mixed(p, count, s);
 }

@@ -144,6 +144,7 @@ struct lrp_plan_s {
   lrp::Workspace<float> w32;
   KernelStats stats;
   bool any_warm = false;                 // the current call has warm-start records
+  int last_count = 0;                    // problems of the most recent lrp_solve_batch
   double* trace_dev = nullptr;           // [B][kTraceLen][kTraceWidth], allocated on first use
   bool trace_on = false;
   std::mutex mu;
