@@ -33,15 +33,20 @@ __device__ inline void racct(const RefineArgs& a, int slot, int cls, double flop
   row[2 * cls + 1] += bytes;
 }
 
-// FP64 Gram passes (symmetric) and triangular applies of one shifted CholeskyQR
-// on two n x m blocks.
-__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m) {
+// Gram passes (symmetric) and triangular applies of one shifted CholeskyQR on
+// two n x m blocks: FP64 classes, or the FP32-pipe classes for the
+// double-float recompression of the sum (FP32 data, w = 4; its second pass
+// reads and writes (hi, lo) planes, w = 8).
+__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m, bool fp32_pipe = false) {
   const double n = a.n;
-  racct(a, slot, LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0), 2.0 * passes * (n * m * 8.0 + a.NB * m * (m + 1.0) * 4.0));
+  const double w = fp32_pipe ? 4.0 : 8.0;
+  racct(a, slot, fp32_pipe ? LRP_K_GRAM_F32 : LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0),
+        2.0 * passes * (n * m * w + a.NB * m * (m + 1.0) * 4.0));
   racct(a, slot, LRP_K_REDUCE, 2.0 * passes * a.NB * m * (m + 1.0) / 2.0,
         2.0 * passes * (a.NB + 1.0) * m * (m + 1.0) * 4.0);
   if (passes > 1)
-    racct(a, slot, LRP_K_GEMM, 2.0 * (passes - 1) * n * m * (m + 1.0), 2.0 * (passes - 1) * 2.0 * n * m * 8.0);
+    racct(a, slot, fp32_pipe ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * (passes - 1) * n * m * (m + 1.0),
+          2.0 * (passes - 1) * n * m * (w + 8.0));
 }
 }  // namespace
 
@@ -214,7 +219,8 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
   if (tid == 0) {
     st->r = r;
     // the tall product (Q-basis block) * Bf that follows on both sides
-    racct(a, slot, LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r, 2.0 * a.n * (m + r) * 8.0);
+    racct(a, slot, (mode == 1 && a.X32.base) ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r,
+          2.0 * a.n * (m + r) * 8.0);
   }
 }
 
@@ -291,8 +297,8 @@ __global__ void k_prepare_sum(RefineArgs a) {
     st->rd = rd;
     st->active = 1;
     const double n = a.n;
-    racct(a, slot, LRP_K_REFINE, 0.0, 2.0 * n * (r0 * 8.0 + rd * 4.0 + (r0 + rd) * 8.0));
-    racct_cholqr(a, slot, 2, r0 + rd);
+    racct(a, slot, LRP_K_REFINE, 0.0, 2.0 * n * (r0 * 8.0 + rd * 4.0 + (r0 + rd) * (a.X32.base ? 4.0 : 8.0)));
+    racct_cholqr(a, slot, 2, r0 + rd, a.X32.base != nullptr);
   }
 }
 
@@ -306,6 +312,13 @@ __global__ void k_assemble_sum(RefineArgs a) {
   const int r0 = st.r0, rd = st.rd;
   const double* stash = a.stash.at(slot, side);
   const float* dU = a.U32[st.upar].at(slot, side);
+  if (a.X32.base) {
+    // both blocks are FP32 values (the FP32 trial and the FP32 correction): exact
+    float* X = a.X32.at(slot, side);
+    for (int t = 0; t < r0; ++t) X[(int64_t)t * a.ld + i] = (float)stash[(int64_t)t * a.ld + i];
+    for (int t = 0; t < rd; ++t) X[(int64_t)(r0 + t) * a.ld + i] = dU[(int64_t)t * a.ld + i];
+    return;
+  }
   double* X = a.X.at(slot, side);
   for (int t = 0; t < r0; ++t) X[(int64_t)t * a.ld + i] = stash[(int64_t)t * a.ld + i];
   for (int t = 0; t < rd; ++t) X[(int64_t)(r0 + t) * a.ld + i] = (double)dU[(int64_t)t * a.ld + i];

@@ -923,6 +923,7 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.NB = d.NB;
   a.corr_tol = p->tol;
   a.final_tol = p->tol;
+  a.X32 = {nullptr, 0, 0};
   return a;
 }
 
@@ -979,17 +980,48 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
                (launch_convert<double, float>(d.n, d.ld, count, p->st, cs<double>(p->w64.Q1, nm, 2 * nm),
                                               Strided<float>{p->w32.Fh, fm32, 2 * fm32}, kDimRF, s)));
     if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
-    // What1 = What0 + dWhat, recompressed in FP64.
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(ra, count, s));
-    // Two passes: the stacked blocks are two near-orthonormal bases, and the
-    // result is the output.
-    if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 2))) return st;
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
-    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
-               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q1, nm, 2 * nm), kDimX,
-                                      Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
-                                      Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
+    // What1 = What0 + dWhat, recompressed.  Two passes: the stacked blocks are
+    // two near-orthonormal bases, and the result is the output.
+    if (d.M <= 64) {
+      // Both blocks hold FP32 values: double-float Grams and products on the
+      // FP32 pipe, FP64-accurate (~1e-13 relative), the first product kept as
+      // (hi, lo) planes for the second pass.
+      RefineArgs rs = ra;
+      rs.X32 = {p->w32.A, nm, 2 * nm};
+      const Strided<const float> a32{p->w32.A, nm, 2 * nm};
+      const Strided<const float> nof{nullptr, 0, 0};
+      const Strided<float> q1h{p->w32.Q1, nm, 2 * nm}, q1l{p->w32.Q2, nm, 2 * nm}, noo{nullptr, 0, 0};
+      const Strided<double> no64{nullptr, 0, 0};
+      Strided<double> G64{p->w64.G, MM, 2 * MM};
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(rs, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(rs, count, s));
+      if ((st = gram_reduce<float>(p, g, a32, kDimX, a32, kDimX, p->w64.part, G64, true, s, true))) return st;
+      LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 0, s));
+      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+                 launch_gemm_dfx(g, p->st, a32, nof, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
+                                 q1l, no64, s));
+      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s,
+                 launch_gram_dd(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
+                                Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX, p->w64.part, s));
+      LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
+      LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 1, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(rs, count, 1, 0.0, d.M, s));
+      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+                 launch_gemm_dfx(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
+                                 Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX,
+                                 Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR, noo, noo,
+                                 Strided<double>{p->w64.U[0], nm, 2 * nm}, s));
+      (void)q1l;
+    } else {
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(ra, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(ra, count, s));
+      if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 2))) return st;
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
+      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+                 launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q1, nm, 2 * nm), kDimX,
+                                        Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
+                                        Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
+    }
     if (step + 1 < p->opts.refine_steps) {
       // Another step refines the FP64 sum: hand it back to the FP32 workspace.
       LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));

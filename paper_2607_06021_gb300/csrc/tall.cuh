@@ -70,6 +70,16 @@ cudaError_t launch_qdeim(const TallGeom& g, const SolveState* st, Strided<const 
                          double* cscore, int32_t* cidx, int cand_blocks, int cand_per_block, int max_c,
                          cudaStream_t s);
 
+// Double-float tall products on the FP32 pipe (dfmat.cu).  Out = A * Bm with A FP32
+// (al.base == nullptr) or (hi, lo) planes, Bm FP64 (M x M, ld M); output FP64
+// when o64.base is set, else (hi, lo) planes.  Gram partials of (hi, lo) data
+// with at most 64 columns (then launch_reduce).
+cudaError_t launch_gemm_dfx(const TallGeom& g, const SolveState* st, Strided<const float> ah, Strided<const float> al,
+                            int sel_in, Strided<const double> bm, int sel_out, Strided<float> oh, Strided<float> ol,
+                            Strided<double> o64, cudaStream_t s);
+cudaError_t launch_gram_dd(const TallGeom& g, const SolveState* st, Strided<const float> xh, Strided<const float> xl,
+                           int sel, double* part, cudaStream_t s);
+
 // Leverage scores of U[s](:, :c) rows (c from sel) and per-block top-c candidates.
 template <typename T>
 cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel,
