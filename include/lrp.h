@@ -304,6 +304,41 @@ lrp_status lrp_plan_kernel_work(lrp_plan_t plan, int32_t kclass, double* flops, 
 /* Clear the launch counts, timings and work totals of a plan. */
 lrp_status lrp_plan_reset_stats(lrp_plan_t plan);
 
+/* ------------------------------------------------------------------ groups
+ *
+ * A group solves one batch as `lanes` concurrent sub-batches: one plan, one CUDA
+ * stream and one host worker thread per lane, so that the lanes' iterations
+ * (each driven from the host) interleave on the GPU and per-problem cores of one
+ * lane overlap tall products of another.  Problems are split into contiguous,
+ * nearly equal shares in order.
+ */
+typedef struct lrp_group_s* lrp_group_t;
+
+/*
+ * Create a group of `lanes` (1..16) plans for n, tol, max_rank; opts->batch is
+ * the group's total capacity, each lane holding ceil(batch / lanes).  Errors as
+ * lrp_plan, plus LRP_EINVAL for lanes out of range or batch < lanes.
+ */
+lrp_status lrp_group_create(lrp_group_t* out, int64_t n, double tol, int32_t max_rank, const lrp_opts* opts,
+                            int32_t lanes);
+
+/*
+ * Solve `count` problems (as lrp_solve_batch; warm-start records are not
+ * accepted).  The lanes start after the work `stream` holds at the call; on
+ * return every lane's work has been enqueued and `stream` waits for it.  Returns
+ * the first lane error, if any.
+ */
+lrp_status lrp_group_solve(lrp_group_t group, int32_t count, const lrp_problem* problems, void* stream);
+
+/* The plan of lane `lane` (for statistics and traces; owned by the group). */
+lrp_status lrp_group_plan(lrp_group_t group, int32_t lane, lrp_plan_t* out);
+
+/* As lrp_plan_pack over the group's last solve: all problems, in order, back to back. */
+lrp_status lrp_group_pack(lrp_group_t group, double* d_packed, int64_t capacity, int64_t* d_offsets, void* stream);
+
+/* Stop the workers and free the lanes' plans. */
+lrp_status lrp_group_destroy(lrp_group_t group);
+
 /* ------------------------------------------------------------------ serving
  *
  * A request server over the batched solver for streams of independent

@@ -109,6 +109,11 @@ def _load():
         "lrp_plan_reset_stats": ([P], I32),
         "lrp_plan_kernel_work": ([P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
         "lrp_plan_pack": ([P, VP, I64, VP, VP], I32),
+        "lrp_group_create": ([ctypes.POINTER(P), I64, D, I32, ctypes.POINTER(lrp_opts), I32], I32),
+        "lrp_group_solve": ([P, I32, ctypes.POINTER(lrp_problem), VP], I32),
+        "lrp_group_plan": ([P, I32, ctypes.POINTER(P)], I32),
+        "lrp_group_pack": ([P, VP, I64, VP, VP], I32),
+        "lrp_group_destroy": ([P], I32),
         "lrp_plan_estimate_bytes": ([I64, D, I32, ctypes.POINTER(lrp_opts), ctypes.POINTER(ctypes.c_size_t)], I32),
         "lrp_server_default_opts": ([ctypes.POINTER(lrp_server_opts)], I32),
         "lrp_request_footprint": ([I64, I32, I32], ctypes.c_size_t),
@@ -162,6 +167,32 @@ def lrp_plan(n: int, tol: float, max_rank: int, opts: lrp_opts | None = None):
     _check(_lib.lrp_plan(ctypes.byref(h), int(n), float(tol), int(max_rank),
                          ctypes.byref(opts) if opts is not None else None), "lrp_plan")
     return h
+
+
+def lrp_group_create(n: int, tol: float, max_rank: int, opts: lrp_opts, lanes: int):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_group_create(ctypes.byref(h), int(n), float(tol), int(max_rank), ctypes.byref(opts), int(lanes)),
+           "lrp_group_create")
+    return h
+
+
+def lrp_group_solve(group, problems, stream) -> int:
+    arr = (lrp_problem * len(problems))(*problems)
+    return _check(_lib.lrp_group_solve(group, len(problems), arr, stream), "lrp_group_solve")
+
+
+def lrp_group_plan(group, lane: int):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_group_plan(group, int(lane), ctypes.byref(h)), "lrp_group_plan")
+    return h
+
+
+def lrp_group_pack(group, d_packed, capacity: int, d_offsets, stream) -> None:
+    _check(_lib.lrp_group_pack(group, d_packed, int(capacity), d_offsets, stream), "lrp_group_pack")
+
+
+def lrp_group_destroy(group) -> None:
+    _check(_lib.lrp_group_destroy(group), "lrp_group_destroy")
 
 
 def lrp_plan_pack(plan, d_packed, capacity: int, d_offsets, stream) -> None:
@@ -323,4 +354,4 @@ def lrp_plan_reset_stats(plan) -> None:
     _check(_lib.lrp_plan_reset_stats(plan), "lrp_plan_reset_stats")
 
 
-from .api import Plan, Server, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401
+from .api import Group, Plan, Server, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401

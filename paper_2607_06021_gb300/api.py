@@ -9,7 +9,8 @@ from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGE
                LRP_SEL_QDEIM,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
-               lrp_plan_set_trace, lrp_plan_trace, lrp_plan_pack,
+               lrp_plan_set_trace, lrp_plan_trace, lrp_plan_pack, lrp_group_create, lrp_group_destroy,
+               lrp_group_pack, lrp_group_plan, lrp_group_solve,
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
                lrp_warm_destroy, lrp_warm_reset, lrp_poll, lrp_request, lrp_server_create,
                lrp_server_default_opts, lrp_server_destroy, lrp_server_get_stats, lrp_server_reset_stats,
@@ -187,7 +188,7 @@ def dst1(X: torch.Tensor, stream=None) -> torch.Tensor:
     return Y
 
 
-__all__ = ["Plan", "Server", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
+__all__ = ["Group", "Plan", "Server", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
 
 
 class Server:
@@ -251,6 +252,82 @@ class Server:
             lrp_server_destroy(self.handle)
             self.handle = None
             self._outputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _LanePlan(Plan):
+    """A lane's plan inside a Group (statistics only; owned by the group)."""
+
+    def __init__(self, handle, n, tol, max_rank, batch):
+        self.handle, self.n, self.tol, self.max_rank, self.batch = handle, n, tol, max_rank, batch
+
+    def close(self):
+        self.handle = None
+
+
+class Group:
+    """lrp_group_*: one batch solved as `lanes` concurrent sub-batches."""
+
+    def __init__(self, n: int, tol: float, max_rank: int, lanes: int, precision: str = "fp64", batch: int = 1,
+                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "ls"):
+        o = lrp_default_opts()
+        o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
+        o.batch, o.max_rhs_rank, o.max_iter, o.m_cap, o.seed = batch, max_rhs_rank, max_iter, m_cap, seed
+        o.selector = LRP_SEL_QDEIM if selector == "qdeim" else LRP_SEL_LEVERAGE
+        self.n, self.tol, self.max_rank, self.batch, self.lanes = n, tol, max_rank, batch, lanes
+        self.handle = lrp_group_create(n, tol, max_rank, o, lanes)
+        per = (batch + lanes - 1) // lanes
+        self.plans = [_LanePlan(lrp_group_plan(self.handle, l), n, tol, max_rank, per) for l in range(lanes)]
+
+    def alloc_outputs(self, device="cuda"):
+        return self.plans[0].alloc_outputs(device)
+
+    def solve_batch_into(self, inputs, outputs, stream=None) -> None:
+        probs = [self.plans[0].problem(*i, o) for i, o in zip(inputs, outputs)]
+        lrp_group_solve(self.handle, probs, _stream(stream))
+
+    def solve_batch(self, inputs, stream=None):
+        outs = [self.alloc_outputs() for _ in inputs]
+        self.solve_batch_into(inputs, outs, stream)
+        torch.cuda.synchronize()
+        res = []
+        for U, S, V, info in outs:
+            inf = parse_info(info)
+            r = inf["rank"]
+            res.append((U[:, :r], S[:r], V[:, :r], inf))
+        return res
+
+    def pack(self, packed: torch.Tensor, offsets: torch.Tensor, stream=None) -> None:
+        lrp_group_pack(self.handle, ctypes.c_void_p(packed.data_ptr()), packed.numel(),
+                       ctypes.c_void_p(offsets.data_ptr()), _stream(stream))
+
+    def kernel_stats(self) -> dict:
+        """Launch counts summed over the lanes (and times / work, see Plan.kernel_stats)."""
+        tot = None
+        for p in self.plans:
+            st = p.kernel_stats()
+            tot = st if tot is None else {k: tuple(a + b for a, b in zip(tot[k], st[k])) for k in tot}
+        return tot
+
+    def reset_stats(self) -> None:
+        for p in self.plans:
+            p.reset_stats()
+
+    def set_timing(self, enable: bool) -> None:
+        for p in self.plans:
+            p.set_timing(enable)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            for p in self.plans:
+                p.close()
+            lrp_group_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -15,10 +15,14 @@
 namespace lrp {
 
 // Offsets (in doubles) of each problem's block [U (n r) | S (r) | V (n r)] and
-// their total in off[count]; one CTA, prefix sum over the problems.
-__global__ void k_pack_offsets(const SolveState* __restrict__ st, int count, int64_t n, int64_t* __restrict__ off) {
+// their total in off[count], starting from *base_in (0 if null); one CTA,
+// prefix sum over the problems.
+__global__ void k_pack_offsets(const SolveState* __restrict__ st, int count, int64_t n, int64_t* __restrict__ off,
+                               const int64_t* __restrict__ base_in) {
   __shared__ int64_t part[1024];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t base = base_in ? *base_in : 0;
+  __syncthreads();  // every thread has read the base before off[0] is written
   const int per = (count + nt - 1) / nt;
   const int b0 = tid * per, b1 = min(count, b0 + per);
   int64_t s = 0;
@@ -29,7 +33,7 @@ __global__ void k_pack_offsets(const SolveState* __restrict__ st, int count, int
   part[tid] = s;
   __syncthreads();
   if (tid == 0) {
-    int64_t acc = 0;
+    int64_t acc = base;
     for (int t = 0; t < nt; ++t) {
       const int64_t v = part[t];
       part[t] = acc;
@@ -82,7 +86,7 @@ extern "C" lrp_status lrp_plan_pack(lrp_plan_t p, double* d_packed, int64_t capa
   const int count = p->last_count;
   if (count < 1) return set_error(LRP_EINVAL, "the plan has not solved a batch yet");
   cudaStream_t s = (cudaStream_t)stream;
-  k_pack_offsets<<<1, 1024, 0, s>>>(p->st, count, p->n, d_offsets);
+  k_pack_offsets<<<1, 1024, 0, s>>>(p->st, count, p->n, d_offsets, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     const dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)count);
