@@ -11,7 +11,7 @@
 //
 //  k_gemm_dfx   Out = A * Bm with A FP32 or (hi, lo), Bm FP64 (split into hi, lo
 //               when staged), Out FP64 or (hi, lo) planes.
-//  k_gram_dd    Gram partials of (hi, lo) data, folded into FP64 every 128 rows.
+//  k_gram_dd    Gram partials of (hi, lo) data, renormalised after every chunk.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -26,7 +26,6 @@ constexpr int DROWS = 128;     // rows per tile
 constexpr int DTILES = 4;      // tiles per CTA
 constexpr int DKC = 32;        // Gram rows per chunk
 constexpr int DMAX = 64;       // widths served by the Gram kernel
-constexpr int DFOLD = 4;       // chunks between FP64 folds
 
 // hi + lo += (ah + al) (bh + bl), see the header.
 __device__ __forceinline__ void dd_madd(float ah, float al, float bh, float bl, float& hi, float& lo) {
@@ -38,6 +37,14 @@ __device__ __forceinline__ void dd_madd(float ah, float al, float bh, float bl, 
   const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   hi = s;
   lo = __fadd_rn(lo, __fadd_rn(e, __fadd_rn(pe, cr)));
+}
+
+// (hi, lo) <- TwoSum(hi, lo): the same value with |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void dd_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+  hi = s;
 }
 
 // (hi, lo) parts of a double: hi = the nearest float, lo = the nearest float to the rest.
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
 
 // Symmetric Gram partials of (hi, lo) data (mx <= 64 columns): 4 x 4 output
 // tiles per thread over the row block, row groups summed in shared memory, every
-// entry a double-float sum folded into FP64 every DFOLD chunks.
+// entry a double-float sum renormalised by TwoSum after every chunk.
 __global__ void __launch_bounds__(DT) k_gram_dd(TallGeom g, const SolveState* __restrict__ st_all,
                                                 Strided<const float> xh, Strided<const float> xl, int sel,
                                                 double* __restrict__ part) {
@@ -179,17 +186,12 @@ __global__ void __launch_bounds__(DT) k_gram_dd(TallGeom g, const SolveState* __
     ia = t0 - ib * (ib + 1) / 2;
   }
   float hi[TS][TS], lo[TS][TS];
-  double tot[TS][TS];
 #pragma unroll
   for (int i = 0; i < TS; ++i)
 #pragma unroll
-    for (int j = 0; j < TS; ++j) {
-      hi[i][j] = lo[i][j] = 0.f;
-      tot[i][j] = 0.0;
-    }
+    for (int j = 0; j < TS; ++j) hi[i][j] = lo[i][j] = 0.f;
   const int wx = tx * TS;
-  int chunk = 0;
-  for (int r = rbeg; r < rend; r += DKC, ++chunk) {
+  for (int r = rbeg; r < rend; r += DKC) {
     for (int e = tid; e < DKC * wx; e += DT) {
       const int kk = e % DKC, c = e / DKC;
       const int row = r + kk;
@@ -211,18 +213,18 @@ __global__ void __launch_bounds__(DT) k_gram_dd(TallGeom g, const SolveState* __
 #pragma unroll
           for (int j = 0; j < TS; ++j) dd_madd(av[i], alv[i], bv[j], blv[j], hi[i][j], lo[i][j]);
       }
-      if ((chunk % DFOLD) == DFOLD - 1 || r + DKC >= rend) {
 #pragma unroll
-        for (int i = 0; i < TS; ++i)
+      for (int i = 0; i < TS; ++i)
 #pragma unroll
-          for (int j = 0; j < TS; ++j) {
-            tot[i][j] += (double)hi[i][j] + (double)lo[i][j];
-            hi[i][j] = lo[i][j] = 0.f;
-          }
-      }
+        for (int j = 0; j < TS; ++j) dd_renorm(hi[i][j], lo[i][j]);
     }
     __syncthreads();
   }
+  double tot[TS][TS];
+#pragma unroll
+  for (int i = 0; i < TS; ++i)
+#pragma unroll
+    for (int j = 0; j < TS; ++j) tot[i][j] = (double)hi[i][j] + (double)lo[i][j];
   double* red = reinterpret_cast<double*>(sm);
   if (own) {
 #pragma unroll

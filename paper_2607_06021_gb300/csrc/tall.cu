@@ -460,6 +460,14 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
 // hi + lo += a * b without rounding the product: a*b = p + pe exactly (one FMA),
 // p is added to hi by TwoSum (Knuth) and every rounding error goes to lo.  The
 // _rn intrinsics keep the compiler from contracting or reordering the steps.
+// (hi, lo) <- TwoSum(hi, lo): the same value with |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+  hi = s;
+}
+
 __device__ __forceinline__ void df_add_product(float a, float b, float& hi, float& lo) {
   const float p = __fmul_rn(a, b);
   const float pe = __fmaf_rn(a, b, -p);
@@ -473,10 +481,10 @@ __device__ __forceinline__ void df_add_product(float a, float b, float& hi, floa
 // Gram partials of FP32 data with near-FP64 accuracy on the FP32 pipe (the first,
 // ill-conditioned CholeskyQR pass of the FP32 iterations).  Same tiling as
 // k_gram_small<float, float, 4, 1>, but each entry is a double-float (hi, lo)
-// sum of exact products, folded into an FP64 total every kDfFold chunks
-// (128 rows): the relative error stays below ~2 (128)^2 eps32^2 ~ 5e-10 in the
-// worst case (~1e-13 typically), against 64x the FP64 pipe's rate.
-constexpr int kDfFold = 4;
+// sum of exact products, renormalised by TwoSum after every chunk so that lo
+// stays within an ulp of hi: the relative error stays below ~n eps32^2 (6e-11
+// at n = 4095) in the worst case, ~1e-13 typically, and only the final sum is
+// converted to FP64 (GB300's FP64 pipe is 1/64 of its FP32 pipe).
 
 __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __restrict__ st_all,
                                                 Strided<const float> xs, int sel_x, double* __restrict__ part) {
@@ -513,14 +521,12 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
   int ia = 0, ib = 0;
   if (own) tile_coords(t0, true, tx, ia, ib);
   float hi[TS][TS], lo[TS][TS];
-  double tot[TS][TS];
 #pragma unroll
   for (int i = 0; i < TS; ++i)
 #pragma unroll
     for (int j = 0; j < TS; ++j) {
       hi[i][j] = 0.f;
       lo[i][j] = 0.f;
-      tot[i][j] = 0.0;
     }
   const int wx = tx * TS;
   constexpr int PF = KC * kSmallGram / NT;  // elements per thread and chunk (8)
@@ -533,8 +539,7 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
     }
   };
   fetch(rbeg);
-  int chunk = 0;
-  for (int r = rbeg; r < rend; r += KC, ++chunk) {
+  for (int r = rbeg; r < rend; r += KC) {
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
       const int e = tid + NT * q, kk = e % KC, c = e / KC;
@@ -552,19 +557,18 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
 #pragma unroll
           for (int j = 0; j < TS; ++j) df_add_product(av[i], bv[j], hi[i][j], lo[i][j]);
       }
-      if ((chunk % kDfFold) == kDfFold - 1 || r + KC >= rend) {
 #pragma unroll
-        for (int i = 0; i < TS; ++i)
+      for (int i = 0; i < TS; ++i)
 #pragma unroll
-          for (int j = 0; j < TS; ++j) {
-            tot[i][j] += (double)hi[i][j] + (double)lo[i][j];
-            hi[i][j] = 0.f;
-            lo[i][j] = 0.f;
-          }
-      }
+        for (int j = 0; j < TS; ++j) df_renorm(hi[i][j], lo[i][j]);
     }
     __syncthreads();
   }
+  double tot[TS][TS];
+#pragma unroll
+  for (int i = 0; i < TS; ++i)
+#pragma unroll
+    for (int j = 0; j < TS; ++j) tot[i][j] = (double)hi[i][j] + (double)lo[i][j];
   if (G == 1) {
     if (own) {
 #pragma unroll
