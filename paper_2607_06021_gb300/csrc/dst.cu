@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "dst.cuh"
 
 namespace lrp {
@@ -298,6 +299,8 @@ void* dst_make_twiddles(int64_t N, bool fp64, cudaStream_t st) {
   return fp64 ? make_twiddles<double>(N, st) : make_twiddles<float>(N, st);
 }
 
+void* dst_make_twiddles_df(int64_t N, cudaStream_t st) { return make_twiddles<dfloat>(N, st); }
+
 size_t dst_smem_bytes(int64_t n, bool fp64) { return (size_t)(n + 1) * (fp64 ? 16 : 8); }
 
 bool dst_smem_supported(int64_t n, bool fp64) {
@@ -369,6 +372,9 @@ cudaError_t dst_configure() {
   LRP_CFG((k_dst1_passB<double, float, float>))
   LRP_CFG((k_dst1_passB<float, double, float>))
   LRP_CFG((k_dst1_passB<float, float, float>))
+  LRP_CFG((k_dst1_smem<double, double, dfloat>))
+  LRP_CFG((k_dst1_passA<double, double, dfloat>))
+  LRP_CFG((k_dst1_passB<double, double, dfloat>))
 #undef LRP_CFG
   return e;
 }
@@ -381,5 +387,7 @@ template cudaError_t dst1_launch<float, double, float>(int64_t, const DstBatch<f
                                                        const void*, cudaStream_t, void*, size_t);
 template cudaError_t dst1_launch<float, float, float>(int64_t, const DstBatch<float, float>&, int, int, int,
                                                      const void*, cudaStream_t, void*, size_t);
+template cudaError_t dst1_launch<double, double, dfloat>(int64_t, const DstBatch<double, double>&, int, int, int,
+                                                         const void*, cudaStream_t, void*, size_t);
 
 }  // namespace lrp

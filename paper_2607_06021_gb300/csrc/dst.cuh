@@ -26,6 +26,8 @@ struct DstBatch {
 // Raises the dynamic shared-memory limit of the DST kernels (call once per process).
 cudaError_t dst_configure();
 void* dst_make_twiddles(int64_t N, bool fp64, cudaStream_t st);
+// Double-float twiddles (for dst1_launch<..., dfloat>).
+void* dst_make_twiddles_df(int64_t N, cudaStream_t st);
 size_t dst_smem_bytes(int64_t n, bool fp64);
 bool dst_smem_supported(int64_t n, bool fp64);
 bool dst_supported(int64_t n);  // n+1 <= 2^21 (shared-memory or multi-pass)

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "core.cuh"
+#include "dfloat.cuh"
 #include "dst.cuh"
 #include "refine.cuh"
 #include "solver.cuh"
@@ -451,7 +452,9 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (s == LRP_OK) {
     p->tw64 = dst_make_twiddles(n + 1, true, st0);
     p->tw32 = dst_make_twiddles(n + 1, false, st0);
-    if (!p->tw64 || !p->tw32) s = set_error(LRP_ENOMEM, "twiddle allocation failed");
+    if (p->opts.precision == LRP_MIXED) p->twdf = dst_make_twiddles_df(n + 1, st0);
+    if (!p->tw64 || !p->tw32 || (p->opts.precision == LRP_MIXED && !p->twdf))
+      s = set_error(LRP_ENOMEM, "twiddle allocation failed");
   }
   if (s == LRP_OK) {
     cudaError_t e = launch_eigenvalues(d.n, p->lam64, p->lam32, st0);
@@ -522,6 +525,7 @@ static void plan_free(lrp_plan_s* p) {
   p->arena.release();
   if (p->tw64) cudaFree(p->tw64);
   if (p->tw32) cudaFree(p->tw32);
+  if (p->twdf) cudaFree(p->twdf);
   if (p->prob_host) cudaFreeHost(p->prob_host);
   if (p->host_ptrs) cudaFreeHost(p->host_ptrs);
   if (p->active_host) cudaFreeHost(p->active_host);
@@ -665,7 +669,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
 // Forward DST of the caller's factors into w.Fh (type T); with do_setup the
 // per-slot state and the h^2-scaled weights are initialised too.
 template <typename T>
-static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, bool do_setup,
+static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, bool do_setup, bool df,
                                 cudaStream_t s) {
   const PlanDims& d = p->dims;
   const int64_t fm = d.ld * w.rf_cap;
@@ -702,6 +706,15 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   job.active_dev = nullptr;
   job.active_stride = 0;
   job.require_active = 0;
+  if constexpr (sizeof(T) == 8) {
+    if (df && p->twdf) {
+      // FP64 data transformed in double-float arithmetic (mixed path)
+      LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+                 (dst1_launch<double, double, dfloat>(d.n, job, d.RF, count, 2, p->twdf, s, p->dst_temp,
+                                                      p->dst_temp_bytes)));
+      return LRP_OK;
+    }
+  }
   const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
              (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
@@ -847,7 +860,8 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
 
 // Final truncation, singular values, info, then W factors = DST of the first r columns.
 template <typename T>
-static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, cudaStream_t s) {
+static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, cudaStream_t s,
+                                 bool df = false) {
   const PlanDims& d = p->dims;
   const int64_t nm = d.ld * d.M;
   CoreBufs<T> cb = make_core_bufs<T>(p, w);
@@ -865,8 +879,16 @@ static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParam
   back.active_stride = 0;
   back.require_active = 0;
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_finalize_impl<T>(cp, cb, back, w.ubufs, nm, 2 * nm, s));
-  const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   const int maxc = p->r_max < d.M ? p->r_max : d.M;
+  if constexpr (sizeof(T) == 8) {
+    if (df && p->twdf) {
+      LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+                 (dst1_launch<double, double, dfloat>(d.n, back, maxc, count, 2, p->twdf, s, p->dst_temp,
+                                                      p->dst_temp_bytes)));
+      return LRP_OK;
+    }
+  }
+  const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
              (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
   return LRP_OK;
@@ -884,7 +906,7 @@ static lrp_status warm_store(lrp_plan_s* p, Workspace<T>& w, const CoreParams& c
 static lrp_status run_fp64(lrp_plan_s* p, int count, cudaStream_t s) {
   CoreParams cp = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   lrp_status st;
-  if ((st = phase_forward<double>(p, p->w64, cp, count, true, s))) return st;
+  if ((st = phase_forward<double>(p, p->w64, cp, count, true, false, s))) return st;
   if ((st = phase_iterate<double>(p, p->w64, cp, count, s))) return st;
   if ((st = warm_store<double>(p, p->w64, cp, s))) return st;
   return phase_finalize<double>(p, p->w64, cp, count, s);
@@ -956,8 +978,9 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   const TallGeom& g = c64.g;
   const Strided<const double> none{nullptr, 0, 0};
   lrp_status st;
-  if ((st = phase_forward<float>(p, p->w32, c32, count, true, s))) return st;
-  if ((st = phase_forward<double>(p, p->w64, c64, count, false, s))) return st;
+  if ((st = phase_forward<float>(p, p->w32, c32, count, true, false, s))) return st;
+  // FP64 transform of the right-hand side for the residual, in double-float
+  if ((st = phase_forward<double>(p, p->w64, c64, count, false, true, s))) return st;
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
   if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
   // Without refinement the FP32 solution is the result (truncated at tol_in).
@@ -1029,7 +1052,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
     }
   }
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
-  return phase_finalize<double>(p, p->w64, c64, count, s);
+  return phase_finalize<double>(p, p->w64, c64, count, s, true);
 }
 }  // namespace lrp
 

@@ -124,6 +124,7 @@ struct lrp_plan_s {
   float* lam32 = nullptr;
   void* tw64 = nullptr;
   void* tw32 = nullptr;
+  void* twdf = nullptr;                  // double-float twiddles (mixed precision)
   lrp::ProblemDev* prob_dev = nullptr;
   lrp::ProblemDev* prob_host = nullptr;  // pinned
   void* host_ptrs = nullptr;             // pinned staging for DST job arrays
