@@ -7,7 +7,7 @@ Sec. 2.1), the index selectors of Algorithm "(Q)DEIM" and Algorithm
 Library primitives serve as single steps (Householder QR, SVD, pinv, pivoted
 QR); nothing is blocked, fused or reordered.
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings where the paper is silent or garbled:
   * initial guess U_{-1}, V_{-1}: orthonormal bases of the transformed RHS
     factors (the paper only says "warm started");
   * leverage scores select the top-c rows deterministically (c = columns of the

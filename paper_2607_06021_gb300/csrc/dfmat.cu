@@ -1,8 +1,8 @@
 // Tall products in double-float arithmetic on the FP32 pipe, for data that are
 // exact FP32 values or double-float (hi, lo) pairs of FP32 planes: the
-// refinement's recompression of the sum of the trial solution and the
-// correction, whose stacked factors are FP32 values (GB300's FP32 pipe is 64x
-// its FP64 pipe).
+// refinement's recompressions of the residual (stacked FP64 factors split into
+// (hi, lo) planes) and of the sum of the trial solution and the correction
+// (stacked FP32 factors).  GB300's FP32 pipe is 64x its FP64 pipe.
 //
 // A product of a = ah + al and b = bh + bl is taken as ah*bh exactly (one FMA
 // gives the rounding error) plus the cross terms ah*bl + al*bh (al*bl is below
@@ -10,7 +10,8 @@
 // of a K-term sum is below ~2 K^2 eps32^2 in the worst case (~1e-13 typically).
 //
 //  k_gemm_dfx   Out = A * Bm with A FP32 or (hi, lo), Bm FP64 (split into hi, lo
-//               when staged), Out FP64 or (hi, lo) planes.
+//               when staged), Out FP64, (hi, lo) planes, or the hi plane alone
+//               (the product rounded to FP32).
 //  k_gram_dd    Gram partials of (hi, lo) data, renormalised after every chunk.
 #include <cuda_runtime.h>
 
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
         if (OUT_DF) {
           const float h = __fadd_rn(hi[i][j], lo[i][j]);
           oh.at(slot, side)[o] = h;
-          ol.at(slot, side)[o] = __fsub_rn(lo[i][j], __fsub_rn(h, hi[i][j]));
+          if (ol.base) ol.at(slot, side)[o] = __fsub_rn(lo[i][j], __fsub_rn(h, hi[i][j]));
         } else {
           o64.at(slot, side)[o] = (double)hi[i][j] + (double)lo[i][j];
         }

@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "core.cuh"
 #include "dense.cuh"
+#include "dfloat.cuh"
 #include "refine.cuh"
 
 namespace lrp {
@@ -35,11 +36,12 @@ __device__ inline void racct(const RefineArgs& a, int slot, int cls, double flop
 
 // Gram passes (symmetric) and triangular applies of one shifted CholeskyQR on
 // two n x m blocks: FP64 classes, or the FP32-pipe classes for the
-// double-float recompression of the sum (FP32 data, w = 4; its second pass
-// reads and writes (hi, lo) planes, w = 8).
-__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m, bool fp32_pipe = false) {
+// double-float recompressions (bytes per element w: 4 for FP32 data, 8 for
+// FP64 data and for (hi, lo) planes).
+__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m, bool fp32_pipe = false,
+                                    double w_elem = 0.0) {
   const double n = a.n;
-  const double w = fp32_pipe ? 4.0 : 8.0;
+  const double w = w_elem > 0.0 ? w_elem : (fp32_pipe ? 4.0 : 8.0);
   racct(a, slot, fp32_pipe ? LRP_K_GRAM_F32 : LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0),
         2.0 * passes * (n * m * w + a.NB * m * (m + 1.0) * 4.0));
   racct(a, slot, LRP_K_REDUCE, 2.0 * passes * a.NB * m * (m + 1.0) / 2.0,
@@ -100,13 +102,15 @@ __global__ void k_prepare_refine(RefineArgs a) {
     const double m = rf + 2.0 * r0, n = a.n;
     // stacked blocks: read Uh_f (FP64) and Uh0 (FP32), write X and the FP64 stash
     racct(a, slot, LRP_K_REFINE, 2.0 * n * r0, 2.0 * n * (rf * 8.0 + r0 * 4.0 + m * 8.0 + r0 * 8.0));
-    racct_cholqr(a, slot, 1, m);
+    if (a.X32lo.base) racct_cholqr(a, slot, 2, m, true, 8.0);
+    else racct_cholqr(a, slot, 1, m);
   }
 }
 
-// Stacked blocks of the residual factors (FP64, ld = a.ld); side 0:
-// [Uh_f | Lambda Uh0 | Uh0], side 1: [Vh_f | Vh0 | Lambda Vh0].  Also stashes
-// Uh0, Vh0 in FP64 for the final sum.
+// Stacked blocks of the residual factors (ld = a.ld); side 0:
+// [Uh_f | Lambda Uh0 | Uh0], side 1: [Vh_f | Vh0 | Lambda Vh0], in FP64, or as
+// double-float (hi, lo) planes when a.X32lo is set.  Also stashes Uh0, Vh0 in
+// FP64 for the final sum.
 __global__ void k_assemble_residual(RefineArgs a) {
   const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
   const SolveState& st = a.st[slot];
@@ -117,8 +121,25 @@ __global__ void k_assemble_residual(RefineArgs a) {
   const double lam = a.lam[i];
   const double* Fh = a.Fh64.at(slot, side);
   const float* U0 = a.U32[st.upar].at(slot, side);
-  double* X = a.X.at(slot, side);
   double* stash = a.stash.at(slot, side);
+  if (a.X32lo.base) {
+    float* Xh = a.X32.at(slot, side);
+    float* Xl = a.X32lo.at(slot, side);
+    auto put = [&](int j, double v) {
+      const dfloat x(v);
+      Xh[(int64_t)j * a.ld + i] = x.hi;
+      Xl[(int64_t)j * a.ld + i] = x.lo;
+    };
+    for (int j = 0; j < rf; ++j) put(j, Fh[(int64_t)j * a.ld + i]);
+    for (int t = 0; t < r0; ++t) {
+      const double u = (double)U0[(int64_t)t * a.ld + i];
+      stash[(int64_t)t * a.ld + i] = u;
+      put(rf + t, side == 0 ? lam * u : u);
+      put(rf + r0 + t, side == 0 ? u : lam * u);
+    }
+    return;
+  }
+  double* X = a.X.at(slot, side);
   for (int j = 0; j < rf; ++j) X[(int64_t)j * a.ld + i] = Fh[(int64_t)j * a.ld + i];
   for (int t = 0; t < r0; ++t) {
     const double u = (double)U0[(int64_t)t * a.ld + i];
@@ -219,7 +240,7 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
   if (tid == 0) {
     st->r = r;
     // the tall product (Q-basis block) * Bf that follows on both sides
-    racct(a, slot, (mode == 1 && a.X32.base) ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r,
+    racct(a, slot, a.X32.base ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r,
           2.0 * a.n * (m + r) * 8.0);
   }
 }

@@ -18,7 +18,8 @@ struct RefineArgs {
   Strided<const double> Fh64;  // FP64 transformed right-hand side, n x rf
   Strided<const float> U32[2]; // FP32 ping-pong factors of the inner solves
   Strided<double> X;           // FP64 stacked blocks, n x M (CholeskyQR input)
-  Strided<float> X32;          // FP32 stacked blocks of the sum (its entries are FP32 values), or base nullptr
+  Strided<float> X32;          // FP32 stacked blocks (the sum's are FP32 values; the residual's the hi plane), or base nullptr
+  Strided<float> X32lo;        // lo plane of the residual's stacked blocks in double-float, or base nullptr
   Strided<double> stash;       // FP64 copy of the trial factors Uh0 / Vh0
   Strided<double> Racc;        // FP64 R of the CholeskyQR passes
   Strided<double> P;           // FP64 inverse of the last pass's R

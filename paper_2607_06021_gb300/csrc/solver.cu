@@ -946,6 +946,7 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.corr_tol = p->tol;
   a.final_tol = p->tol;
   a.X32 = {nullptr, 0, 0};
+  a.X32lo = {nullptr, 0, 0};
   return a;
 }
 
@@ -985,23 +986,68 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
   // Without refinement the FP32 solution is the result (truncated at tol_in).
   if (p->opts.refine_steps == 0) return phase_finalize<float>(p, p->w32, c32, count, s);
+  const int rcap_res = p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M;
   for (int step = 0; step < p->opts.refine_steps; ++step) {
-    // Residual of the trial solution, recompressed in FP64.
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(ra, count, s));
-    // One shifted-Cholesky pass: the residual only needs the accuracy of the
-    // FP32 correction solve, and its cancellation happens in the FP64 core.
-    if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 1))) return st;
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M, s));
-    LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
-               launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.A, nm, 2 * nm), kDimX,
-                                      Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
-                                      Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
-    // FP32 correction solve on the residual (already in transformed variables).
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_setup_correction(ra, count, s));
-    LRP_LAUNCH(p, LRP_K_REFINE, 1, s,
-               (launch_convert<double, float>(d.n, d.ld, count, p->st, cs<double>(p->w64.Q1, nm, 2 * nm),
-                                              Strided<float>{p->w32.Fh, fm32, 2 * fm32}, kDimRF, s)));
+    // Residual of the trial solution, recompressed with FP64 accuracy.  One
+    // shifted-Cholesky pass: the residual only needs the accuracy of the FP32
+    // correction solve, and its cancellation happens in the FP64 core.
+    if (d.M <= 64) {
+      // Stacked blocks as double-float (hi, lo) planes, Grams and products on
+      // the FP32 pipe.  The stacked blocks are numerically rank deficient (the
+      // residual is small because [Uh_f, Lambda Uh0, Uh0] nearly share a
+      // span), so the first pass's shift (above the double-float Gram's
+      // ~1e-13 relative error) leaves Q1 = X R1^{-1} far from orthonormal; a
+      // second pass makes the residual's factors orthonormal, which is what
+      // the FP32 correction solve evaluates its cross entries from.
+      RefineArgs rr = ra;
+      rr.X32 = {p->w32.Q1, nm, 2 * nm};
+      rr.X32lo = {p->w32.Q2, nm, 2 * nm};
+      CoreParams c64r = c64;
+      c64r.shift_rel = 1e-12;
+      Strided<double> G64{p->w64.G, MM, 2 * MM};
+      const Strided<const float> xh{p->w32.Q1, nm, 2 * nm}, xl{p->w32.Q2, nm, 2 * nm};
+      // Q1 planes: the trial's FP32 factors are stashed by the assembly, so
+      // the iteration factor buffers are free until the correction solve.
+      const Strided<float> q1h{p->w32.A, nm, 2 * nm}, q1l{p->w32.U[0], nm, 2 * nm};
+      const Strided<float> noo{nullptr, 0, 0};
+      const Strided<double> no64{nullptr, 0, 0};
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(rr, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(rr, count, s));
+      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s, launch_gram_dd(g, p->st, xh, xl, kDimX, p->w64.part, s));
+      LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
+      LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64r, cb64, kDimX, 0, s));
+      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+                 launch_gemm_dfx(g, p->st, xh, xl, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
+                                 q1l, no64, s));
+      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s,
+                 launch_gram_dd(g, p->st, Strided<const float>{p->w32.A, nm, 2 * nm},
+                                Strided<const float>{p->w32.U[0], nm, 2 * nm}, kDimX, p->w64.part, s));
+      LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
+      LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64r, cb64, kDimX, 1, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(rr, count, 0, p->mixed_residual_tol, rcap_res, s));
+      // The residual's factors, rounded to FP32, are the correction solve's
+      // right-hand side.
+      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+                 launch_gemm_dfx(g, p->st, Strided<const float>{p->w32.A, nm, 2 * nm},
+                                 Strided<const float>{p->w32.U[0], nm, 2 * nm}, kDimX,
+                                 Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
+                                 Strided<float>{p->w32.Fh, fm32, 2 * fm32}, noo, no64, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_setup_correction(ra, count, s));
+    } else {
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(ra, count, s));
+      if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 1))) return st;
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, rcap_res, s));
+      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+                 launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.A, nm, 2 * nm), kDimX,
+                                        Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
+                                        Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
+      // FP32 correction solve on the residual (already in transformed variables).
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_setup_correction(ra, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s,
+                 (launch_convert<double, float>(d.n, d.ld, count, p->st, cs<double>(p->w64.Q1, nm, 2 * nm),
+                                                Strided<float>{p->w32.Fh, fm32, 2 * fm32}, kDimRF, s)));
+    }
     if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
     // What1 = What0 + dWhat, recompressed.  Two passes: the stacked blocks are
     // two near-orthonormal bases, and the result is the output.
