@@ -37,10 +37,19 @@ WORKLOAD = ("n=4095 (h=1/4096), RHS rank 20 = 16 seeded Gaussians + 4 eigenfunct
             "(p,q in 1..64), tol 1e-8, max rank 64, index-set capacity 64")
 METRIC = "Poisson solves/s & p50/p99 latency at rel err<=1e-6, mixed vs plain FP64"
 # ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
-# FP64 4 flop/clk/SM (2 FMA), FP32 256 flop/clk/SM (128 lanes x FMA).
+# FP64 4 flop/clk/SM (2 FMA), FP32 256 flop/clk/SM (128 lanes x FMA).  Double-
+# float arithmetic runs on the FP32 lanes (128 instructions/clk/SM): a multiply-
+# add of FP32 data into a (hi, lo) sum takes 10 instructions (exact product by
+# FMA, TwoSum, low-part sum), one of (hi, lo) data 13 (plus the cross terms), and
+# the FFT's double-float butterflies ~14.8 instructions per nominal flop (an add
+# 20, a multiply 7; a radix-2 butterfly 4 multiplies and 6 adds for 10 flops).
 SMS, SM_GHZ = 152, 2.070
 FP64_PEAK_TFLOPS = SMS * 4 * SM_GHZ / 1e3
 FP32_PEAK_TFLOPS = SMS * 256 * SM_GHZ / 1e3
+FP32_LANE_TOPS = SMS * 128 * SM_GHZ / 1e3
+DF_MADD32_TFLOPS = FP32_LANE_TOPS / 10 * 2
+DF_MADD_TFLOPS = FP32_LANE_TOPS / 13 * 2
+DF_FFT_TFLOPS = FP32_LANE_TOPS / 14.8
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -334,22 +343,47 @@ def gpu_arm(args, rank, world, local_rank, precisions):
     return results, rhss, hbm_peak, peak_src
 
 
-# Kernel classes whose time is bounded by arithmetic rather than HBM, with the
-# pipe that bounds them.  FP64 path: every tall product on the FP64 pipe.  Mixed
-# path: the FP32 iterations' products on the FP32 pipe, the ill-conditioned first
-# CholeskyQR pass (FP64 accumulation) and the refinement's products on FP64.
-ALU_CLASSES = {"fp64": {"gram": "fp64", "gemm": "fp64", "cross": "fp64", "reduce": "fp64"},
-               "mixed": {"gram": "fp64", "gemm": "fp64", "gram_f32": "fp32", "gemm_f32": "fp32", "cross": "fp32"}}
-ALU_PEAKS = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS}
+# The arithmetic pipe of each kernel class with algorithmic flops; every class is
+# held to the roofline max(flops / pipe peak, bytes / HBM peak), its bound the
+# larger term.  FP64 path: every product and the DST on the FP64 pipe.  Mixed
+# path: the FP32 iterations on the FP32 pipe, the double-float Grams, products
+# and DST on the FP32 lanes at their instruction counts.
+PIPES = {"fp64": {"gram": "fp64", "gemm": "fp64", "cross": "fp64", "reduce": "fp64", "dst": "fp64",
+                  "leverage": "fp64"},
+         "mixed": {"gram_f32": "fp32", "gemm_f32": "fp32", "cross": "fp32", "dst": "fp32", "leverage": "fp32",
+                   "reduce": "fp64", "gram_df": "df32", "gemm_df": "df", "dst_df": "df_fft",
+                   "gram": "fp64", "gemm": "fp64"}}
+ALU_PEAKS = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS, "df32": DF_MADD32_TFLOPS,
+             "df": DF_MADD_TFLOPS, "df_fft": DF_FFT_TFLOPS}
+PEAK_SOURCE = {"fp64": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk/SM",
+               "fp32": "FP32 pipe: 152 SMs x 2070 MHz x 256 flop/clk/SM",
+               "df32": "double-float multiply-add of FP32 data: 152 SMs x 2070 MHz x 128 lanes / 10 instructions x 2 flop",
+               "df": "double-float multiply-add of (hi, lo) data: 152 SMs x 2070 MHz x 128 lanes / 13 instructions x 2 flop",
+               "df_fft": "double-float FFT: 152 SMs x 2070 MHz x 128 lanes / 14.8 instructions per flop"}
 # DRAM bytes (read + write) per launch from ncu captures of the mixed bench at
 # batch 128, scaled by batch / 128 (the launches' data grow with the slots);
 # a class whose kernel changed since its capture has no entry.
-TRAFFIC_B128 = {("mixed", "gemm"): (577.1e6, "profiles/k_gemm_nn_double_mixed_n4095_batch128.md")}
+TRAFFIC_B128 = {}
+
+
+def class_bound(prec, name, launches, ms, flops, nbytes, hbm_peak):
+    """Roofline of one kernel class: the larger of its ALU and HBM times."""
+    t = ms / 1e3
+    pipe = PIPES[prec].get(name)
+    t_alu = flops / (ALU_PEAKS[pipe] * 1e12) if pipe else 0.0
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    if pipe and t_alu >= t_hbm:
+        achieved = flops / t / 1e12
+        return {"bound": "alu", "pipe": pipe, "achieved": achieved, "peak": ALU_PEAKS[pipe], "unit": "TFLOP/s",
+                "frac": achieved / ALU_PEAKS[pipe], "algorithmic_per_launch": flops / launches}
+    achieved = nbytes / t / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "algorithmic_per_launch": nbytes / launches}
 
 
 def roofline(res, prec, hbm_peak, peak_src, batch):
     """Dominant kernel class (most event-timed time, among classes with
-    algorithmic work) against its bound."""
+    algorithmic work) against its roofline."""
     ks = {k: v for k, v in res["kernels"].items() if k != "all" and v[2] + v[3] > 0}
     if not ks:
         return None
@@ -357,20 +391,9 @@ def roofline(res, prec, hbm_peak, peak_src, batch):
     launches, ms, flops, nbytes = ks[name]
     if ms <= 0 or launches <= 0:
         return None
-    if name in ALU_CLASSES[prec]:
-        pipe = ALU_CLASSES[prec][name]
-        peak = ALU_PEAKS[pipe]
-        achieved = flops / (ms / 1e3) / 1e12
-        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-               "peak_source": f"{pipe.upper()} pipe: 152 SMs x 2070 MHz x "
-                              f"{'4' if pipe == 'fp64' else '256'} flop/clk/SM"}
-    else:
-        achieved = nbytes / (ms / 1e3) / 1e9
-        out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-               "frac": achieved / hbm_peak, "peak_source": peak_src}
-    out.update({"kernel": name, "launches": launches, "avg_launch_us": 1e3 * ms / launches,
-                "algorithmic_per_launch": (flops if out["bound"] == "alu" else nbytes) / launches,
-                "traffic": None})
+    out = class_bound(prec, name, launches, ms, flops, nbytes, hbm_peak)
+    out["peak_source"] = PEAK_SOURCE[out["pipe"]] if out["bound"] == "alu" else peak_src
+    out.update({"kernel": name, "launches": launches, "avg_launch_us": 1e3 * ms / launches, "traffic": None})
     tr = TRAFFIC_B128.get((prec, name))
     if tr is not None:
         out["traffic"] = tr[0] * batch / 128
@@ -379,17 +402,14 @@ def roofline(res, prec, hbm_peak, peak_src, batch):
 
 
 def class_rooflines(res, prec, hbm_peak):
-    """Every kernel class with algorithmic work, against its own bound."""
+    """Every kernel class with algorithmic work, against its own roofline."""
     out = {}
     for name, (launches, ms, flops, nbytes) in res["kernels"].items():
         if name == "all" or ms <= 0 or flops + nbytes <= 0:
             continue
-        if name in ALU_CLASSES[prec]:
-            peak = ALU_PEAKS[ALU_CLASSES[prec][name]]
-            out[name] = {"bound": "alu_" + ALU_CLASSES[prec][name], "ms": round(ms, 3),
-                         "frac": round(flops / (ms / 1e3) / 1e12 / peak, 4)}
-        else:
-            out[name] = {"bound": "hbm", "ms": round(ms, 3), "frac": round(nbytes / (ms / 1e3) / 1e9 / hbm_peak, 4)}
+        b = class_bound(prec, name, launches, ms, flops, nbytes, hbm_peak)
+        out[name] = {"bound": b["bound"] if b["bound"] == "hbm" else "alu_" + b["pipe"], "ms": round(ms, 3),
+                     "frac": round(b["frac"], 4)}
     return out
 
 

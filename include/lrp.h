@@ -252,7 +252,10 @@ typedef enum lrp_kernel_class {
   LRP_K_REFINE = 11,   /* mixed precision: residual/sum assembly and recompression cores */
   LRP_K_GRAM_F32 = 12, /* partial Gram products with FP32 accumulation (FP32 iterations) */
   LRP_K_GEMM_F32 = 13, /* tall-skinny products on FP32 data (FP32 iterations) */
-  LRP_K_COUNT = 14
+  LRP_K_GRAM_DF = 14,  /* Gram partials in double-float arithmetic on the FP32 pipe (mixed precision) */
+  LRP_K_GEMM_DF = 15,  /* tall-skinny products in double-float arithmetic on the FP32 pipe (mixed precision) */
+  LRP_K_DST_DF = 16,   /* DST-I of FP64 data in double-float arithmetic (mixed precision) */
+  LRP_K_COUNT = 17
 } lrp_kernel_class;
 
 /*

@@ -19,7 +19,7 @@ LRP_NOT_CONVERGED, LRP_RANK_CAPPED, LRP_EAGAIN, LRP_ECAPACITY = 5, 6, 7, 8
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_SEL_LEVERAGE, LRP_SEL_QDEIM = 0, 1
 KERNEL_CLASSES = ["dst", "cross", "gram", "reduce", "gemm", "leverage", "chol", "core", "select", "stop",
-                  "other", "refine", "gram_f32", "gemm_f32"]
+                  "other", "refine", "gram_f32", "gemm_f32", "gram_df", "gemm_df", "dst_df"]
 
 
 class LrpError(RuntimeError):

@@ -45,12 +45,13 @@ __device__ inline double dst_col_flops(int n) {
 }
 
 // Three symmetric Gram passes, two triangular applies, on side sizes m0, m1.
-// FP32 data (w == 4) run every pass on the FP32 pipe (pass 1 in double-float).
+// FP32 data (w == 4) run every pass on the FP32 pipe, pass 1 in double-float.
 __device__ inline void acct_cholqr3(double* row, double n, double m0, double m1, int NB, double w) {
   for (double m : {m0, m1}) {
     const double gf = n * m * (m + 1.0), gb = n * m * w + NB * m * (m + 1.0) / 2.0 * 8.0;
     if (w == 4.0) {
-      acct_add(row, LRP_K_GRAM_F32, 3.0 * gf, 3.0 * gb);
+      acct_add(row, LRP_K_GRAM_DF, gf, gb);
+      acct_add(row, LRP_K_GRAM_F32, 2.0 * gf, 2.0 * gb);
     } else {
       acct_add(row, LRP_K_GRAM, 3.0 * gf, 3.0 * gb);
     }
@@ -85,9 +86,9 @@ __device__ void acct_iteration(double* row, int n_, int p_, int q_, int r_, int 
   }
 }
 
-__device__ void acct_back(double* row, int n_, int r_out, int w_) {
+__device__ void acct_back(double* row, int n_, int r_out, int w_, bool df) {
   const double n = n_, w = w_;
-  acct_add(row, LRP_K_DST, 2.0 * r_out * dst_col_flops(n_), 2.0 * r_out * n * (8.0 + w));
+  acct_add(row, df ? LRP_K_DST_DF : LRP_K_DST, 2.0 * r_out * dst_col_flops(n_), 2.0 * r_out * n * (8.0 + w));
 }
 
 // ------------------------------------------------------------------- kernels
@@ -727,7 +728,7 @@ __global__ void k_finalize(CoreParams p, CoreBufs<T> b, DstBatch<T, double> back
   if (rout < 1) rout = 1;
   stp->r_star = rstar;
   stp->r_out = rout;
-  if (b.acct) acct_back(b.acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rout, (int)sizeof(T));
+  if (b.acct) acct_back(b.acct + (int64_t)slot * 2 * LRP_K_COUNT, p.g.n, rout, (int)sizeof(T), p.dst_df != 0);
   if (rstar > p.r_max) stp->flags |= kFlagRankCapped;
   for (int t = 0; t < rout; ++t) pr.S[t] = s[t];
   T* ub = ubufs[parity];

@@ -40,6 +40,7 @@ struct CoreParams {
   uint64_t seed;
   int selector;        // lrp_selector
   int noise_floor_stop;  // 1: the eta S_min term counts as met once S_min is at the data's noise floor
+  int dst_df;          // 1: the back transform runs in double-float arithmetic (work accounting)
   int cand_blocks;     // leverage candidate blocks per side
   int cand_per_block;
   double* trace;       // [nslots][kTraceLen][kTraceWidth] per-iteration record, or nullptr

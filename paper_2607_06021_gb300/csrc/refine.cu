@@ -35,19 +35,19 @@ __device__ inline void racct(const RefineArgs& a, int slot, int cls, double flop
 }
 
 // Gram passes (symmetric) and triangular applies of one shifted CholeskyQR on
-// two n x m blocks: FP64 classes, or the FP32-pipe classes for the
-// double-float recompressions (bytes per element w: 4 for FP32 data, 8 for
+// two n x m blocks: FP64 classes, or the double-float classes for the
+// recompressions on the FP32 pipe (bytes per element w: 4 for FP32 data, 8 for
 // FP64 data and for (hi, lo) planes).
-__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m, bool fp32_pipe = false,
+__device__ inline void racct_cholqr(const RefineArgs& a, int slot, int passes, double m, bool df = false,
                                     double w_elem = 0.0) {
   const double n = a.n;
-  const double w = w_elem > 0.0 ? w_elem : (fp32_pipe ? 4.0 : 8.0);
-  racct(a, slot, fp32_pipe ? LRP_K_GRAM_F32 : LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0),
+  const double w = w_elem > 0.0 ? w_elem : (df ? 4.0 : 8.0);
+  racct(a, slot, df ? LRP_K_GRAM_DF : LRP_K_GRAM, 2.0 * passes * n * m * (m + 1.0),
         2.0 * passes * (n * m * w + a.NB * m * (m + 1.0) * 4.0));
   racct(a, slot, LRP_K_REDUCE, 2.0 * passes * a.NB * m * (m + 1.0) / 2.0,
         2.0 * passes * (a.NB + 1.0) * m * (m + 1.0) * 4.0);
   if (passes > 1)
-    racct(a, slot, fp32_pipe ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * (passes - 1) * n * m * (m + 1.0),
+    racct(a, slot, df ? LRP_K_GEMM_DF : LRP_K_GEMM, 2.0 * (passes - 1) * n * m * (m + 1.0),
           2.0 * (passes - 1) * n * m * (w + 8.0));
 }
 }  // namespace
@@ -102,6 +102,9 @@ __global__ void k_prepare_refine(RefineArgs a) {
     const double m = rf + 2.0 * r0, n = a.n;
     // stacked blocks: read Uh_f (FP64) and Uh0 (FP32), write X and the FP64 stash
     racct(a, slot, LRP_K_REFINE, 2.0 * n * r0, 2.0 * n * (rf * 8.0 + r0 * 4.0 + m * 8.0 + r0 * 8.0));
+    // the FP64 forward transform of the right-hand side (double-float), one FFT of length N per column
+    const double N = n + 1.0;
+    racct(a, slot, LRP_K_DST_DF, 2.0 * rf * 5.0 * N * log2(N), 2.0 * rf * n * 16.0);
     if (a.X32lo.base) racct_cholqr(a, slot, 2, m, true, 8.0);
     else racct_cholqr(a, slot, 1, m);
   }
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
   if (tid == 0) {
     st->r = r;
     // the tall product (Q-basis block) * Bf that follows on both sides
-    racct(a, slot, a.X32.base ? LRP_K_GEMM_F32 : LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r,
+    racct(a, slot, a.X32.base ? LRP_K_GEMM_DF : LRP_K_GEMM, 2.0 * 2.0 * a.n * m * r,
           2.0 * a.n * (m + r) * 8.0);
   }
 }

@@ -593,7 +593,7 @@ template <typename T>
 static lrp_status gram_reduce(lrp_plan_s* p, const TallGeom& g, Strided<const T> x, int sx, Strided<const T> y,
                               int sy, double* part, Strided<double> G, bool sym, cudaStream_t s, bool acc64 = true) {
   // FP32 data run on the FP32 pipe (FP32 or double-float accumulation)
-  const int cls = (sizeof(T) == 8) ? LRP_K_GRAM : LRP_K_GRAM_F32;
+  const int cls = (sizeof(T) == 8) ? LRP_K_GRAM : (acc64 ? LRP_K_GRAM_DF : LRP_K_GRAM_F32);
   LRP_LAUNCH(p, cls, gram_kernels(p), s, launch_gram<T>(g, p->st, x, sx, y, sy, part, G, sym, s, acc64));
   LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, sx, sy, part, G, sym, s));
   return LRP_OK;
@@ -658,6 +658,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   cp.drop_rel = 64.0 * 2.220446049250313e-16;
   cp.redundancy = redundancy;
   cp.noise_floor_stop = 0;
+  cp.dst_df = 0;
   cp.seed = p->opts.seed;
   cp.selector = p->opts.selector;
   cp.cand_blocks = d.cand_blocks;
@@ -709,7 +710,7 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   if constexpr (sizeof(T) == 8) {
     if (df && p->twdf) {
       // FP64 data transformed in double-float arithmetic (mixed path)
-      LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+      LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
                  (dst1_launch<double, double, dfloat>(d.n, job, d.RF, count, 2, p->twdf, s, p->dst_temp,
                                                       p->dst_temp_bytes)));
       return LRP_OK;
@@ -882,7 +883,7 @@ static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParam
   const int maxc = p->r_max < d.M ? p->r_max : d.M;
   if constexpr (sizeof(T) == 8) {
     if (df && p->twdf) {
-      LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
+      LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
                  (dst1_launch<double, double, dfloat>(d.n, back, maxc, count, 2, p->twdf, s, p->dst_temp,
                                                       p->dst_temp_bytes)));
       return LRP_OK;
@@ -969,6 +970,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   // residual step corrects what they leave.
   c32.max_iter = p->opts.max_iter < p->mixed_inner_max_iter ? p->opts.max_iter : p->mixed_inner_max_iter;
   CoreParams c64 = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
+  c64.dst_df = 1;
   CoreBufs<double> cb64 = make_core_bufs<double>(p, p->w64);
   RefineArgs ra = make_refine_args(p);
   // The correction dW enters the sum at its own size ||dW|| ~ ||W - W0||, so
@@ -981,7 +983,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   lrp_status st;
   if ((st = phase_forward<float>(p, p->w32, c32, count, true, false, s))) return st;
   // FP64 transform of the right-hand side for the residual, in double-float
-  if ((st = phase_forward<double>(p, p->w64, c64, count, false, true, s))) return st;
+  if (p->opts.refine_steps > 0 && (st = phase_forward<double>(p, p->w64, c64, count, false, true, s))) return st;
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
   if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
   // Without refinement the FP32 solution is the result (truncated at tol_in).
@@ -1013,13 +1015,13 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       const Strided<double> no64{nullptr, 0, 0};
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(rr, count, s));
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(rr, count, s));
-      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s, launch_gram_dd(g, p->st, xh, xl, kDimX, p->w64.part, s));
+      LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s, launch_gram_dd(g, p->st, xh, xl, kDimX, p->w64.part, s));
       LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64r, cb64, kDimX, 0, s));
-      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, xh, xl, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
                                  q1l, no64, s));
-      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s,
                  launch_gram_dd(g, p->st, Strided<const float>{p->w32.A, nm, 2 * nm},
                                 Strided<const float>{p->w32.U[0], nm, 2 * nm}, kDimX, p->w64.part, s));
       LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
@@ -1027,7 +1029,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(rr, count, 0, p->mixed_residual_tol, rcap_res, s));
       // The residual's factors, rounded to FP32, are the correction solve's
       // right-hand side.
-      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, Strided<const float>{p->w32.A, nm, 2 * nm},
                                  Strided<const float>{p->w32.U[0], nm, 2 * nm}, kDimX,
                                  Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
@@ -1066,16 +1068,16 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(rs, count, s));
       if ((st = gram_reduce<float>(p, g, a32, kDimX, a32, kDimX, p->w64.part, G64, true, s, true))) return st;
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 0, s));
-      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, a32, nof, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
                                  q1l, no64, s));
-      LRP_LAUNCH(p, LRP_K_GRAM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s,
                  launch_gram_dd(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
                                 Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX, p->w64.part, s));
       LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 1, s));
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(rs, count, 1, 0.0, d.M, s));
-      LRP_LAUNCH(p, LRP_K_GEMM_F32, 1, s,
+      LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
                                  Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX,
                                  Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR, noo, noo,
