@@ -78,6 +78,7 @@ typedef struct lrp_opts {
 #define LRP_FLAG_CAPACITY 4    /* an index set reached m_cap */
 #define LRP_FLAG_BAD_INPUT 8   /* non-finite data met */
 #define LRP_FLAG_STALLED 16    /* an FP32 solve stopped at its noise floor: the change stopped halving */
+#define LRP_FLAG_ROLLED_BACK 32 /* a stalled FP32 solve returned its previous iterate (the last step grew the change) */
 
 typedef struct lrp_info {
   int32_t rank;          /* r = max(min(r*, max_rank), 1) columns written to U, V, S */

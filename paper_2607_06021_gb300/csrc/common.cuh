@@ -62,6 +62,7 @@ enum : int32_t {
   kFlagCapacity = 4,   // index set hit m_cap
   kFlagBadInput = 8,
   kFlagStalled = 16,   // FP32 solve stopped at its noise floor (change stopped halving)
+  kFlagRolledBack = 32,  // a stalled FP32 solve returned its previous iterate
 };
 
 // Size selectors for the generic tall kernels: which per-side dimension of

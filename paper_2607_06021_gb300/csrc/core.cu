@@ -96,10 +96,47 @@ __device__ void acct_back(double* row, int n_, int r_out, int w_, bool df) {
 constexpr int kCholSmemDim = 64;
 constexpr size_t kCholSmemBytes = kCholSmemDim * kCholSmemDim * sizeof(double);
 
-template <typename T>
+// Column l of X = R^{-1} for each of the CTA's warps in turn (columns l = wid,
+// wid + nw, ...): back substitution in axpy form, lanes owning rows
+// i' = lane + 32 q of the running sums s(i') = -sum_{k > i'} R(i', k) x_k, so
+// that each step is one shuffle and one update per lane.  Dropped pivots give
+// zero rows; entries below the diagonal are zeroed.
+template <typename TC, int Q>
+__device__ void chol_inverse_cols(const TC* __restrict__ W, int Lc, TC* __restrict__ X, int ldx, int m,
+                                  const TC* __restrict__ rinv, const int* __restrict__ dropped) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < m; l += nw) {
+    TC acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = TC(0);
+    for (int i = l; i >= 0; --i) {
+      TC si = TC(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q == (i >> 5)) si = acc[q];
+      si = __shfl_sync(0xffffffffu, si, i & 31);
+      const TC xi = dropped[i] ? TC(0) : ((i == l ? TC(1) : TC(0)) + si) * rinv[i];
+      if (lane == (i & 31)) X[(int64_t)l * ldx + i] = xi;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int ip = lane + 32 * q;
+        if (ip < i) acc[q] -= W[(int64_t)i * Lc + ip] * xi;
+      }
+    }
+    for (int i = l + 1 + lane; i < m; i += 32) X[(int64_t)l * ldx + i] = TC(0);
+  }
+}
+
+// Shifted/equilibrated Cholesky of one pass of CholeskyQR for every (problem,
+// side): R with R^T R = G (+ shift), P = R^{-1} and the accumulated R.  TC is the
+// arithmetic type: FP64 for the FP64 path and for the first (ill-conditioned)
+// pass of the FP32 iterations, FP32 for their later passes, whose Grams are
+// near the identity.
+template <typename T, typename TC>
 __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int sel, int pass) {
-  extern __shared__ double chol_smem[];
-  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  extern __shared__ __align__(16) unsigned char chol_raw[];
+  const int slot = slot_of(p.g, blockIdx.x >> 1), side = blockIdx.x & 1;
+  if (slot < 0) return;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
@@ -107,23 +144,24 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   const double* G = b.G.at(slot, side);
   // Working triangle W: shared memory (leading dimension kCholSmemDim) when
   // m <= kCholSmemDim, else the slot's global scratch (leading dimension M).
-  // The R^{-1} / product buffer Tm is always in the slot's scratch (L2-resident),
-  // which keeps the CTA's shared memory at one m_cap^2 block.
+  // The R^{-1} / product buffer Tm is in the slot's scratch (leading
+  // dimension M, L2-resident): the inverse only writes it.
   const bool in_smem = m <= kCholSmemDim;
   const int Lc = in_smem ? kCholSmemDim : M;
   double* base = b.scratch + (int64_t)slot * b.scratch_stride;
-  double* W = in_smem ? chol_smem : base + (int64_t)(8 + side) * M * M;
-  double* Tm = base + (int64_t)(10 + side) * M * M;  // leading dimension M
+  TC* W = in_smem ? reinterpret_cast<TC*>(chol_raw) : reinterpret_cast<TC*>(base + (int64_t)(8 + side) * M * M);
+  TC* Tm = reinterpret_cast<TC*>(base + (int64_t)(10 + side) * M * M);
   double* P = b.P.at(slot, side);
   double* Racc = b.Racc.at(slot, side);
   __shared__ double red[32];
   __shared__ int dropped[kMaxM];
+  __shared__ double dsc[kMaxM];
+  __shared__ TC rinv[kMaxM];
   const int tid = threadIdx.x, nt = blockDim.x;
 
   // Pass 0 equilibrates: W = D G D with D = diag(G_jj^{-1/2}) (zero columns are
   // dropped), so R = R' D^{-1} and R^{-1} = D R'^{-1}; the relative diagonal test
   // on R is unchanged and the shift acts on unit-diagonal data.
-  __shared__ double dsc[kMaxM];
   for (int j = tid; j < m; j += nt) {
     const double gjj = G[(int64_t)j * M + j];
     dsc[j] = (pass == 0) ? ((gjj > 0.0) ? 1.0 / sqrt(gjj) : 0.0) : 1.0;
@@ -133,7 +171,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
     const double v = G[(int64_t)j * M + i] * dsc[i] * dsc[j];
-    W[(int64_t)j * Lc + i] = (i <= j) ? v : 0.0;
+    W[(int64_t)j * Lc + i] = (i <= j) ? (TC)v : TC(0);
     if (i == j) {
       tr += v;
       mx = fmax(mx, v);
@@ -143,22 +181,24 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   mx = block_max(mx, red);
   const double shift = (pass == 0) ? p.shift_rel * tr : 0.0;
   if (pass == 0 && tid == 0) stp->gram_trace[side] = tr;
-  for (int j = tid; j < m; j += nt) W[(int64_t)j * Lc + j] += (dsc[j] > 0.0) ? shift : 0.0;
-  const double thr = (pass == 0) ? 0.0 : p.drop_rel * mx;
+  for (int j = tid; j < m; j += nt) W[(int64_t)j * Lc + j] += (dsc[j] > 0.0) ? (TC)shift : TC(0);
+  const TC thr = (pass == 0) ? TC(0) : (TC)(p.drop_rel * mx);
   __syncthreads();
 
   for (int j = 0; j < m; ++j) {
-    const double d = W[(int64_t)j * Lc + j];
+    const TC d = W[(int64_t)j * Lc + j];
     const bool drop = !(d > thr);
-    const double rjj = drop ? 0.0 : sqrt(d);
+    const TC rjj = drop ? TC(0) : sqrt(d);
+    const TC ri = drop ? TC(0) : TC(1) / rjj;
     __syncthreads();
     for (int l = j + 1 + tid; l < m; l += nt) {
-      double* wl = W + (int64_t)l * Lc + j;
-      *wl = drop ? 0.0 : (*wl / rjj);
+      TC* wl = W + (int64_t)l * Lc + j;
+      *wl = *wl * ri;
     }
     if (tid == 0) {
       W[(int64_t)j * Lc + j] = rjj;
       dropped[j] = drop ? 1 : 0;
+      rinv[j] = ri;
     }
     __syncthreads();
     if (!drop) {
@@ -173,44 +213,35 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
     __syncthreads();
   }
 
-  // P = R^{-1}: column l by back substitution (dropped rows give zeros).
-  for (int l = tid; l < m; l += nt) {
-    double* x = Tm + (int64_t)l * M;
-    for (int i = m - 1; i > l; --i) x[i] = 0.0;
-    for (int i = l; i >= 0; --i) {
-      if (dropped[i]) {
-        x[i] = 0.0;
-        continue;
-      }
-      double s = (i == l) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= l; ++k) s -= W[(int64_t)k * Lc + i] * x[k];
-      x[i] = s / W[(int64_t)i * Lc + i];
-    }
-  }
+  // P = R^{-1} (dropped rows give zeros)
+  if (m <= 64)
+    chol_inverse_cols<TC, 2>(W, Lc, Tm, M, m, rinv, dropped);
+  else
+    chol_inverse_cols<TC, kMaxM / 32>(W, Lc, Tm, M, m, rinv, dropped);
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
-    P[(int64_t)j * M + i] = dsc[i] * Tm[(int64_t)j * M + i];
+    P[(int64_t)j * M + i] = dsc[i] * (double)Tm[(int64_t)j * M + i];
   }
   __syncthreads();
   // Racc <- R (pass 0, undoing the equilibration) or R * Racc.
   if (pass == 0) {
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? W[(int64_t)j * Lc + i] / dsc[j] : 0.0;
+      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? (double)W[(int64_t)j * Lc + i] / dsc[j] : 0.0;
     }
   } else {
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, l = e / m;
-      double s = 0.0;
+      TC s = TC(0);
       if (i <= l)
-        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * Racc[(int64_t)l * M + k];
+        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * (TC)Racc[(int64_t)l * M + k];
       Tm[(int64_t)l * M + i] = s;
     }
     __syncthreads();
     for (int e = tid; e < m * m; e += nt) {
       const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = Tm[(int64_t)j * M + i];
+      Racc[(int64_t)j * M + i] = (double)Tm[(int64_t)j * M + i];
     }
   }
 }
@@ -233,7 +264,8 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
   using TC = T;
   extern __shared__ double core_smem_d[];
   TC* core_smem = reinterpret_cast<TC*>(core_smem_d);
-  const int slot = blockIdx.x;
+  const int slot = slot_of(p.g, blockIdx.x);
+  if (slot < 0) return;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
@@ -504,7 +536,8 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
   extern __shared__ unsigned char smem_raw[];
   double* key = reinterpret_cast<double*>(smem_raw);
   int* id = reinterpret_cast<int*>(key + sort_len);
-  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const int slot = slot_of(p.g, blockIdx.x >> 1), side = blockIdx.x & 1;
+  if (slot < 0) return;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
@@ -599,9 +632,13 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
   }
 }
 
+// Largest best change at which an FP32 solve may stop on a stall (see k_stop).
+constexpr double kStallRhoMax = 1e-3;
+
 template <typename T>
 __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
-  const int slot = blockIdx.x;
+  const int slot = slot_of(p.g, blockIdx.x);
+  if (slot < 0) return;
   SolveState* stp = p.st + slot;
   if (!stp->active) return;
   const int M = p.g.M;
@@ -656,6 +693,7 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
       e[6] = stp->snorm;
       e[7] = stp->cnt_next[0];
     }
+    const double rho_prev = stp->rho;
     stp->rho = rho;
     stp->iters += 1;
     stp->total_iters += 1;
@@ -666,7 +704,9 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
     if (stp->tol_abs > 0.0 && stp->snorm > 0.0) tol_eff = fmax(tol_eff, fmin(0.1, stp->tol_abs / stp->snorm));
     const bool conv = fmax(rho, stp->eta_smin) < tol_eff;
     // FP32 solves: once the change has failed twice in a row to halve its best
-    // value, the iteration moves only within the data's rounding noise.
+    // value, with that best value within the FP32 noise region (<= 1e-3), the
+    // iteration moves only within the data's rounding noise.  Above it the
+    // iteration is still converging, slowly: it continues to max_iter.
     if (p.noise_floor_stop && stp->iters >= 2) {
       if (stp->rho_best == 0.0 || rho < 0.5 * stp->rho_best) {
         stp->rho_best = rho;
@@ -678,13 +718,23 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
     if (conv) {
       stp->flags |= kFlagConverged;
       stp->active = 0;
-    } else if (p.noise_floor_stop && stp->stall >= 2) {
+    } else if (p.noise_floor_stop && stp->stall >= 2 && stp->rho_best <= kStallRhoMax) {
       stp->flags |= kFlagStalled;
       stp->active = 0;
+      // A last step that grew the change (an index update that FP32 noise
+      // made worse) is undone: the previous iterate, still held in the other
+      // half of the ping-pong buffers, is the result.
+      if (stp->iters >= 2 && rho > rho_prev) {
+        stp->k -= 1;
+        stp->r = rp;
+        stp->snorm = stp->snorm_prev;
+        stp->rho = rho_prev;
+        stp->flags |= kFlagRolledBack;
+      }
     } else if (stp->k >= p.max_iter) {
       stp->active = 0;
     }
-    stp->r_prev = r;
+    stp->r_prev = stp->r;
     stp->snorm_prev = stp->snorm;
     stp->cnt[0] = stp->cnt_next[0];
     stp->cnt[1] = stp->cnt_next[1];
@@ -847,22 +897,57 @@ __global__ void k_eigenvalues(int n, double* lam64, float* lam32) {
   if (lam32) lam32[k] = (float)l;
 }
 
-__global__ void k_count_active(const SolveState* st, int nslots, int32_t* out) {
-  __shared__ int c;
-  if (threadIdx.x == 0) c = 0;
-  __syncthreads();
+// Active slots: their count in out[0] and, when list is given, their indices in
+// ascending order in list[0 .. count), then -1 up to nslots (the launch list
+// of the next Cross-DEIM iteration).  One CTA; each thread scans a contiguous
+// chunk of slots and the chunks' counts are prefix-summed across the block.
+__global__ void k_count_active(const SolveState* st, int nslots, int32_t* out, int32_t* list) {
+  __shared__ int wsum[32];
+  __shared__ int total;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = (nslots + nt - 1) / nt;
+  const int b = min(nslots, tid * chunk), e = min(nslots, b + chunk);
   int local = 0;
-  for (int s = threadIdx.x; s < nslots; s += blockDim.x) local += st[s].active ? 1 : 0;
-  atomicAdd(&c, local);
+  for (int s = b; s < e; ++s) local += st[s].active ? 1 : 0;
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[wid] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) *out = c;
+  if (wid == 0) {
+    const int v = lane < (nt >> 5) ? wsum[lane] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane < (nt >> 5)) wsum[lane] = inc - v;
+    if (lane == (nt >> 5) - 1) total = inc;
+  }
+  __syncthreads();
+  if (tid == 0) *out = total;
+  if (!list) return;
+  int pos = wsum[wid] + incl - local;
+  for (int s = b; s < e; ++s)
+    if (st[s].active) list[pos++] = s;
+  for (int i = total + tid; i < nslots; i += nt) list[i] = -1;
 }
 
 // ------------------------------------------------------------------ launches
 
 template <typename T>
 cudaError_t launch_chol(const CoreParams& p, const CoreBufs<T>& b, int sel, int pass, cudaStream_t s) {
-  k_chol<T><<<p.g.nslots * 2, CT, kCholSmemBytes, s>>>(p, b, sel, pass);
+  if constexpr (sizeof(T) == 4) {
+    if (pass > 0) {
+      k_chol<T, float><<<p.g.nslots * 2, CT, kCholSmemDim * kCholSmemDim * sizeof(float), s>>>(p, b, sel, pass);
+      return cudaGetLastError();
+    }
+  }
+  k_chol<T, double><<<p.g.nslots * 2, CT, kCholSmemBytes, s>>>(p, b, sel, pass);
   return cudaGetLastError();
 }
 
@@ -913,9 +998,9 @@ cudaError_t core_configure() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem_bytes<float>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
+    e = cudaFuncSetAttribute(k_chol<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_chol<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
+    e = cudaFuncSetAttribute(k_chol<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemBytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_bytes);
   return e;
@@ -939,8 +1024,8 @@ cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, cudaStream_t s) {
-  k_count_active<<<1, 256, 0, s>>>(st, nslots, out);
+cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, int32_t* list, cudaStream_t s) {
+  k_count_active<<<1, 256, 0, s>>>(st, nslots, out, list);
   return cudaGetLastError();
 }
 

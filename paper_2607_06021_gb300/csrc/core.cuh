@@ -111,6 +111,6 @@ cudaError_t launch_warm_store(const CoreParams& p, const CoreBufs<T>& b, T* cons
 cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t s);
 
 // Number of active slots (written to a host-visible counter).
-cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, cudaStream_t s);
+cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, int32_t* list, cudaStream_t s);
 
 }  // namespace lrp

@@ -67,7 +67,8 @@ __device__ void block_argmax(double& s, int& r, double* ss, int* rr) {
 template <typename T>
 __global__ void __launch_bounds__(QT) k_qdeim_init(TallGeom g, const SolveState* __restrict__ st_all,
                                                    Strided<const T> us, int sel, QdeimBufs q) {
-  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int slot = slot_of(g, blockIdx.y >> 1), side = blockIdx.y & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(QT) k_qdeim_init(TallGeom g, const SolveState*
 template <typename T>
 __global__ void __launch_bounds__(QT) k_qdeim_pivot(TallGeom g, const SolveState* __restrict__ st_all,
                                                     Strided<const T> us, int sel, QdeimBufs q, int j) {
-  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const int slot = slot_of(g, blockIdx.x >> 1), side = blockIdx.x & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);
@@ -169,7 +171,8 @@ __global__ void __launch_bounds__(QT) k_qdeim_pivot(TallGeom g, const SolveState
 template <typename T>
 __global__ void __launch_bounds__(QT) k_qdeim_update(TallGeom g, const SolveState* __restrict__ st_all,
                                                      Strided<const T> us, int sel, QdeimBufs q, int j) {
-  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int slot = slot_of(g, blockIdx.y >> 1), side = blockIdx.y & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);
@@ -218,7 +221,8 @@ __global__ void __launch_bounds__(QT) k_qdeim_update(TallGeom g, const SolveStat
 __global__ void k_qdeim_emit(TallGeom g, const SolveState* __restrict__ st_all, int sel, QdeimBufs q,
                              double* __restrict__ cscore, int32_t* __restrict__ cidx, int cand_blocks,
                              int cand_per_block) {
-  const int slot = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const int slot = slot_of(g, blockIdx.x >> 1), side = blockIdx.x & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);

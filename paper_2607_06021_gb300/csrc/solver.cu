@@ -115,11 +115,12 @@ lrp_status Workspace<T>::allocate(const PlanDims& d, DeviceArena& arena, int rfc
 
 template <typename T>
 void Workspace<T>::release_graphs() {
-  for (auto& g : graphs)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& row : graphs)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
   graph_count = -1;
 }
 
@@ -393,6 +394,7 @@ static lrp_status plan_layout(lrp_plan_s* p) {
   p->lam32 = p->arena.get<float>((size_t)d.n);
   p->prob_dev = p->arena.get<ProblemDev>((size_t)d.B);
   p->active_dev = p->arena.get<int32_t>(4);
+  p->act_list = p->arena.get<int32_t>((size_t)d.B);
   p->acct = p->arena.get<double>((size_t)d.B * 2 * LRP_K_COUNT);
   p->dvec = p->arena.get<double>((size_t)d.B * d.M);
   {
@@ -745,14 +747,15 @@ static lrp_status select_rows(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g,
 // Runs `body` directly, or (when graphs are enabled and timing is off) replays
 // a CUDA graph captured from it on first use for this batch count.
 template <typename T, typename Body>
-static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int kind, cudaStream_t s, Body body) {
+static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int kind, int level, cudaStream_t s,
+                               Body body) {
   if (!p->use_graphs || p->stats.timing || !p->cap_stream) return body(s);
   if (w.graph_count != count) {
     SetupGuard guard;
     w.release_graphs();
     w.graph_count = count;
   }
-  if (!w.graphs[kind]) {
+  if (!w.graphs[kind][level]) {
     CaptureGuard capture;
     int64_t before[LRP_K_COUNT];
     for (int c = 0; c < LRP_K_COUNT; ++c) before[c] = p->stats.launches[c];
@@ -767,19 +770,19 @@ static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int ki
       return st;
     }
     if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("stream capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&w.graphs[kind], graph, 0);
+    e = cudaGraphInstantiate(&w.graphs[kind][level], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      w.graphs[kind] = nullptr;
+      w.graphs[kind][level] = nullptr;
       return set_error(LRP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     for (int c = 0; c < LRP_K_COUNT; ++c) {
-      w.graph_launches[kind][c] = p->stats.launches[c] - before[c];
+      w.graph_launches[kind][level][c] = p->stats.launches[c] - before[c];
       p->stats.launches[c] = before[c];
     }
   }
-  LRP_CUDA(cudaGraphLaunch(w.graphs[kind], s));
-  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += w.graph_launches[kind][c];
+  LRP_CUDA(cudaGraphLaunch(w.graphs[kind][level], s));
+  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += w.graph_launches[kind][level][c];
   return LRP_OK;
 }
 
@@ -803,9 +806,13 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
                                  kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
     // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
     LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_warm_load<T>(cp, cb, Strided<T>{w.U[1], nm, 2 * nm}, s));
-    return select_rows<T>(p, w, g, cs<T>(w.U[1], nm, 2 * nm), kDimC0, s);
+    lrp_status sr = select_rows<T>(p, w, g, cs<T>(w.U[1], nm, 2 * nm), kDimC0, s);
+    if (sr) return sr;
+    // launch list of the first iteration
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, p->act_list, s));
+    return LRP_OK;
   };
-  lrp_status st0 = run_captured<T>(p, w, count, 3, s, init);
+  lrp_status st0 = run_captured<T>(p, w, count, 3, 0, s, init);
   if (st0) return st0;
   Strided<double> Gx{w.X, MM, 2 * MM};
   Strided<double> Ge{w.GE, MM, 2 * MM};
@@ -816,44 +823,59 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   ca.lam = (sizeof(T) == 8) ? (const T*)p->lam64 : (const T*)p->lam32;
   ca.idx = {w.idx, d.M, 2 * (int64_t)d.M};
   ca.A = {w.A, nm, 2 * nm};
+  // Each iteration launches over the compacted list of the slots still active
+  // (k_count_active), in a bucket of the whole batch (level 0) or 2^(level-1)
+  // entries, chosen from the count the host reads back.
+  int level = 0;
   for (int k = 0; k < p->opts.max_iter; ++k) {
     const int par = k & 1;
+    CoreParams cpi = cp;
+    cpi.g.act = p->act_list;
+    cpi.g.nslots = level == 0 ? count : (1 << (level - 1));
+    const TallGeom& gi = cpi.g;
     auto iteration = [&](cudaStream_t s) -> lrp_status {
-      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cp, cb, k == 0 ? kDimC0 : kDimR, s));
-      LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(g, p->st, ca, s));
-      lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.A, nm, 2 * nm, kDimOther, s);
+      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cpi, cb, k == 0 ? kDimC0 : kDimR, s));
+      LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
+      lrp_status st = cholqr3<T>(p, w, gi, cpi, cb, w.A, nm, 2 * nm, kDimOther, s);
       if (st) return st;
-      LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cp, cb, par, s));
+      LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cpi, cb, par, s));
       LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
-                 launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
+                 launch_gemm_nn<T>(gi, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
                                    Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
                                    none, 0, s));
-      st = select_rows<T>(p, w, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, s);
+      st = select_rows<T>(p, w, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, s);
       if (st) return st;
       if (k > 0) {
         // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
-        st = gram_reduce<T>(p, g, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
+        st = gram_reduce<T>(p, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
                             w.part, Gx, false, s, sizeof(T) == 8);
         if (st) return st;
         LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
-                   launch_gemm_nn<T>(g, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
+                   launch_gemm_nn<T>(gi, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
                                      Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
                                      Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
-        st = gram_reduce<T>(p, g, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part,
+        st = gram_reduce<T>(p, gi, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part,
                             Ge, true, s, sizeof(T) == 8);
         if (st) return st;
       }
-      LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cp, cb, par, s));
-      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, s));
+      LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cpi, cb, par, s));
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, p->act_list, s));
       return LRP_OK;
     };
     const int kind = (k == 0) ? 0 : ((k & 1) ? 1 : 2);
-    lrp_status st = run_captured<T>(p, w, count, kind, s, iteration);
+    lrp_status st = run_captured<T>(p, w, count, kind, level, s, iteration);
     if (st) return st;
     if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
       LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       LRP_CUDA(cudaStreamSynchronize(s));
-      if (*p->active_host == 0) break;
+      const int na = *p->active_host;
+      if (na == 0) break;
+      int b = 1, l = 1;
+      while (b < na) {
+        b <<= 1;
+        ++l;
+      }
+      level = (b >= count || l >= kGraphLevels) ? 0 : l;
     }
   }
   return LRP_OK;

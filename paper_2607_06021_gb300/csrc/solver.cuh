@@ -29,6 +29,9 @@ struct DeviceArena {
 
 namespace lrp {
 
+// Launch buckets of the iteration graphs: the whole batch, then 1, 2, 4, ... slots.
+constexpr int kGraphLevels = 18;
+
 lrp_status set_error(lrp_status s, const std::string& msg);
 
 struct PlanDims {
@@ -85,10 +88,11 @@ struct Workspace {
   int rf_cap = 0;  // columns of Fh (and entries of w) per slot and side
   // Captured CUDA graphs of one Cross-DEIM iteration: [0] the first iteration,
   // [1] odd iterations, [2] even iterations >= 2, [3] the initial bases; valid for
-  // graph_count problems (grids depend on the batch count).
+  // graph_count problems.  The second index is the launch bucket: level 0 the
+  // whole batch, level l >= 1 a compacted list of 2^(l-1) active slots.
   int graph_count = -1;
-  cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
-  int64_t graph_launches[4][LRP_K_COUNT] = {};
+  cudaGraphExec_t graphs[4][kGraphLevels] = {};
+  int64_t graph_launches[4][kGraphLevels][LRP_K_COUNT] = {};
   void release_graphs();
   lrp_status allocate(const PlanDims& d, DeviceArena& arena, int rf_cap);
 };
@@ -129,6 +133,7 @@ struct lrp_plan_s {
   lrp::ProblemDev* prob_host = nullptr;  // pinned
   void* host_ptrs = nullptr;             // pinned staging for DST job arrays
   int32_t* active_dev = nullptr;
+  int32_t* act_list = nullptr;           // compacted active slots (written by k_count_active)
   double* acct = nullptr;                // [B][LRP_K_COUNT][2] algorithmic flops / bytes
   double* dvec = nullptr;                // [B][M] weights of the stacked refinement products
   unsigned char* dst_temp = nullptr;     // HBM staging of the multi-pass DST (n+1 > 8192)

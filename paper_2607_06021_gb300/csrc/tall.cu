@@ -33,13 +33,48 @@ constexpr int NT = 256;
 constexpr int kSmallGram = 64;
 constexpr int kSmallRows = 32;
 
+// Cross tile: XR rows x XC columns per CTA, 256 threads; warp w owns columns
+// 8w..8w+7 of the tile and its 32 four-row groups, so that every store of a
+// column segment is 512 contiguous bytes (FP32).
+constexpr int XR = 128;
+constexpr int XC = 64;
+constexpr int XK = 16;
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+// 1 / x: the exact quotient in FP64; in FP32 the correctly rounded reciprocal
+// (the product then carries at most ~1.5 ulp, below the FP32 data's noise).
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __restrict__ st_all, CrossArgs<T> a) {
-  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int m = st.cnt[1 - side];
-  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * TN;
+  const int r0 = blockIdx.x * XR, c0 = blockIdx.y * XC;
   if (c0 >= m || r0 >= g.n) return;
   const int rf = st.rf;
   const T* Fs = a.F.at(slot, side);
@@ -47,65 +82,73 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   const int32_t* ix = a.idx.at(slot, 1 - side);
   const T* w = a.w + (int64_t)slot * a.wstride;
 
-  __shared__ T As[TK][TM];
-  __shared__ T Bs[TK][TN];
-  __shared__ int jc[TN];
-  __shared__ T lamc[TN];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  if (tid < TN) {
+  __shared__ __align__(16) T As[XK][XR];
+  __shared__ __align__(16) T Bs[XK][XC];
+  __shared__ int jc[XC];
+  __shared__ T lamc[XC];
+  const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;  // rows 4 ty.., columns 8 tx..
+  if (tid < XC) {
     const int c = c0 + tid;
     const int j = (c < m) ? ix[c] : -1;
     jc[tid] = j;
     lamc[tid] = (j >= 0) ? a.lam[j] : (T)1;
   }
   __syncthreads();
-  T acc[4][4];
+  T acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int j = 0; j < 8; ++j) acc[i][j] = (T)0;
 
-  for (int k0 = 0; k0 < rf; k0 += TK) {
+  for (int k0 = 0; k0 < rf; k0 += XK) {
 #pragma unroll
-    for (int q = 0; q < (TK * TM) / NT; ++q) {
+    for (int q = 0; q < (XK * XR) / NT; ++q) {
       const int e = tid + NT * q;
-      const int kk = e / TM, i = e % TM;
+      const int kk = e / XR, i = e % XR;
       const int row = r0 + i, k = k0 + kk;
       As[kk][i] = (row < g.n && k < rf) ? Fs[(int64_t)k * g.ld + row] : (T)0;
     }
 #pragma unroll
-    for (int q = 0; q < (TK * TN) / NT; ++q) {
+    for (int q = 0; q < (XK * XC) / NT; ++q) {
       const int e = tid + NT * q;
-      const int kk = e / TN, c = e % TN;
+      const int kk = e / XC, c = e % XC;
       const int k = k0 + kk, j = jc[c];
       Bs[kk][c] = (j >= 0 && k < rf) ? w[k] * Fo[(int64_t)k * g.ld + j] : (T)0;
     }
     __syncthreads();
+    const int kn = min(XK, rf - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      T av[4], b0[4], b1[4];
+      ld4<T>(&As[kk][4 * ty], av);
+      ld4<T>(&Bs[kk][8 * tx], b0);
+      ld4<T>(&Bs[kk][8 * tx + 4], b1);
 #pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-      T av[4], bv[4];
+      for (int i = 0; i < 4; ++i) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] = fma(av[i], b0[j], acc[i][j]);
+          acc[i][j + 4] = fma(av[i], b1[j], acc[i][j + 4]);
+        }
+      }
     }
     __syncthreads();
   }
   T* A = a.A.at(slot, side);
+  const int row0 = r0 + 4 * ty;
+  if (row0 >= g.n) return;
+  T li[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = r0 + ty + 16 * i;
-    if (row >= g.n) continue;
-    const T li = a.lam[row];
+  for (int i = 0; i < 4; ++i) li[i] = (row0 + i < g.n) ? a.lam[row0 + i] : (T)1;
+  // ld is a multiple of 32 and row0 of 4: whole 4-row segments stay inside the
+  // padded column (rows n..ld-1 are padding)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = tx + 16 * j;
-      if (c0 + c < m) A[(int64_t)(c0 + c) * g.ld + row] = acc[i][j] / (li + lamc[c]);
-    }
+  for (int j = 0; j < 8; ++j) {
+    const int c = 8 * tx + j;
+    if (c0 + c >= m) continue;
+    T v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (row0 + i < g.n) ? acc[i][j] * recip(li[i] + lamc[c]) : (T)0;
+    st4<T>(&A[(int64_t)(c0 + c) * g.ld + row0], v);
   }
 }
 
@@ -216,7 +259,8 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
                                                 Strided<const T> zsub, int mode) {
-  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
@@ -337,7 +381,8 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
   constexpr int KC = kSmallRows;          // rows per shared-memory chunk
   constexpr int LDS = kSmallGram + 4;     // padded row length (keeps 16-byte alignment)
   static_assert((kSmallGram / TS) * (kSmallGram / TS) <= NT * TPT, "tiles per thread");
-  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
@@ -491,7 +536,8 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
   constexpr int KC = kSmallRows;
   constexpr int LDS = kSmallGram + 4;
   constexpr int TS = 4;
-  const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x);
@@ -602,7 +648,8 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
 
 __global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int sel_x, int sel_y,
                          const double* __restrict__ part, Strided<double> G, bool symmetric) {
-  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int slot = slot_of(g, blockIdx.y >> 1), side = blockIdx.y & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mx = dim_of(st, side, sel_x), my = dim_of(st, side, sel_y);
@@ -619,11 +666,13 @@ __global__ void k_reduce(TallGeom g, const SolveState* __restrict__ st_all, int 
 }
 
 // Bitonic sort of (score desc, index asc) pairs in shared memory; len a power of two.
-__device__ inline bool before(double sa, int ia, double sb, int ib) {
+template <typename K>
+__device__ inline bool before(K sa, int ia, K sb, int ib) {
   return (sa > sb) || (sa == sb && ia < ib);
 }
 
-__device__ void bitonic_sort(double* key, int* idx, int len) {
+template <typename K>
+__device__ void bitonic_sort(K* key, int* idx, int len) {
   for (int size = 2; size <= len; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int t = threadIdx.x; t < len; t += blockDim.x) {
@@ -632,7 +681,7 @@ __device__ void bitonic_sort(double* key, int* idx, int len) {
           const bool up = ((t & size) == 0);
           const bool t_first = before(key[t], idx[t], key[p], idx[p]);
           if (up != t_first) {
-            const double k = key[t];
+            const K k = key[t];
             key[t] = key[p];
             key[p] = k;
             const int i = idx[t];
@@ -650,10 +699,13 @@ template <typename T>
 __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> us, int sel,
                            double* __restrict__ cscore, int32_t* __restrict__ cidx, int cand_blocks,
                            int cand_per_block, int rows_per_cand_block, int sort_len) {
+  // Scores, their sums and the sort keys are in the data's precision (T): the
+  // FP32 iterations keep them off the FP64 pipe.
   extern __shared__ unsigned char smem_raw[];
-  double* key = reinterpret_cast<double*>(smem_raw);
+  T* key = reinterpret_cast<T*>(smem_raw);
   int* id = reinterpret_cast<int*>(key + sort_len);
-  const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int slot = slot_of(g, blockIdx.y >> 1), side = blockIdx.y & 1;
+  if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int c = dim_of(st, side, sel);
@@ -663,12 +715,12 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
   const T* U = us.at(slot, side);
   for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
     const int row = rbeg + t;
-    double s = -1.0;
+    T s = T(-1);
     int ii = 0x7fffffff;
     if (row < rend) {
-      s = 0.0;
+      s = T(0);
       for (int q = 0; q < c; ++q) {
-        const double v = (double)U[(int64_t)q * g.ld + row];
+        const T v = U[(int64_t)q * g.ld + row];
         s = fma(v, v, s);
       }
       ii = row;
@@ -677,11 +729,11 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
     id[t] = ii;
   }
   __syncthreads();
-  bitonic_sort(key, id, sort_len);
+  bitonic_sort<T>(key, id, sort_len);
   const int64_t base = ((int64_t)(slot * 2 + side) * cand_blocks + blk) * cand_per_block;
   for (int t = threadIdx.x; t < cand_per_block; t += blockDim.x) {
-    const bool ok = (t < c) && (t < sort_len) && key[t] >= 0.0;
-    cscore[base + t] = ok ? key[t] : -1.0;
+    const bool ok = (t < c) && (t < sort_len) && key[t] >= T(0);
+    cscore[base + t] = ok ? (double)key[t] : -1.0;
     cidx[base + t] = ok ? id[t] : -1;
   }
 }
@@ -692,7 +744,7 @@ static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 template <typename T>
 cudaError_t launch_cross(const TallGeom& g, const SolveState* st, const CrossArgs<T>& a, cudaStream_t s) {
-  dim3 grid(cdiv(g.n, TM), cdiv(g.M, TN), g.nslots * 2);
+  dim3 grid(cdiv(g.n, XR), cdiv(g.M, XC), g.nslots * 2);
   k_cross<T><<<grid, NT, 0, s>>>(g, st, a);
   return cudaGetLastError();
 }
@@ -737,7 +789,7 @@ cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> 
   const int rows = cdiv(g.n, cand_blocks);
   int len = 1;
   while (len < rows) len <<= 1;
-  const size_t smem = (size_t)len * (sizeof(double) + sizeof(int));
+  const size_t smem = (size_t)len * (sizeof(T) + sizeof(int));
   auto kern = k_leverage<T>;
   dim3 grid(cand_blocks, g.nslots * 2);
   kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len);

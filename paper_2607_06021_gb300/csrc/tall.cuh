@@ -12,10 +12,16 @@ struct TallGeom {
   int n;        // rows
   int64_t ld;   // leading dimension of every n-row workspace matrix (>= n, multiple of 32)
   int M;        // capacity (m_cap): columns of n-row matrices, order of small matrices
-  int nslots;   // batch slots launched
+  int nslots;   // batch slots launched (grid entries; see act)
   int NB;       // row blocks of the Gram partials
   int rows_per_block;  // ceil(n / NB) rounded up to 32
+  // Slot of each launched entry: act[i] (-1: nothing to do), or the identity
+  // when null.  The Cross-DEIM iterations launch over the compacted list of
+  // the slots still active, so that finished slots cost no CTAs.
+  const int32_t* act = nullptr;
 };
+
+__device__ __forceinline__ int slot_of(const TallGeom& g, int i) { return g.act ? g.act[i] : i; }
 
 template <typename T>
 struct CrossArgs {

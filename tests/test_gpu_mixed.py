@@ -43,3 +43,29 @@ def test_mixed_accuracy_and_refinement_gain(name, seed):
     Uo, So, Vo, oinfo, _ = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, r_max, seed=0,
                                             m_cap=min(2 * r_max + rhs.rank, 256))
     assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) <= 1e-6
+
+
+def test_mixed_batch_error_bar():
+    """A batch of 128 seeded n = 4095 problems (the bench workload, tol 1e-8):
+    every solve within the 1e-6 relative error of the solves/s metric, most of
+    them near tol."""
+    import numpy as np
+
+    import paper_2607_06021_gb300 as lrp
+    from tests.gpu_util import rhs_dev, to_np
+    K = 128
+    rhss = [li.workload_n4095(seed) for seed in range(K)]
+    inputs = [rhs_dev(r) for r in rhss]
+    plan = lrp.Plan(4095, 1e-8, 64, precision="mixed", batch=K, max_rhs_rank=20, m_cap=64)
+    outs = [plan.alloc_outputs() for _ in range(K)]
+    plan.solve_batch_into(inputs, outs)
+    torch.cuda.synchronize()
+    errs = []
+    for i in range(K):
+        r = lrp.parse_info(outs[i][3])["rank"]
+        G = po.SpectralSolution(rhss[i].U, rhss[i].s, rhss[i].V)
+        errs.append(po.rel_error_vs_exact(to_np(outs[i][0][:, :r]), to_np(outs[i][1][:r]), to_np(outs[i][2][:, :r]), G))
+    plan.close()
+    errs = np.array(errs)
+    assert errs.max() <= 1e-6, (int(errs.argmax()), errs.max())
+    assert np.median(errs) <= 1e-7, np.median(errs)
