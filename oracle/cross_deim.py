@@ -11,7 +11,9 @@ Readings where the paper is silent or garbled:
   * initial guess U_{-1}, V_{-1}: orthonormal bases of the transformed RHS
     factors (the paper only says "warm started");
   * leverage scores select the top-c rows deterministically (c = columns of the
-    input basis), ties to the lower index, in place of Bernoulli sampling;
+    input basis), ties to the lower index, in place of Bernoulli sampling; the
+    Bernoulli form of Algorithm LeverageScores is the selector "bernoulli", its
+    c = sample_factor x columns and its draws from Philox4x32-10;
   * new indices are appended after the previous ones in descending score;
   * the growth safeguard adds one index to I_k (not to I_k^*), drawn from the
     SplitMix64 generator (Steele, Lea, Flood 2014) keyed by (seed, k, side),
@@ -55,6 +57,59 @@ def growth_index(seed: int, k: int, side: int, n: int, present) -> int:
     while i in present:
         i = (i + 1) % n
     return int(i)
+
+
+M32 = (1 << 32) - 1
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)   # multipliers of the Philox-4x32 S-box
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)   # Weyl increments of the key schedule
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+    easy as 1, 2, 3", SC 2011): ten rounds of the 4x32 S-box on the counter
+    (c0, c1, c2, c3), the 2x32 key advanced by the Weyl increments before every
+    round but the first.  Counter words may be NumPy uint64 arrays holding
+    32-bit values (vectorised over rows); returns the four output words."""
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & np.uint64(M32) for c in ctr)
+    k0, k1 = int(key[0]) & M32, int(key[1]) & M32
+    m0, m1 = np.uint64(PHILOX_M[0]), np.uint64(PHILOX_M[1])
+    mask, sh = np.uint64(M32), np.uint64(32)
+    for r in range(10):
+        if r:
+            k0 = (k0 + PHILOX_W[0]) & M32
+            k1 = (k1 + PHILOX_W[1]) & M32
+        p0 = m0 * c0  # exact: 32 x 32 -> 64 bits
+        p1 = m1 * c2
+        c0, c1, c2, c3 = ((p1 >> sh) ^ c1 ^ np.uint64(k0)) & mask, p1 & mask, \
+            ((p0 >> sh) ^ c3 ^ np.uint64(k1)) & mask, p0 & mask
+    return c0, c1, c2, c3
+
+
+def philox_uniform(seed: int, k: int, side: int, rows) -> np.ndarray:
+    """Uniform doubles in [0, 1) with 53 random bits, one per row: Philox4x32-10
+    with counter (row, k, side, 0) and key (low, high 32 bits of seed); the
+    double is (x0 >> 5) 2^26 + (x1 >> 6), scaled by 2^-53 (exact)."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    z = np.zeros_like(rows)
+    x0, x1, _, _ = philox4x32_10((rows, z + np.uint64(k & M32), z + np.uint64(side & M32), z),
+                                 (seed & M32, (seed >> 32) & M32))
+    a = (x0 >> np.uint64(5)).astype(np.float64)
+    b = (x1 >> np.uint64(6)).astype(np.float64)
+    return (a * 67108864.0 + b) / 9007199254740992.0
+
+
+def select_bernoulli(U: np.ndarray, seed: int, k: int, side: int, factor: float = 1.0) -> np.ndarray:
+    """Algorithm LeverageScores as printed: row i is sampled independently with
+    probability p_i = min(1, c pi_i), c = factor x (columns of U), pi the
+    leverage scores; c pi_i is evaluated as factor x sum_eta U(i, eta)^2.  The
+    draws are Philox uniforms (philox_uniform); sampled rows in descending score,
+    ties to the lower index."""
+    s = np.sum(U * U, axis=1)
+    p = np.minimum(1.0, factor * s)
+    u = philox_uniform(seed, k, side, np.arange(U.shape[0]))
+    keep = np.nonzero(u < p)[0]
+    order = np.lexsort((keep, -s[keep]))
+    return keep[order]
 
 
 def leverage_scores(U: np.ndarray) -> np.ndarray:
@@ -192,14 +247,19 @@ class CrossDEIMInfo:
 def cross_deim(G, U0, V0, tol: float, r_max: int, maxiter: int = 30,
                selector: str = "ls", seed: int = 0, m_cap: int | None = None,
                inloop_rel: float | None = None, redundancy: float = 1e-12,
-               I0=None, J0=None, A0=None):
+               I0=None, J0=None, A0=None, sample_factor: float = 1.0):
     """Algorithm Cross-DEIM on a matrix given by entry access (G.cols / G.rows).
 
     Returns (U, S, V, info): the first r = max(min(r*, r_max), 1) singular
     triplets of the last cross approximation.
     """
-    sel = SELECTORS[selector]
     n_rows, n_cols = G.shape
+
+    def sel(Ub, k, side):
+        if selector == "bernoulli":
+            return select_bernoulli(Ub, seed, k, side, sample_factor)
+        return SELECTORS[selector](Ub)
+
     U_prev, V_prev = U0, V0
     I = list(I0) if I0 is not None else []
     J = list(J0) if J0 is not None else []
@@ -208,8 +268,8 @@ def cross_deim(G, U0, V0, tol: float, r_max: int, maxiter: int = 30,
     drop_rel = None if inloop_rel is None else inloop_rel * tol
     res = None
     for k in range(maxiter):
-        Istar = sel(U_prev)
-        Jstar = sel(V_prev)
+        Istar = sel(U_prev, k, 0)
+        Jstar = sel(V_prev, k, 1)
         I_new = union_ordered(I, Istar, m_cap)
         if (len(I_new) == len(I) or k == 0) and (m_cap is None or len(I_new) < m_cap):
             g = growth_index(seed, k, 0, n_rows, I_new)
@@ -261,7 +321,7 @@ def orth(X: np.ndarray) -> np.ndarray:
 
 def poisson_solve(U_f, s_f, V_f, tol: float, r_max: int, maxiter: int = 30,
                   selector: str = "ls", seed: int = 0, m_cap: int | None = None,
-                  inloop_rel: float | None = None, warm=None):
+                  inloop_rel: float | None = None, warm=None, sample_factor: float = 1.0):
     """Low-rank Poisson solve of Sec. 3.2.
 
     Fhat = DST(U_f) S_f DST(V_f)^T, Cross-DEIM on What (Eq. g_for_p), then
@@ -279,6 +339,6 @@ def poisson_solve(U_f, s_f, V_f, tol: float, r_max: int, maxiter: int = 30,
         I0, J0, last = warm
         U0, V0, A0 = last[0], last[2], None
     Uh, S, Vh, info = cross_deim(G, U0, V0, tol, r_max, maxiter, selector, seed,
-                                 m_cap, inloop_rel, I0=I0, J0=J0, A0=A0)
+                                 m_cap, inloop_rel, I0=I0, J0=J0, A0=A0, sample_factor=sample_factor)
     info.spectral = (Uh, S, Vh)
     return dst1(Uh), S, dst1(Vh), info, G

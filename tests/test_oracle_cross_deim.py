@@ -220,3 +220,62 @@ def test_warm_resolve_of_perturbed_rhs(seed):
     err_c = po.rel_error_vs_exact(Uc, Sc, Vc, G)
     err_w = po.rel_error_vs_exact(Uw, Sw, Vw, G)
     assert err_w < max(10 * tol, 1.01 * err_c)
+
+
+def test_philox4x32_10_published_known_answers():
+    # Known-answer vectors of Philox4x32-10 published with the generator
+    # (Salmon et al., SC 2011; the Random123 distribution's test vectors).
+    kat = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+           ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+           ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+            (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in kat:
+        got = tuple(int(v) for v in cd.philox4x32_10(ctr, key))
+        assert got == want, [hex(v) for v in got]
+
+
+def test_philox_uniform_range_and_moments():
+    u = cd.philox_uniform(7, 3, 1, np.arange(200000))
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5 * np.sqrt(1 / 12 / u.size)
+    assert abs(u.var() - 1 / 12) < 5 * np.sqrt(1 / 180 / u.size)
+    # distinct counters give distinct draws: no row repeats another's value
+    assert np.unique(u).size == u.size
+
+
+def test_bernoulli_leverage_inclusion_frequencies():
+    # Algorithm LeverageScores samples row i with probability min(1, c pi_i):
+    # over many keys the inclusion frequency of each row is that probability.
+    rng = np.random.default_rng(5)
+    n, c = 120, 4
+    U = np.linalg.qr(rng.standard_normal((n, c)) * np.geomspace(0.01, 10.0, n)[:, None])[0]
+    factor = 3.0
+    p = np.minimum(1.0, factor * np.sum(U * U, axis=1))
+    assert (p == 1.0).any() and (p < 0.05).any()
+    T = 3000
+    hits = np.zeros(n)
+    sizes = []
+    for key in range(T):
+        rows = cd.select_bernoulli(U, key, 2, 0, factor)
+        hits[rows] += 1
+        sizes.append(rows.size)
+        # sampled rows come in descending score, ties to the lower index
+        sc = np.sum(U[rows] ** 2, axis=1)
+        assert np.all(np.diff(sc) <= 0)
+    freq = hits / T
+    sd = np.sqrt(np.maximum(p * (1 - p), 1e-12) / T)
+    assert np.all(np.abs(freq - p) <= 5 * sd + 1e-12), np.max(np.abs(freq - p) / (sd + 1e-12))
+    assert np.all(freq[p == 1.0] == 1.0)
+    assert abs(np.mean(sizes) - p.sum()) < 5 * np.sqrt(np.sum(p * (1 - p)) / T)
+    # expected sample size is at most c = factor x columns
+    assert p.sum() <= factor * c + 1e-12
+
+
+def test_bernoulli_cross_deim_small_grid_within_tolerance():
+    n = 63
+    rhs = li.gaussian_eigen_rhs(n, 11, 3)
+    tol = 1e-8
+    U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, 40, selector="bernoulli", seed=3)
+    W = po.full_grid_solve(rhs.dense())
+    err = np.linalg.norm((U * S) @ V.T - W) / np.linalg.norm(W)
+    assert err < 10 * tol
