@@ -54,7 +54,10 @@ typedef enum lrp_precision {
 
 typedef enum lrp_selector {
   LRP_SEL_LEVERAGE = 0,  /* Algorithm LeverageScores, deterministic top-c (Sec. 2.2.2) */
-  LRP_SEL_QDEIM = 1      /* Algorithm (Q)DEIM: pivoted QR of U^T (Sec. 2.2.1) */
+  LRP_SEL_QDEIM = 1,     /* Algorithm (Q)DEIM: pivoted QR of U^T (Sec. 2.2.1) */
+  LRP_SEL_BERNOULLI = 2  /* Algorithm LeverageScores as printed (Sec. 2.2.2): row i sampled with
+                            probability min(1, c pi_i), c = sample_factor x columns; draws from
+                            Philox4x32-10 keyed by seed, counter (row, iteration, side, 0) */
 } lrp_selector;
 
 /* Solver options.  lrp_default_opts fills the defaults noted here. */
@@ -68,7 +71,10 @@ typedef struct lrp_opts {
   int32_t m_cap;         /* index-set capacity, default min(2*max_rank + max_rhs_rank, 256) */
   int32_t check_every;   /* host reads the active-solve count every this many
                             iterations, default 1 */
-  uint64_t seed;         /* key of the growth-index generator (SplitMix64), default 0 */
+  uint64_t seed;         /* key of the growth-index generator (SplitMix64) and of the
+                            Bernoulli draws (Philox4x32-10), default 0 */
+  double sample_factor;  /* LRP_SEL_BERNOULLI: c / columns, the expected sample size over the
+                            basis width (> 0), default 1 */
 } lrp_opts;
 
 /* Per-problem report, written by the device into caller memory. */

@@ -5,7 +5,8 @@ import ctypes
 
 import torch
 
-from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK, LRP_SEL_LEVERAGE,
+from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGED, LRP_OK, LRP_SEL_BERNOULLI,
+               LRP_SEL_LEVERAGE,
                LRP_SEL_QDEIM,
                LRP_RANK_CAPPED, lrp_default_opts, lrp_dst1, lrp_info, lrp_plan, lrp_plan_destroy,
                lrp_plan_kernel_stats, lrp_plan_kernel_work, lrp_plan_reset_stats, lrp_plan_set_timing,
@@ -46,7 +47,7 @@ class Plan:
 
     def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
-                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls"):
+                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls", sample_factor: float = 1.0):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch = batch
@@ -56,7 +57,8 @@ class Plan:
         o.seed = seed
         o.check_every = check_every
         o.refine_steps = refine_steps
-        o.selector = LRP_SEL_QDEIM if selector == "qdeim" else LRP_SEL_LEVERAGE
+        o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
+        o.sample_factor = sample_factor
         self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
         self.handle = lrp_plan(n, tol, max_rank, o)
 
@@ -278,7 +280,8 @@ class Group:
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch, o.max_rhs_rank, o.max_iter, o.m_cap, o.seed = batch, max_rhs_rank, max_iter, m_cap, seed
-        o.selector = LRP_SEL_QDEIM if selector == "qdeim" else LRP_SEL_LEVERAGE
+        o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
+        o.sample_factor = sample_factor
         self.n, self.tol, self.max_rank, self.batch, self.lanes = n, tol, max_rank, batch, lanes
         self.handle = lrp_group_create(n, tol, max_rank, o, lanes)
         per = (batch + lanes - 1) // lanes

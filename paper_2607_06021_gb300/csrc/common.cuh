@@ -155,6 +155,36 @@ __host__ __device__ inline uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the
+// 4x32 S-box (two 32 x 32 -> 64-bit products, xored with the other counter
+// words and the key), the 2x32 key advanced by the Weyl increments before
+// every round but the first.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = (uint32_t)p1;
+    c[2] = n2;
+    c[3] = (uint32_t)p0;
+  }
+}
+
+// Uniform double in [0, 1) with 53 random bits for (row, iteration k, side):
+// Philox4x32-10 with counter (row, k, side, 0) and key (low, high words of
+// seed); (x0 >> 5) 2^26 + (x1 >> 6), scaled by 2^-53.
+__host__ __device__ inline double philox_uniform(uint64_t seed, uint32_t k, uint32_t side, uint32_t row) {
+  uint32_t c[4] = {row, k, side, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * (1.0 / 9007199254740992.0);
+}
+
 // Device part of a warm-start record (lrp_warm_t).
 struct WarmDev {
   int32_t valid;      // holds a result

@@ -546,8 +546,10 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
   const int total = p.cand_blocks * p.cand_per_block;
   const int64_t base = (int64_t)(slot * 2 + side) * total;
   // Top-c merge of all candidates in chunks that fit the shared sort buffer: each
-  // pass sorts the current best c entries together with the next chunk.
-  const int cc0 = min(c, kMaxM);
+  // pass sorts the current best c entries together with the next chunk.  The
+  // Bernoulli selector keeps every sampled candidate (up to kMaxM), best first.
+  const bool take_all = p.selector == LRP_SEL_BERNOULLI;
+  const int cc0 = take_all ? kMaxM : min(c, kMaxM);
   const int chunk = (total <= sort_len) ? sort_len : sort_len - kMaxM;
   int have = 0;  // best entries kept at key[0..have)
   for (int start = 0; start < total; start += chunk) {
@@ -594,7 +596,7 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
   int32_t* set = b.idx.at(slot, side);
   __shared__ int isnew[kMaxM];
   const int cnt0 = stp->cnt[side];
-  const int cc = min(c, min(sort_len, kMaxM));
+  const int cc = min(take_all ? kMaxM : c, min(sort_len, kMaxM));
   for (int t = threadIdx.x; t < cc; t += blockDim.x) {
     int nw = (key[t] >= 0.0) ? 1 : 0;
     if (nw) {

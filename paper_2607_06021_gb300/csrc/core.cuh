@@ -39,6 +39,7 @@ struct CoreParams {
   double redundancy;   // |diag R| threshold relative to max |diag R| (paper: 1e-12)
   uint64_t seed;
   int selector;        // lrp_selector
+  double sample_factor;  // LRP_SEL_BERNOULLI: c / columns
   int noise_floor_stop;  // 1: the eta S_min term counts as met once S_min is at the data's noise floor
   int dst_df;          // 1: the back transform runs in double-float arithmetic (work accounting)
   int cand_blocks;     // leverage candidate blocks per side

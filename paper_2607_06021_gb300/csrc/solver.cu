@@ -316,6 +316,7 @@ extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   if (!o) return set_error(LRP_EINVAL, "opts is NULL");
   o->precision = LRP_FP64;
   o->selector = LRP_SEL_LEVERAGE;
+  o->sample_factor = 1.0;
   o->max_iter = 30;
   o->refine_steps = 1;
   o->max_rhs_rank = 64;
@@ -338,7 +339,9 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.max_rhs_rank < 1 || o.max_rhs_rank > kMaxRF) return set_error(LRP_EINVAL, "max_rhs_rank out of range");
   if (o.batch < 1 || o.batch > 65535) return set_error(LRP_EINVAL, "batch out of range");
   if (o.precision != LRP_FP64 && o.precision != LRP_MIXED) return set_error(LRP_EINVAL, "unknown precision");
-  if (o.selector != LRP_SEL_LEVERAGE && o.selector != LRP_SEL_QDEIM) return set_error(LRP_EINVAL, "unknown selector");
+  if (o.selector != LRP_SEL_LEVERAGE && o.selector != LRP_SEL_QDEIM && o.selector != LRP_SEL_BERNOULLI)
+    return set_error(LRP_EINVAL, "unknown selector");
+  if (!(o.sample_factor > 0.0) || !(o.sample_factor < 1e300)) return set_error(LRP_EINVAL, "sample_factor must be > 0");
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
   if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
@@ -663,6 +666,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   cp.dst_df = 0;
   cp.seed = p->opts.seed;
   cp.selector = p->opts.selector;
+  cp.sample_factor = p->opts.sample_factor;
   cp.cand_blocks = d.cand_blocks;
   cp.cand_per_block = d.cand_per_block;
   cp.trace = p->trace_on ? p->trace_dev : nullptr;
@@ -725,8 +729,8 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
 }
 
 // Row candidates for the next index-set enrichment from the current factors:
-// leverage scores (Algorithm LeverageScores, the default) or QDEIM pivots
-// (Algorithm IS), both read by k_select.
+// leverage scores (Algorithm LeverageScores: top-c, the default, or Bernoulli
+// sampling) or QDEIM pivots (Algorithm IS), all read by k_select.
 template <typename T>
 static lrp_status select_rows(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, Strided<const T> U, int sel,
                               cudaStream_t s) {
@@ -736,8 +740,16 @@ static lrp_status select_rows(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g,
                launch_qdeim<T>(g, p->st, U, sel, w.qd, w.cand_score, w.cand_idx, d.cand_blocks, d.cand_per_block,
                                d.M, s));
   } else {
+    LevSample ls;
+    if (p->opts.selector == LRP_SEL_BERNOULLI) {
+      ls.on = 1;
+      ls.k_ofs = (sel == kDimC0) ? 0 : 1;  // initial candidates: iteration 0
+      ls.seed = p->opts.seed;
+      ls.factor = p->opts.sample_factor;
+    }
     LRP_LAUNCH(p, LRP_K_LEVERAGE, 1, s,
-               launch_leverage<T>(g, p->st, U, sel, w.cand_score, w.cand_idx, d.cand_blocks, d.cand_per_block, s));
+               launch_leverage<T>(g, p->st, U, sel, w.cand_score, w.cand_idx, d.cand_blocks, d.cand_per_block, s,
+                                  ls));
   }
   return LRP_OK;
 }
@@ -1289,6 +1301,6 @@ extern "C" const char* lrp_status_string(lrp_status s) {
   return "LRP_UNKNOWN";
 }
 
-static_assert(sizeof(lrp_opts) == 40, "lrp_opts layout");
+static_assert(sizeof(lrp_opts) == 48, "lrp_opts layout");
 static_assert(sizeof(lrp_info) == 64, "lrp_info layout");
 static_assert(sizeof(lrp_problem) == 104, "lrp_problem layout");

@@ -698,7 +698,7 @@ __device__ void bitonic_sort(K* key, int* idx, int len) {
 template <typename T>
 __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> us, int sel,
                            double* __restrict__ cscore, int32_t* __restrict__ cidx, int cand_blocks,
-                           int cand_per_block, int rows_per_cand_block, int sort_len) {
+                           int cand_per_block, int rows_per_cand_block, int sort_len, LevSample ls) {
   // Scores, their sums and the sort keys are in the data's precision (T): the
   // FP32 iterations keep them off the FP64 pipe.
   extern __shared__ unsigned char smem_raw[];
@@ -724,6 +724,11 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
         s = fma(v, v, s);
       }
       ii = row;
+      // Bernoulli: keep the row with probability min(1, c pi_i) = min(1, factor s)
+      if (ls.on) {
+        const double pr = fmin(1.0, ls.factor * (double)s);
+        if (!(philox_uniform(ls.seed, (uint32_t)(st.k + ls.k_ofs), (uint32_t)side, (uint32_t)row) < pr)) s = T(-1);
+      }
     }
     key[t] = s;
     id[t] = ii;
@@ -732,7 +737,7 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
   bitonic_sort<T>(key, id, sort_len);
   const int64_t base = ((int64_t)(slot * 2 + side) * cand_blocks + blk) * cand_per_block;
   for (int t = threadIdx.x; t < cand_per_block; t += blockDim.x) {
-    const bool ok = (t < c) && (t < sort_len) && key[t] >= T(0);
+    const bool ok = (t < (ls.on ? cand_per_block : c)) && (t < sort_len) && key[t] >= T(0);
     cscore[base + t] = ok ? (double)key[t] : -1.0;
     cidx[base + t] = ok ? id[t] : -1;
   }
@@ -785,14 +790,14 @@ cudaError_t launch_reduce(const TallGeom& g, const SolveState* st, int sel_x, in
 
 template <typename T>
 cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel, double* cand_score,
-                            int32_t* cand_idx, int cand_blocks, int cand_per_block, cudaStream_t s) {
+                            int32_t* cand_idx, int cand_blocks, int cand_per_block, cudaStream_t s, LevSample ls) {
   const int rows = cdiv(g.n, cand_blocks);
   int len = 1;
   while (len < rows) len <<= 1;
   const size_t smem = (size_t)len * (sizeof(T) + sizeof(int));
   auto kern = k_leverage<T>;
   dim3 grid(cand_blocks, g.nslots * 2);
-  kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len);
+  kern<<<grid, 512, smem, s>>>(g, st, U, sel, cand_score, cand_idx, cand_blocks, cand_per_block, rows, len, ls);
   return cudaGetLastError();
 }
 
@@ -812,7 +817,7 @@ cudaError_t tall_configure() {
                                       Strided<const T>, int, double*, Strided<double>, bool, cudaStream_t,    \
                                       bool);                                                                  \
   template cudaError_t launch_leverage<T>(const TallGeom&, SolveState*, Strided<const T>, int, double*,      \
-                                          int32_t*, int, int, cudaStream_t);
+                                          int32_t*, int, int, cudaStream_t, LevSample);
 LRP_INST(double)
 LRP_INST(float)
 #undef LRP_INST

@@ -86,10 +86,22 @@ cudaError_t launch_gemm_dfx(const TallGeom& g, const SolveState* st, Strided<con
 cudaError_t launch_gram_dd(const TallGeom& g, const SolveState* st, Strided<const float> xh, Strided<const float> xl,
                            int sel, double* part, cudaStream_t s);
 
-// Leverage scores of U[s](:, :c) rows (c from sel) and per-block top-c candidates.
+// Bernoulli form of Algorithm LeverageScores: when on, row i is a candidate
+// with probability min(1, factor * ||U(i,:)||^2), keyed by its score.  The
+// draw belongs to the iteration that uses the candidates: the slot's k plus
+// k_ofs (0 before the first iteration, 1 at the end of iteration k).
+struct LevSample {
+  int on = 0;
+  int k_ofs = 0;
+  uint64_t seed = 0;
+  double factor = 1.0;
+};
+
+// Leverage scores of U[s](:, :c) rows (c from sel) and per-block candidates:
+// the top c rows, or the best cand_per_block sampled rows (Bernoulli).
 template <typename T>
 cudaError_t launch_leverage(const TallGeom& g, SolveState* st, Strided<const T> U, int sel,
                             double* cand_score, int32_t* cand_idx, int cand_blocks, int cand_per_block,
-                            cudaStream_t s);
+                            cudaStream_t s, LevSample ls = LevSample());
 
 }  // namespace lrp
