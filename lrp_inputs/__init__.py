@@ -147,3 +147,13 @@ def serving_stream(count: int, rate: float, seed: int = 0, kmin: int = 8, kmax: 
         rhs = gaussian_eigen_rhs((1 << k) - 1, int(rng.integers(0, 2**31 - 1)), r)
         out.append(Request(float(t[i]), rhs, not fp64, 1e-10 if fp64 else 1e-6, -1))
     return out
+
+
+def initial_bases(n: int, r: int, seed: int) -> LowRankRHS:
+    """Seeded initial guesses U_0, V_0 (n x r, standard normal entries, U drawn
+    before V) for Cross-DEIM on a matrix given by its entries (the test matrices
+    of Sec. 4.1); s is all ones.  The method orthonormalises them itself."""
+    rng = np.random.default_rng(seed)
+    U = np.asfortranarray(rng.standard_normal((n, r)))
+    V = np.asfortranarray(rng.standard_normal((n, r)))
+    return LowRankRHS(n, U, np.ones(r), V)
