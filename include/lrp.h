@@ -60,6 +60,18 @@ typedef enum lrp_selector {
                             Philox4x32-10 keyed by seed, counter (row, iteration, side, 0) */
 } lrp_selector;
 
+/* The matrix Cross-DEIM approximates.  LRP_MAT_POISSON: the transformed solution
+   of the Poisson problem (Sec. 3.2), right-hand side F = U_f diag(s_f) V_f^T.
+   The test matrices of Sec. 4.1 (n x n, FP64 plans only): lrp_problem.d_U_f and
+   d_V_f are then the initial guesses U_0, V_0 (n x r_f; orthonormalised by the
+   solver), d_s_f is unused and may be NULL, and U, S, V approximate the matrix
+   itself. */
+typedef enum lrp_matrix {
+  LRP_MAT_POISSON = 0,
+  LRP_MAT_HILBERT = 1,   /* H(i, j) = 1 / (1 + i + j), i, j from 0 */
+  LRP_MAT_K = 2          /* K(i, j) = (|x_i + y_j| / 2)^5, x_i = -1 + 2i/(n-1), y_j likewise */
+} lrp_matrix;
+
 /* Solver options.  lrp_default_opts fills the defaults noted here. */
 typedef struct lrp_opts {
   int32_t precision;     /* lrp_precision, default LRP_FP64 */
@@ -75,6 +87,8 @@ typedef struct lrp_opts {
                             Bernoulli draws (Philox4x32-10), default 0 */
   double sample_factor;  /* LRP_SEL_BERNOULLI: c / columns, the expected sample size over the
                             basis width (> 0), default 1 */
+  int32_t matrix;        /* lrp_matrix, default LRP_MAT_POISSON */
+  int32_t reserved0;     /* 0 */
 } lrp_opts;
 
 /* Per-problem report, written by the device into caller memory. */

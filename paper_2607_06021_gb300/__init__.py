@@ -18,6 +18,7 @@ LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ECUDA, LRP_ETIMEDOUT = 0, 1, 2, 3, 4
 LRP_NOT_CONVERGED, LRP_RANK_CAPPED, LRP_EAGAIN, LRP_ECAPACITY = 5, 6, 7, 8
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_SEL_LEVERAGE, LRP_SEL_QDEIM, LRP_SEL_BERNOULLI = 0, 1, 2
+LRP_MAT_POISSON, LRP_MAT_HILBERT, LRP_MAT_K = 0, 1, 2
 KERNEL_CLASSES = ["dst", "cross", "gram", "reduce", "gemm", "leverage", "chol", "core", "select", "stop",
                   "other", "refine", "gram_f32", "gemm_f32", "gram_df", "gemm_df", "dst_df"]
 
@@ -33,7 +34,8 @@ class lrp_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("max_rhs_rank", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("m_cap", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("sample_factor", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("sample_factor", ctypes.c_double),
+                ("matrix", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class lrp_info(ctypes.Structure):

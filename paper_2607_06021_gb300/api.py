@@ -47,7 +47,8 @@ class Plan:
 
     def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
-                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls", sample_factor: float = 1.0):
+                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls", sample_factor: float = 1.0,
+                 matrix: str = "poisson"):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch = batch
@@ -59,6 +60,7 @@ class Plan:
         o.refine_steps = refine_steps
         o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
         o.sample_factor = sample_factor
+        o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
         self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
         self.handle = lrp_plan(n, tol, max_rank, o)
 
@@ -276,12 +278,14 @@ class Group:
     """lrp_group_*: one batch solved as `lanes` concurrent sub-batches."""
 
     def __init__(self, n: int, tol: float, max_rank: int, lanes: int, precision: str = "fp64", batch: int = 1,
-                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "ls"):
+                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "ls",
+                 sample_factor: float = 1.0, matrix: str = "poisson"):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch, o.max_rhs_rank, o.max_iter, o.m_cap, o.seed = batch, max_rhs_rank, max_iter, m_cap, seed
         o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
         o.sample_factor = sample_factor
+        o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
         self.n, self.tol, self.max_rank, self.batch, self.lanes = n, tol, max_rank, batch, lanes
         self.handle = lrp_group_create(n, tol, max_rank, o, lanes)
         per = (batch + lanes - 1) // lanes

@@ -818,7 +818,8 @@ __global__ void k_setup(CoreParams p, const ProblemDev* prob, T* w, int wstride,
   const bool act = slot < nactive && prob[slot].rf > 0;
   const int rf = act ? prob[slot].rf : 0;
   const double h = 1.0 / (double)(p.g.n + 1);
-  for (int k = threadIdx.x; k < rf; k += blockDim.x) w[(int64_t)slot * wstride + k] = (T)(h * h * prob[slot].s_f[k]);
+  if (prob[slot].s_f)  // weights of the Poisson right-hand side (unused for a matrix given by entries)
+    for (int k = threadIdx.x; k < rf; k += blockDim.x) w[(int64_t)slot * wstride + k] = (T)(h * h * prob[slot].s_f[k]);
   if (threadIdx.x == 0) {
     SolveState st;
     memset(&st, 0, sizeof(st));

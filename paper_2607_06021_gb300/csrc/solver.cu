@@ -20,6 +20,7 @@
 #include "core.cuh"
 #include "dfloat.cuh"
 #include "dst.cuh"
+#include "matrix.cuh"
 #include "refine.cuh"
 #include "solver.cuh"
 #include "tall.cuh"
@@ -317,6 +318,8 @@ extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   o->precision = LRP_FP64;
   o->selector = LRP_SEL_LEVERAGE;
   o->sample_factor = 1.0;
+  o->matrix = LRP_MAT_POISSON;
+  o->reserved0 = 0;
   o->max_iter = 30;
   o->refine_steps = 1;
   o->max_rhs_rank = 64;
@@ -332,7 +335,9 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   lrp_opts o;
   lrp_default_opts(&o);
   if (opts) o = *opts;
-  if (n < 1 || !is_pow2(n + 1)) return set_error(LRP_EINVAL, "n+1 must be a power of two >= 2");
+  const bool poisson = o.matrix == LRP_MAT_POISSON;
+  if (n < 1 || (poisson && !is_pow2(n + 1))) return set_error(LRP_EINVAL, "n+1 must be a power of two >= 2");
+  if (!poisson && n > (1 << 24)) return set_error(LRP_EINVAL, "n must be at most 2^24 for the test matrices");
   if (!(tol > 0.0) || !(tol < 1.0)) return set_error(LRP_EINVAL, "tol must be in (0, 1)");
   if (max_rank < 1) return set_error(LRP_EINVAL, "max_rank must be >= 1");
   if (o.max_iter < 1 || o.max_iter > 1000) return set_error(LRP_EINVAL, "max_iter out of range");
@@ -342,9 +347,14 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.selector != LRP_SEL_LEVERAGE && o.selector != LRP_SEL_QDEIM && o.selector != LRP_SEL_BERNOULLI)
     return set_error(LRP_EINVAL, "unknown selector");
   if (!(o.sample_factor > 0.0) || !(o.sample_factor < 1e300)) return set_error(LRP_EINVAL, "sample_factor must be > 0");
+  if (o.matrix != LRP_MAT_POISSON && o.matrix != LRP_MAT_HILBERT && o.matrix != LRP_MAT_K)
+    return set_error(LRP_EINVAL, "unknown matrix");
+  if (o.matrix != LRP_MAT_POISSON && o.precision != LRP_FP64)
+    return set_error(LRP_EINVAL, "the test matrices are solved in FP64 only");
+  if (o.matrix == LRP_MAT_K && n < 2) return set_error(LRP_EINVAL, "the K matrix needs n >= 2");
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
-  if (!dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
+  if (poisson && !dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
   if (!fp64 && o.refine_steps != 0 && o.refine_steps != 1)
     return set_error(LRP_EINVAL, "refine_steps must be 0 or 1 (one refinement step is built)");
   p->n = n;
@@ -400,7 +410,7 @@ static lrp_status plan_layout(lrp_plan_s* p) {
   p->act_list = p->arena.get<int32_t>((size_t)d.B);
   p->acct = p->arena.get<double>((size_t)d.B * 2 * LRP_K_COUNT);
   p->dvec = p->arena.get<double>((size_t)d.B * d.M);
-  {
+  if (p->opts.matrix == LRP_MAT_POISSON) {
     const size_t per_col = dst_temp_bytes(n, true);
     const int maxc = max_rank < d.M ? max_rank : d.M;
     const int cols = d.RF > maxc ? d.RF : maxc;
@@ -454,7 +464,7 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   }
   cudaStream_t st0 = nullptr;
   s = plan_layout(p);
-  if (s == LRP_OK) {
+  if (s == LRP_OK && p->opts.matrix == LRP_MAT_POISSON) {
     p->tw64 = dst_make_twiddles(n + 1, true, st0);
     p->tw32 = dst_make_twiddles(n + 1, false, st0);
     if (p->opts.precision == LRP_MIXED) p->twdf = dst_make_twiddles_df(n + 1, st0);
@@ -714,6 +724,11 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   job.active_stride = 0;
   job.require_active = 0;
   if constexpr (sizeof(T) == 8) {
+    if (p->opts.matrix != LRP_MAT_POISSON) {
+      // a matrix given by entries: the initial guesses are used as they are
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_copy_cols(job, d.n, d.RF, s));
+      return LRP_OK;
+    }
     if (df && p->twdf) {
       // FP64 data transformed in double-float arithmetic (mixed path)
       LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
@@ -847,7 +862,17 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
     const TallGeom& gi = cpi.g;
     auto iteration = [&](cudaStream_t s) -> lrp_status {
       LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cpi, cb, k == 0 ? kDimC0 : kDimR, s));
-      LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
+      if constexpr (sizeof(T) == 8) {
+        if (p->opts.matrix != LRP_MAT_POISSON) {
+          LRP_LAUNCH(p, LRP_K_CROSS, 1, s,
+                     launch_cross_matrix(gi, p->st, p->opts.matrix, Strided<double>{(double*)w.A, nm, 2 * nm},
+                                         Strided<const int32_t>{w.idx, d.M, 2 * (int64_t)d.M}, s));
+        } else {
+          LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
+        }
+      } else {
+        LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
+      }
       lrp_status st = cholqr3<T>(p, w, gi, cpi, cb, w.A, nm, 2 * nm, kDimOther, s);
       if (st) return st;
       LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cpi, cb, par, s));
@@ -916,6 +941,10 @@ static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParam
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_finalize_impl<T>(cp, cb, back, w.ubufs, nm, 2 * nm, s));
   const int maxc = p->r_max < d.M ? p->r_max : d.M;
   if constexpr (sizeof(T) == 8) {
+    if (p->opts.matrix != LRP_MAT_POISSON) {
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_copy_cols(back, d.n, maxc, s));
+      return LRP_OK;
+    }
     if (df && p->twdf) {
       LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
                  (dst1_launch<double, double, dfloat>(d.n, back, maxc, count, 2, p->twdf, s, p->dst_temp,
@@ -1142,7 +1171,7 @@ static lrp_status validate_problem(const lrp_plan_s* p, const lrp_problem& pr) {
   const int64_t n = p->n;
   if (pr.warm && pr.warm->plan != p) return set_error(LRP_EINVAL, "warm-start record belongs to another plan");
   if (pr.r_f < 1 || pr.r_f > p->dims.RF) return set_error(LRP_EINVAL, "r_f out of range [1, max_rhs_rank]");
-  if (!pr.d_U_f || !pr.d_V_f || !pr.d_s_f || !pr.d_U || !pr.d_S || !pr.d_V)
+  if (!pr.d_U_f || !pr.d_V_f || (!pr.d_s_f && p->opts.matrix == LRP_MAT_POISSON) || !pr.d_U || !pr.d_S || !pr.d_V)
     return set_error(LRP_EINVAL, "NULL factor pointer");
   if (pr.ldu_f < n || pr.ldv_f < n || pr.ldu < n || pr.ldv < n) return set_error(LRP_EINVAL, "leading dimension < n");
   return LRP_OK;
@@ -1301,6 +1330,6 @@ extern "C" const char* lrp_status_string(lrp_status s) {
   return "LRP_UNKNOWN";
 }
 
-static_assert(sizeof(lrp_opts) == 48, "lrp_opts layout");
+static_assert(sizeof(lrp_opts) == 56, "lrp_opts layout");
 static_assert(sizeof(lrp_info) == 64, "lrp_info layout");
 static_assert(sizeof(lrp_problem) == 104, "lrp_problem layout");

@@ -48,7 +48,7 @@ def test_host_side_argument_checks_need_no_gpu():
 
 def test_struct_layouts_match_header():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
-    assert ctypes.sizeof(pkg.lrp_opts) == 48
+    assert ctypes.sizeof(pkg.lrp_opts) == 56
     assert ctypes.sizeof(pkg.lrp_info) == 64
     assert ctypes.sizeof(pkg.lrp_problem) == 104
     assert ctypes.sizeof(pkg.lrp_server_opts) == 24
