@@ -65,6 +65,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the bench line: solve time, rank and iterations against n (Sec. 4.2 scaling)")
+    ap.add_argument("--sweep-kmin", type=int, default=10)
+    ap.add_argument("--sweep-kmax", type=int, default=20)
+    ap.add_argument("--sweep-seeds", type=int, default=3, help="growth-index seeds per size")
+    ap.add_argument("--sweep-selectors", default="ls,bernoulli,qdeim", help="index selectors of the sweep")
+    ap.add_argument("--sweep-sample-factor", type=float, default=4.0, help="Bernoulli c / columns in the sweep")
+    ap.add_argument("--test-matrices", action="store_true",
+                    help="instead of the bench line: Cross-DEIM on the test matrices of Sec. 4.1")
     ap.add_argument("--serve-requests", type=int, default=800,
                     help="requests of the serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, requests/s")
@@ -597,6 +606,103 @@ def reference_arm(args, rank):
     print(json.dumps(line))
 
 
+def _timed_solve(plan, inputs, torch):
+    """One warm-up solve, then the wall time (ms) of one solve with the
+    device synchronised on both sides, and its result on the host."""
+    plan.solve(*inputs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U, S, V, info = plan.solve(*inputs)
+    torch.cuda.synchronize()
+    return 1e3 * (time.perf_counter() - t0), U, S, V, info
+
+
+def sweep(args):
+    """Solve time, final rank and iterations against n = 2^k - 1 (Sec. 4.2,
+    Figs. of the Poisson solver's scaling), for the paper's right-hand side (one
+    Gaussian, lrp_inputs.paper_gaussian_rhs), tol 1e-6, rank cap 64, mixed and
+    FP64 precision, `sweep_seeds` growth-index seeds per size; the error of
+    every solve against the exact solution (exact sums up to n = 4095, the
+    oracle's stratified row-sample estimate above).  The exponent of time
+    against N_DOF = n^2 is fitted over n >= 2^14 - 1."""
+    import numpy as np
+    import torch
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+    from oracle import poisson as po
+    from tests.gpu_util import rhs_dev, to_np
+    tol, rmax = 1e-6, 64
+    rows = []
+    for k in range(args.sweep_kmin, args.sweep_kmax + 1):
+        n = (1 << k) - 1
+        rhs = li.paper_gaussian_rhs(n)
+        G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+        inputs = rhs_dev(rhs)
+        for prec, sel in [(p, s) for s in args.sweep_selectors.split(",") for p in ("mixed", "fp64")]:
+            t, it, rk, er = [], [], [], []
+            for seed in range(args.sweep_seeds):
+                plan = lrp.Plan(n, tol, rmax, precision=prec, max_rhs_rank=1, seed=seed, selector=sel,
+                                sample_factor=args.sweep_sample_factor)
+                ms, U, S, V, info = _timed_solve(plan, inputs, torch)
+                plan.close()
+                U, S, V = to_np(U), to_np(S), to_np(V)
+                e = (po.rel_error_vs_exact(U, S, V, G) if n <= 4095 else po.rel_error_sampled(U, S, V, G)[0])
+                t.append(ms)
+                it.append(info["total_iterations"])
+                rk.append(info["rank"])
+                er.append(e)
+            rows.append({"n": n, "precision": prec, "selector": sel, "ms_mean": float(np.mean(t)), "ms_std": float(np.std(t)),
+                         "iterations_mean": float(np.mean(it)), "iterations_std": float(np.std(it)),
+                         "rank_mean": float(np.mean(rk)), "rank_std": float(np.std(rk)), "rel_err_max": float(max(er))})
+        torch.cuda.empty_cache()
+    fit = {}
+    for sel in args.sweep_selectors.split(","):
+        for prec in ("mixed", "fp64"):
+            pts = [(2.0 * np.log(r["n"]), np.log(r["ms_mean"])) for r in rows
+                   if r["precision"] == prec and r["selector"] == sel and r["n"] >= 16383]
+            if len(pts) >= 2:
+                x, y = np.array(pts).T
+                fit[f"{sel}/{prec}"] = {"exponent_vs_ndof": float(np.polyfit(x, y, 1)[0]), "sizes": len(pts)}
+    return {"mode": "sweep", "rhs": "exp(-36((x-0.1)^2+(y-0.55)^2)) on [-1,1]^2 (Sec. 4.2, sign read as +)",
+            "tol": tol, "max_rank": rmax, "seeds": args.sweep_seeds, "bernoulli_sample_factor": args.sweep_sample_factor,
+            "rows": rows, "fit_n_ge_16383": fit,
+            "time": "wall time of one solve after a warm-up solve of the same plan, device synchronised"}
+
+
+def test_matrices(args):
+    """Cross-DEIM on the test matrices of Sec. 4.1 (H at tol 1e-9, K at tol
+    1e-6) for three sizes and the QDEIM and leverage-score selectors: time per
+    solve, iterations, rank, and the relative Frobenius error against the matrix
+    (dense up to n = 8192, else from 256 seeded rows)."""
+    import numpy as np
+    import torch
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+    from oracle import matrices as om
+    from tests.gpu_util import rhs_dev, to_np
+    out = []
+    for kind, tol in (("hilbert", 1e-9), ("k", 1e-6)):
+        for n in (1024, 8192, 65536):
+            x0 = li.initial_bases(n, 4, 7)
+            inputs = rhs_dev(x0)
+            G = om.MATRICES[kind](n)
+            for sel in ("qdeim", "ls"):
+                plan = lrp.Plan(n, tol, 128, max_rhs_rank=4, selector=sel, seed=7, matrix=kind)
+                ms, U, S, V, info = _timed_solve(plan, inputs, torch)
+                plan.close()
+                U, S, V = to_np(U), to_np(S), to_np(V)
+                rows = np.arange(n) if n <= 8192 else np.sort(np.random.default_rng(3).choice(n, 256, replace=False))
+                A = G.rows(rows)
+                err = float(np.linalg.norm(A - (U[rows] * S) @ V.T) / np.linalg.norm(A))
+                out.append({"matrix": kind, "n": n, "tol": tol, "selector": sel, "ms": ms,
+                            "iterations": info["iterations"], "rank": info["rank"], "status": info["status"],
+                            "rel_err": err, "error_rows": "all" if n <= 8192 else 256})
+    return {"mode": "test_matrices", "rows": out,
+            "time": "wall time of one solve after a warm-up solve of the same plan, device synchronised"}
+
+
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
@@ -604,6 +710,10 @@ def main():
         reference_arm(args, rank)
         return
     import paper_2607_06021_gb300 as lrp  # noqa: F401  (fails loudly without the library)
+    if args.sweep or args.test_matrices:
+        if rank == 0:
+            print(json.dumps(sweep(args) if args.sweep else test_matrices(args)))
+        return
     if args.precision == "both":
         precisions = ["fp64", "mixed"]
     else:

@@ -157,3 +157,15 @@ def initial_bases(n: int, r: int, seed: int) -> LowRankRHS:
     U = np.asfortranarray(rng.standard_normal((n, r)))
     V = np.asfortranarray(rng.standard_normal((n, r)))
     return LowRankRHS(n, U, np.ones(r), V)
+
+
+def paper_gaussian_rhs(n: int) -> LowRankRHS:
+    """The right-hand side of the paper's Poisson experiment (Sec. 4.2), read as
+    the Gaussian exp(-36((x-0.1)^2 + (y-0.55)^2)) on [-1, 1]^2 (the printed
+    exponent has a sign error that makes it grow without bound), mapped to this
+    grid's unit square by x = 2x' - 1: exp(-144((x'-0.55)^2 + (y'-0.775)^2)),
+    one separable term (rank 1)."""
+    x = grid(n)
+    U = np.asfortranarray(np.exp(-144.0 * (x - 0.55) ** 2)[:, None])
+    V = np.asfortranarray(np.exp(-144.0 * (x - 0.775) ** 2)[:, None])
+    return LowRankRHS(n, U, np.ones(1), V)
