@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--refine-steps", type=int, default=1,
+                    help="mixed precision: 1 residual-correction step, or 2 (a second one where the first looks unreliable)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line: solve time, rank and iterations against n (Sec. 4.2 scaling)")
     ap.add_argument("--sweep-kmin", type=int, default=10)
@@ -287,9 +289,11 @@ def gpu_arm(args, rank, world, local_rank, precisions):
     results = {}
     for prec in precisions:
         if args.lanes > 1:
-            plan = lrp.Group(N, TOL, RMAX, lanes=args.lanes, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP)
+            plan = lrp.Group(N, TOL, RMAX, lanes=args.lanes, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
+                             refine_steps=args.refine_steps)
         else:
-            plan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP)
+            plan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
+                            refine_steps=args.refine_steps)
 
         def step():
             with torch.cuda.stream(stream):
@@ -338,7 +342,8 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         # one plan of the same batch, so that no launch shares the GPU with
         # another lane's (concurrent lanes would fold their waits into each
         # launch's event interval).
-        tplan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP)
+        tplan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
+                         refine_steps=args.refine_steps)
         with torch.cuda.stream(stream):
             tplan.solve_batch_into(batch.inputs, batch.outputs, stream)
         tplan.set_timing(True)
@@ -729,6 +734,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch_per_gpu": args.batch, "lanes": args.lanes, "precision": head,
+                   "refine_steps": args.refine_steps,
                    "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"},
         "latency_ms": {"p50": statistics.median(ms), "p99": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
                        "note": "per step; every solve of a batch completes at the end of its step"},

@@ -77,7 +77,9 @@ typedef struct lrp_opts {
   int32_t precision;     /* lrp_precision, default LRP_FP64 */
   int32_t selector;      /* lrp_selector, default LRP_SEL_LEVERAGE */
   int32_t max_iter;      /* Cross-DEIM iterations, default 30 */
-  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps, 1 (default) or 0 (FP32 result) */
+  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps: 0 (the FP32 result), 1 (default),
+                            or 2: a second step for the problems whose first correction looks
+                            unreliable (LRP_FLAG_REFINED_TWICE; the others are unchanged) */
   int32_t max_rhs_rank;  /* capacity for r_f, default 64 (<= 256) */
   int32_t batch;         /* max problems per lrp_solve_batch call, default 1 */
   int32_t m_cap;         /* index-set capacity, default min(2*max_rank + max_rhs_rank, 256) */
@@ -99,6 +101,7 @@ typedef struct lrp_opts {
 #define LRP_FLAG_BAD_INPUT 8   /* non-finite data met */
 #define LRP_FLAG_STALLED 16    /* an FP32 solve stopped at its noise floor: the change stopped halving */
 #define LRP_FLAG_ROLLED_BACK 32 /* a stalled FP32 solve returned its previous iterate (the last step grew the change) */
+#define LRP_FLAG_REFINED_TWICE 64 /* the first correction looked unreliable: a second refinement step ran */
 
 typedef struct lrp_info {
   int32_t rank;          /* r = max(min(r*, max_rank), 1) columns written to U, V, S */

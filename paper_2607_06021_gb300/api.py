@@ -279,9 +279,10 @@ class Group:
 
     def __init__(self, n: int, tol: float, max_rank: int, lanes: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "ls",
-                 sample_factor: float = 1.0, matrix: str = "poisson"):
+                 sample_factor: float = 1.0, matrix: str = "poisson", refine_steps: int = 1):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
+        o.refine_steps = refine_steps
         o.batch, o.max_rhs_rank, o.max_iter, o.m_cap, o.seed = batch, max_rhs_rank, max_iter, m_cap, seed
         o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
         o.sample_factor = sample_factor

@@ -54,6 +54,7 @@ struct SolveState {
   double tol_abs;        // > 0: also accept changes below tol_abs in absolute terms (correction solves)
   double rho_best;       // smallest rho of this solve after its first iteration (0: none yet)
   int32_t stall;         // iterations since rho last fell below half of rho_best
+  double rho_jump;       // largest rho / rho_best seen after rho_best was first set
 };
 
 enum : int32_t {
@@ -63,6 +64,8 @@ enum : int32_t {
   kFlagBadInput = 8,
   kFlagStalled = 16,   // FP32 solve stopped at its noise floor (change stopped halving)
   kFlagRolledBack = 32,  // a stalled FP32 solve returned its previous iterate
+  kFlagRefinedTwice = 64,  // a second refinement step ran
+  kFlagHeld = 128,     // internal: kept out of the second refinement step
 };
 
 // Size selectors for the generic tall kernels: which per-side dimension of

@@ -710,6 +710,7 @@ __global__ void k_stop(CoreParams p, CoreBufs<T> b, int parity) {
     // iteration moves only within the data's rounding noise.  Above it the
     // iteration is still converging, slowly: it continues to max_iter.
     if (p.noise_floor_stop && stp->iters >= 2) {
+      if (stp->rho_best > 0.0) stp->rho_jump = fmax(stp->rho_jump, rho / stp->rho_best);
       if (stp->rho_best == 0.0 || rho < 0.5 * stp->rho_best) {
         stp->rho_best = rho;
         stp->stall = 0;

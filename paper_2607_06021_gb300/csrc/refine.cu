@@ -123,7 +123,9 @@ __global__ void k_assemble_residual(RefineArgs a) {
   const int rf = st.rf0, r0 = st.r0;
   const double lam = a.lam[i];
   const double* Fh = a.Fh64.at(slot, side);
-  const float* U0 = a.U32[st.upar].at(slot, side);
+  // the solution being refined: the FP32 trial, or (second step) the FP64 sum
+  const float* U0 = a.U64.base ? nullptr : a.U32[st.upar].at(slot, side);
+  const double* U0d = a.U64.base ? a.U64.at(slot, side) : nullptr;
   double* stash = a.stash.at(slot, side);
   if (a.X32lo.base) {
     float* Xh = a.X32.at(slot, side);
@@ -135,7 +137,7 @@ __global__ void k_assemble_residual(RefineArgs a) {
     };
     for (int j = 0; j < rf; ++j) put(j, Fh[(int64_t)j * a.ld + i]);
     for (int t = 0; t < r0; ++t) {
-      const double u = (double)U0[(int64_t)t * a.ld + i];
+      const double u = U0d ? U0d[(int64_t)t * a.ld + i] : (double)U0[(int64_t)t * a.ld + i];
       stash[(int64_t)t * a.ld + i] = u;
       put(rf + t, side == 0 ? lam * u : u);
       put(rf + r0 + t, side == 0 ? u : lam * u);
@@ -145,7 +147,7 @@ __global__ void k_assemble_residual(RefineArgs a) {
   double* X = a.X.at(slot, side);
   for (int j = 0; j < rf; ++j) X[(int64_t)j * a.ld + i] = Fh[(int64_t)j * a.ld + i];
   for (int t = 0; t < r0; ++t) {
-    const double u = (double)U0[(int64_t)t * a.ld + i];
+    const double u = U0d ? U0d[(int64_t)t * a.ld + i] : (double)U0[(int64_t)t * a.ld + i];
     stash[(int64_t)t * a.ld + i] = u;
     const double first = (side == 0) ? lam * u : u;
     const double second = (side == 0) ? u : lam * u;
@@ -336,6 +338,21 @@ __global__ void k_assemble_sum(RefineArgs a) {
   const int r0 = st.r0, rd = st.rd;
   const double* stash = a.stash.at(slot, side);
   const float* dU = a.U32[st.upar].at(slot, side);
+  if (a.X32.base && a.X32lo.base) {
+    // second step: the solution being refined is FP64, stored as (hi, lo) planes
+    float* Xh = a.X32.at(slot, side);
+    float* Xl = a.X32lo.at(slot, side);
+    for (int t = 0; t < r0; ++t) {
+      const dfloat x(stash[(int64_t)t * a.ld + i]);
+      Xh[(int64_t)t * a.ld + i] = x.hi;
+      Xl[(int64_t)t * a.ld + i] = x.lo;
+    }
+    for (int t = 0; t < rd; ++t) {
+      Xh[(int64_t)(r0 + t) * a.ld + i] = dU[(int64_t)t * a.ld + i];
+      Xl[(int64_t)(r0 + t) * a.ld + i] = 0.f;
+    }
+    return;
+  }
   if (a.X32.base) {
     // both blocks are FP32 values (the FP32 trial and the FP32 correction): exact
     float* X = a.X32.at(slot, side);
@@ -359,6 +376,82 @@ __global__ void k_final_state(RefineArgs a) {
   st->iters = st->total_iters;
   st->flags = conv ? (st->flags | kFlagConverged) : (st->flags & ~kFlagConverged);
   st->active = 0;
+}
+
+// After the first refinement step: a problem goes through a second step when
+// its first correction is unreliable, i.e. when
+//   (a) the correction is large against the trial solution it corrects, so that
+//       its FP32 accuracy (at best ~1e-5 of itself) leaves an error above
+//       10 tol: ||dS|| / ||S0|| max(rho_c, 1e-5) > 10 tol, or
+//   (b) the correction solve jumped (its change rose more than tenfold above
+//       its best value, itself below 1e-2) and may have settled on a poor
+//       index set.
+// The others are held: valid = 0 until k_release_held, so that no kernel of
+// the second step touches them.
+__global__ void k_check_refine(RefineArgs a, int nslots, int32_t* count) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslots) return;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  double s0n = 0.0;
+  for (int t = 0; t < st->r0; ++t) s0n += a.s0[(int64_t)slot * a.M + t] * a.s0[(int64_t)slot * a.M + t];
+  s0n = sqrt(s0n);
+  const double est = s0n > 0.0 ? st->snorm / s0n * fmax(st->rho, 1e-5) : 0.0;
+  const bool jumped = st->rho_jump > 10.0 && st->rho_best > 0.0 && st->rho_best < 1e-2;
+  if (est > 10.0 * a.final_tol || jumped) {
+    st->flags |= kFlagRefinedTwice;
+    atomicAdd(count, 1);
+  } else {
+    st->valid = 0;
+    st->active = 0;
+    st->flags |= kFlagHeld;
+  }
+}
+
+// Second step: the solution being refined is the FP64 sum of the first step
+// (factors in a.U64, singular values in a.sig_out, rank st->r); it enters at
+// its tail-rule rank at tol / 10, capped so that r_f + 2 r0 <= M.
+__global__ void k_prepare_refine2(RefineArgs a) {
+  const int slot = blockIdx.x;
+  SolveState* st = a.st + slot;
+  if (!st->valid) return;
+  const int M = a.M;
+  const int rf = st->rf0;
+  const double* sig = a.sig_out + (int64_t)slot * a.sig_out_stride;
+  int r0 = tail_rank_dev(sig, st->r, 0.1 * a.final_tol);
+  const int cap = (M - rf) / 2;
+  if (r0 > cap) r0 = cap;
+  if (r0 < 1) r0 = 1;
+  double* d = a.dvec + (int64_t)slot * M;
+  double* s0 = a.s0 + (int64_t)slot * M;
+  const double h = 1.0 / (double)(a.n + 1);
+  const ProblemDev& pr = a.prob[slot];
+  for (int k = threadIdx.x; k < rf; k += blockDim.x) d[k] = h * h * pr.s_f[k];
+  for (int t = threadIdx.x; t < r0; t += blockDim.x) {
+    s0[t] = sig[t];
+    d[rf + t] = -sig[t];
+    d[rf + r0 + t] = -sig[t];
+  }
+  if (threadIdx.x == 0) {
+    st->r0 = r0;
+    st->mx[0] = st->mx[1] = rf + 2 * r0;
+    st->active = 1;
+    const double m = rf + 2.0 * r0, n = a.n;
+    racct(a, slot, LRP_K_REFINE, 2.0 * n * r0, 2.0 * n * (rf * 8.0 + r0 * 8.0 + m * 8.0 + r0 * 8.0));
+    if (a.X32lo.base) racct_cholqr(a, slot, 2, m, true, 8.0);
+    else racct_cholqr(a, slot, 1, m);
+  }
+}
+
+// Held problems rejoin for the final state and transform.
+__global__ void k_release_held(RefineArgs a, int nslots) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslots) return;
+  SolveState* st = a.st + slot;
+  if (st->flags & kFlagHeld) {
+    st->flags &= ~kFlagHeld;
+    st->valid = 1;
+  }
 }
 
 // ------------------------------------------------------------------ launches
@@ -410,6 +503,21 @@ cudaError_t launch_assemble_sum(const RefineArgs& a, int nslots, cudaStream_t s)
   k_assemble_sum<<<dim3(cdiv(a.n, 256), 2 * nslots), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
+cudaError_t launch_check_refine(const RefineArgs& a, int nslots, int32_t* count, cudaStream_t s) {
+  k_check_refine<<<cdiv(nslots, 128), 128, 0, s>>>(a, nslots, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_refine2(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_prepare_refine2<<<nslots, 64, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_release_held(const RefineArgs& a, int nslots, cudaStream_t s) {
+  k_release_held<<<cdiv(nslots, 128), 128, 0, s>>>(a, nslots);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_final_state(const RefineArgs& a, int nslots, cudaStream_t s) {
   k_final_state<<<nslots, 32, 0, s>>>(a);
   return cudaGetLastError();

@@ -17,6 +17,7 @@ struct RefineArgs {
   const double* lam;           // FP64 eigenvalues
   Strided<const double> Fh64;  // FP64 transformed right-hand side, n x rf
   Strided<const float> U32[2]; // FP32 ping-pong factors of the inner solves
+  Strided<const double> U64;   // FP64 factors of the solution being refined (a second step), or base nullptr
   Strided<double> X;           // FP64 stacked blocks, n x M (CholeskyQR input)
   Strided<float> X32;          // FP32 stacked blocks (the sum's are FP32 values; the residual's the hi plane), or base nullptr
   Strided<float> X32lo;        // lo plane of the residual's stacked blocks in double-float, or base nullptr
@@ -51,5 +52,10 @@ cudaError_t launch_convert(int n, int64_t ld, int nslots, const SolveState* st, 
 cudaError_t launch_prepare_sum(const RefineArgs& a, int nslots, cudaStream_t s);
 cudaError_t launch_assemble_sum(const RefineArgs& a, int nslots, cudaStream_t s);
 cudaError_t launch_final_state(const RefineArgs& a, int nslots, cudaStream_t s);
+// Second refinement step: flag the problems whose first correction looks
+// unreliable (count of flagged in *count) and hold the others out of it.
+cudaError_t launch_check_refine(const RefineArgs& a, int nslots, int32_t* count, cudaStream_t s);
+cudaError_t launch_prepare_refine2(const RefineArgs& a, int nslots, cudaStream_t s);
+cudaError_t launch_release_held(const RefineArgs& a, int nslots, cudaStream_t s);
 
 }  // namespace lrp

@@ -355,8 +355,8 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.check_every < 1) o.check_every = 1;
   const bool fp64 = (o.precision == LRP_FP64);
   if (poisson && !dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
-  if (!fp64 && o.refine_steps != 0 && o.refine_steps != 1)
-    return set_error(LRP_EINVAL, "refine_steps must be 0 or 1 (one refinement step is built)");
+  if (!fp64 && (o.refine_steps < 0 || o.refine_steps > 2))
+    return set_error(LRP_EINVAL, "refine_steps must be 0, 1 or 2");
   p->n = n;
   p->tol = tol;
   p->mixed_inner_tol = 1e-4;
@@ -1011,6 +1011,7 @@ static RefineArgs make_refine_args(lrp_plan_s* p) {
   a.final_tol = p->tol;
   a.X32 = {nullptr, 0, 0};
   a.X32lo = {nullptr, 0, 0};
+  a.U64 = {nullptr, 0, 0};
   return a;
 }
 
@@ -1052,7 +1053,13 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   // Without refinement the FP32 solution is the result (truncated at tol_in).
   if (p->opts.refine_steps == 0) return phase_finalize<float>(p, p->w32, c32, count, s);
   const int rcap_res = p->w32.rf_cap < d.M ? p->w32.rf_cap : d.M;
-  for (int step = 0; step < p->opts.refine_steps; ++step) {
+  // Step 0 refines the FP32 trial; step 1 (refine_steps == 2) refines the FP64
+  // result of step 0 for the problems whose first correction looks unreliable
+  // (k_check_refine), the others held out of it.
+  bool held = false;
+  for (int step = 0; step < 2; ++step) {
+    RefineArgs rstep = ra;
+    if (step) rstep.U64 = {p->w64.U[0], nm, 2 * nm};
     // Residual of the trial solution, recompressed with FP64 accuracy.  One
     // shifted-Cholesky pass: the residual only needs the accuracy of the FP32
     // correction solve, and its cancellation happens in the FP64 core.
@@ -1064,7 +1071,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       // ~1e-13 relative error) leaves Q1 = X R1^{-1} far from orthonormal; a
       // second pass makes the residual's factors orthonormal, which is what
       // the FP32 correction solve evaluates its cross entries from.
-      RefineArgs rr = ra;
+      RefineArgs rr = rstep;
       rr.X32 = {p->w32.Q1, nm, 2 * nm};
       rr.X32lo = {p->w32.Q2, nm, 2 * nm};
       CoreParams c64r = c64;
@@ -1076,7 +1083,10 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       const Strided<float> q1h{p->w32.A, nm, 2 * nm}, q1l{p->w32.U[0], nm, 2 * nm};
       const Strided<float> noo{nullptr, 0, 0};
       const Strided<double> no64{nullptr, 0, 0};
-      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(rr, count, s));
+      if (step)
+        LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine2(rr, count, s));
+      else
+        LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(rr, count, s));
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(rr, count, s));
       LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s, launch_gram_dd(g, p->st, xh, xl, kDimX, p->w64.part, s));
       LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
@@ -1099,8 +1109,11 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
                                  Strided<float>{p->w32.Fh, fm32, 2 * fm32}, noo, no64, s));
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_setup_correction(ra, count, s));
     } else {
-      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(ra, count, s));
-      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(ra, count, s));
+      if (step)
+        LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine2(rstep, count, s));
+      else
+        LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_refine(rstep, count, s));
+      LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(rstep, count, s));
       if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 1))) return st;
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, rcap_res, s));
       LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
@@ -1117,23 +1130,32 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
     // What1 = What0 + dWhat, recompressed.  Two passes: the stacked blocks are
     // two near-orthonormal bases, and the result is the output.
     if (d.M <= 64) {
-      // Both blocks hold FP32 values: double-float Grams and products on the
-      // FP32 pipe, FP64-accurate (~1e-13 relative), the first product kept as
+      // Both blocks hold FP32 values (step 0), or the first block is the FP64
+      // result of step 0 held as (hi, lo) planes (the lo plane in the free
+      // right-hand-side buffer): double-float Grams and products on the FP32
+      // pipe, FP64-accurate (~1e-13 relative), the first product kept as
       // (hi, lo) planes for the second pass.
       RefineArgs rs = ra;
       rs.X32 = {p->w32.A, nm, 2 * nm};
+      if (step) rs.X32lo = {p->w32.Fh, fm32, 2 * fm32};
       const Strided<const float> a32{p->w32.A, nm, 2 * nm};
       const Strided<const float> nof{nullptr, 0, 0};
+      const Strided<const float> a32lo = step ? Strided<const float>{p->w32.Fh, fm32, 2 * fm32} : nof;
       const Strided<float> q1h{p->w32.Q1, nm, 2 * nm}, q1l{p->w32.Q2, nm, 2 * nm}, noo{nullptr, 0, 0};
       const Strided<double> no64{nullptr, 0, 0};
       Strided<double> G64{p->w64.G, MM, 2 * MM};
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_prepare_sum(rs, count, s));
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(rs, count, s));
-      if ((st = gram_reduce<float>(p, g, a32, kDimX, a32, kDimX, p->w64.part, G64, true, s, true))) return st;
+      if (step) {
+        LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s, launch_gram_dd(g, p->st, a32, a32lo, kDimX, p->w64.part, s));
+        LRP_LAUNCH(p, LRP_K_REDUCE, 1, s, launch_reduce(g, p->st, kDimX, kDimX, p->w64.part, G64, true, s));
+      } else if ((st = gram_reduce<float>(p, g, a32, kDimX, a32, kDimX, p->w64.part, G64, true, s, true))) {
+        return st;
+      }
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 0, s));
       LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
-                 launch_gemm_dfx(g, p->st, a32, nof, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
-                                 q1l, no64, s));
+                 launch_gemm_dfx(g, p->st, a32, a32lo, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX,
+                                 q1h, q1l, no64, s));
       LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s,
                  launch_gram_dd(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
                                 Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX, p->w64.part, s));
@@ -1156,12 +1178,17 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
                                         Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                         Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
     }
-    if (step + 1 < p->opts.refine_steps) {
-      // Another step refines the FP64 sum: hand it back to the FP32 workspace.
-      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
-      return set_error(LRP_EINVAL, "refine_steps > 1 is not built");
+    if (step == 0 && p->opts.refine_steps >= 2) {
+      LRP_CUDA(cudaMemsetAsync(p->active_dev, 0, sizeof(int32_t), s));
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_check_refine(ra, count, p->active_dev, s));
+      LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LRP_CUDA(cudaStreamSynchronize(s));
+      held = true;
+      if (*p->active_host > 0) continue;
     }
+    break;
   }
+  if (held) LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_release_held(ra, count, s));
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
   return phase_finalize<double>(p, p->w64, c64, count, s, true);
 }

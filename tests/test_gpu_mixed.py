@@ -69,3 +69,38 @@ def test_mixed_batch_error_bar():
     errs = np.array(errs)
     assert errs.max() <= 1e-6, (int(errs.argmax()), errs.max())
     assert np.median(errs) <= 1e-7, np.median(errs)
+
+
+def test_second_refinement_step_only_touches_flagged_problems():
+    """refine_steps = 2: the problems whose first correction looks unreliable
+    (flag 64) take a second step; every other problem returns exactly the
+    one-step result; all stay within the 1e-6 bar."""
+    import numpy as np
+
+    import paper_2607_06021_gb300 as lrp
+    from tests.gpu_util import rhs_dev, to_np
+    K = 96
+    rhss = [li.workload_n4095(seed) for seed in range(K)]
+    inputs = [rhs_dev(r) for r in rhss]
+    outs = {}
+    for rs in (1, 2):
+        plan = lrp.Plan(4095, 1e-8, 64, precision="mixed", batch=K, max_rhs_rank=20, m_cap=64, refine_steps=rs)
+        o = [plan.alloc_outputs() for _ in range(K)]
+        plan.solve_batch_into(inputs, o)
+        torch.cuda.synchronize()
+        outs[rs] = ([lrp.parse_info(x[3]) for x in o], o)
+        plan.close()
+    flagged = 0
+    for i in range(K):
+        inf1, o1 = outs[1][0][i], outs[1][1][i]
+        inf2, o2 = outs[2][0][i], outs[2][1][i]
+        r = inf2["rank"]
+        if inf2["flags"] & 64:
+            flagged += 1
+        else:
+            assert inf2["rank"] == inf1["rank"]
+            assert torch.equal(o1[1][:r], o2[1][:r]) and torch.equal(o1[0][:, :r], o2[0][:, :r])
+        G = po.SpectralSolution(rhss[i].U, rhss[i].s, rhss[i].V)
+        err = po.rel_error_vs_exact(to_np(o2[0][:, :r]), to_np(o2[1][:r]), to_np(o2[2][:, :r]), G)
+        assert err <= 1e-6, (i, err, inf2)
+    assert flagged < K // 4, flagged
