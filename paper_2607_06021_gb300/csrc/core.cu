@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
 // (L = M).  Region use: R0 Q(I,:) -> compaction work; R1 Z(J,:) -> eta work;
 // R2 pinv work -> V of the core SVD -> V_k(J,:); R3 V of the pinv SVD -> U~;
 // R4 T1 -> V~; R5 core -> U_k(I,:).
-constexpr int kCoreSmemDim = 64;
+constexpr int kCoreSmemDim = 48;
 template <typename TC>
 constexpr size_t core_smem_bytes() {
   return 6 * kCoreSmemDim * kCoreSmemDim * sizeof(TC);
