@@ -228,6 +228,17 @@ def e2e_pipeline(plan, batch, stream, K, torch):
     with torch.cuda.stream(copy):
         dev_in[0].copy_(batch.host_in, non_blocking=True)
         in_ready[0].record(copy)
+    def fetch(j):
+        # results of step j (already packed) move to the host on the copy stream;
+        # reading their size waits only for step j, not for the step queued after it
+        sj = j & 1
+        total = int(batch.offsets[sj][B].item())
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[sj])
+            batch.host_res[sj][:total].copy_(batch.packed[sj][:total], non_blocking=True)
+            out_done[sj].record(copy)
+        d2h.append(8 * (total + B + 1))
+
     for k in range(K):
         s = k & 1
         # the next step's inputs move while this step solves (slot 1-s was last
@@ -245,16 +256,34 @@ def e2e_pipeline(plan, batch, stream, K, torch):
                 stream.wait_event(out_done[s])  # packed[s] of step k-2 has been read
             plan.pack(batch.packed[s], batch.offsets[s], stream)
             done[s].record(stream)
-            total = int(batch.offsets[s][B].item())
-        with torch.cuda.stream(copy):
-            copy.wait_event(done[s])
-            batch.host_res[s][:total].copy_(batch.packed[s][:total], non_blocking=True)
-            out_done[s].record(copy)
-        d2h.append(8 * (total + B + 1))
+        if k >= 1:
+            fetch(k - 1)
+    fetch(K - 1)
     stream.wait_stream(copy)
     end.record(stream)
     torch.cuda.synchronize()
     return start.elapsed_time(end), d2h
+
+
+def copy_bandwidth(batch, stream, torch):
+    """GB/s of one host-to-device copy of a step's inputs and one device-to-host
+    copy of the same number of bytes of packed results (pinned host memory)."""
+    out = {}
+    n_in = batch.host_in.numel() * batch.host_in.element_size()
+    n_out = min(batch.packed[0].numel(), batch.host_res[0].numel())
+    for name, fn, nbytes in (("h2d_gbs", lambda: batch.dev_in.copy_(batch.host_in, non_blocking=True), n_in),
+                             ("d2h_gbs", lambda: batch.host_res[0][:n_out].copy_(batch.packed[0][:n_out],
+                                                                                non_blocking=True), 8 * n_out)):
+        with torch.cuda.stream(stream):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[name] = round(nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    return out
 
 
 def gpu_arm(args, rank, world, local_rank, precisions):
@@ -332,6 +361,7 @@ def gpu_arm(args, rank, world, local_rank, precisions):
                           "d2h_bytes_per_step": int(sum(d2h) / max(len(d2h), 1)),
                           "results": "compact: rank columns of U, V and rank values of S per problem (lrp_plan_pack)",
                           "pipeline": "next step's H2D and previous step's D2H on a copy stream, overlapping the solve"}
+            res["e2e"].update(copy_bandwidth(batch, stream, torch))
         # Per-problem reports of the last step.
         torch.cuda.synchronize()
         infos = [lrp.parse_info(o[3]) for o in batch.outputs]
