@@ -89,6 +89,34 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_barrier(world: int) -> None:
+    """Barrier of the replicas (one process per GPU; no-op alone)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(v: float, world: int, device) -> float:
+    """The largest of the ranks' values (the whole job's timed region)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank: int, batch: int) -> list:
+    """Input seeds of a rank's batch: disjoint across ranks (weak scaling)."""
+    return [1000 * rank + i for i in range(batch)]
+
+
+def whole_job_value(batch: int, world: int, steps: int, total_ms: float) -> float:
+    """Solves per second of all ranks together over the slowest rank's time."""
+    return batch * world * steps / (total_ms / 1e3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -298,22 +326,17 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
     B = args.batch
-    rhss = [li.workload_n4095(seed=1000 * rank + i) for i in range(B)]
+    rhss = [li.workload_n4095(seed=sd) for sd in replica_seeds(rank, B)]
     batch = Batch(rhss, torch, device)
     stream = torch.cuda.Stream(device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     hbm_peak, peak_src = load_peaks()
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replica_barrier(world)
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world, device)
 
     results = {}
     for prec in precisions:
@@ -350,13 +373,13 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         launches = plan.kernel_stats()["all"][0]
         total_ms = max_over_ranks(sum(ms))
         res = {"ms": ms, "total_ms": total_ms, "wall_s": wall, "clocks": clk, "launches": launches,
-               "value": B * world * args.steps / (total_ms / 1e3)}
+               "value": whole_job_value(B, world, args.steps, total_ms)}
         # End to end through the public call with host buffers (pinned), copies inside the timed region.
         if not args.no_e2e:
             barrier()
             e2e_total, d2h = e2e_pipeline(plan, batch, stream, args.steps, torch)
             e2e_total = max_over_ranks(e2e_total)
-            res["e2e"] = {"value": B * world * args.steps / (e2e_total / 1e3), "unit": "solves/s",
+            res["e2e"] = {"value": whole_job_value(B, world, args.steps, e2e_total), "unit": "solves/s",
                           "h2d_bytes_per_step": batch.h2d_bytes,
                           "d2h_bytes_per_step": int(sum(d2h) / max(len(d2h), 1)),
                           "results": "compact: rank columns of U, V and rank values of S per problem (lrp_plan_pack)",
