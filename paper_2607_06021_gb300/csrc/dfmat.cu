@@ -61,7 +61,7 @@ template <bool OUT_DF>
 __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* __restrict__ st_all,
                                                  Strided<const float> ah, Strided<const float> al, int sel_in,
                                                  Strided<const double> bm, int sel_out, Strided<float> oh,
-                                                 Strided<float> ol, Strided<double> o64) {
+                                                 Strided<float> ol, Strided<double> o64, int tri) {
   const int slot = blockIdx.z >> 1, side = blockIdx.z & 1;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
@@ -78,7 +78,10 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
   const double* Bm = bm.at(slot, side);
   constexpr int TX = 8, TY = DT / TX, RI = DROWS / TY;  // 8 column groups of 4, 32 row groups of 4
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  const int nkb = (mi + 63) / 64;
+  // an upper-triangular Bm: output column c takes rows k <= c only, so the
+  // CTA's 32 columns need k < c0 + 32
+  const int klim = tri ? min(mi, c0 + 32) : mi;
+  const int nkb = (klim + 63) / 64;
   for (int tile = 0; tile < DTILES; ++tile) {
     const int r0 = rbase + tile * DROWS;
     if (r0 >= g.n) break;
@@ -87,8 +90,8 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
     for (int i = 0; i < RI; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
-    for (int kb = 0; kb < mi; kb += 64) {
-      const int kend = min(mi, kb + 64);
+    for (int kb = 0; kb < klim; kb += 64) {
+      const int kend = min(klim, kb + 64);
       if (tile == 0 || nkb > 1) {
         __syncthreads();
         const int kpad = (kend - kb + DK - 1) / DK * DK;
@@ -249,12 +252,12 @@ __global__ void __launch_bounds__(DT) k_gram_dd(TallGeom g, const SolveState* __
 
 cudaError_t launch_gemm_dfx(const TallGeom& g, const SolveState* st, Strided<const float> ah, Strided<const float> al,
                             int sel_in, Strided<const double> bm, int sel_out, Strided<float> oh, Strided<float> ol,
-                            Strided<double> o64, cudaStream_t s) {
+                            Strided<double> o64, cudaStream_t s, bool tri) {
   const dim3 grid((g.n + DROWS * DTILES - 1) / (DROWS * DTILES), (g.M + 31) / 32, g.nslots * 2);
   if (o64.base)
-    k_gemm_dfx<false><<<grid, DT, 0, s>>>(g, st, ah, al, sel_in, bm, sel_out, oh, ol, o64);
+    k_gemm_dfx<false><<<grid, DT, 0, s>>>(g, st, ah, al, sel_in, bm, sel_out, oh, ol, o64, tri ? 1 : 0);
   else
-    k_gemm_dfx<true><<<grid, DT, 0, s>>>(g, st, ah, al, sel_in, bm, sel_out, oh, ol, o64);
+    k_gemm_dfx<true><<<grid, DT, 0, s>>>(g, st, ah, al, sel_in, bm, sel_out, oh, ol, o64, tri ? 1 : 0);
   return cudaGetLastError();
 }
 

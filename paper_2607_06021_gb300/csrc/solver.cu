@@ -1093,7 +1093,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64r, cb64, kDimX, 0, s));
       LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, xh, xl, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX, q1h,
-                                 q1l, no64, s));
+                                 q1l, no64, s, true));
       LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s,
                  launch_gram_dd(g, p->st, Strided<const float>{p->w32.A, nm, 2 * nm},
                                 Strided<const float>{p->w32.U[0], nm, 2 * nm}, kDimX, p->w64.part, s));
@@ -1155,7 +1155,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<double>(c64, cb64, kDimX, 0, s));
       LRP_LAUNCH(p, LRP_K_GEMM_DF, 1, s,
                  launch_gemm_dfx(g, p->st, a32, a32lo, kDimX, Strided<const double>{p->w64.P, MM, 2 * MM}, kDimX,
-                                 q1h, q1l, no64, s));
+                                 q1h, q1l, no64, s, true));
       LRP_LAUNCH(p, LRP_K_GRAM_DF, 1, s,
                  launch_gram_dd(g, p->st, Strided<const float>{p->w32.Q1, nm, 2 * nm},
                                 Strided<const float>{p->w32.Q2, nm, 2 * nm}, kDimX, p->w64.part, s));

@@ -82,7 +82,7 @@ cudaError_t launch_qdeim(const TallGeom& g, const SolveState* st, Strided<const 
 // with at most 64 columns (then launch_reduce).
 cudaError_t launch_gemm_dfx(const TallGeom& g, const SolveState* st, Strided<const float> ah, Strided<const float> al,
                             int sel_in, Strided<const double> bm, int sel_out, Strided<float> oh, Strided<float> ol,
-                            Strided<double> o64, cudaStream_t s);
+                            Strided<double> o64, cudaStream_t s, bool tri = false);
 cudaError_t launch_gram_dd(const TallGeom& g, const SolveState* st, Strided<const float> xh, Strided<const float> xl,
                            int sel, double* part, cudaStream_t s);
 
