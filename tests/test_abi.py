@@ -46,6 +46,37 @@ def test_host_side_argument_checks_need_no_gpu():
     assert pkg.status_string(pkg.LRP_RANK_CAPPED) == "LRP_RANK_CAPPED"
 
 
+def test_option_checks_need_no_gpu():
+    # Option combinations the library refuses on the host, before any device call.
+    pkg = pytest.importorskip("paper_2607_06021_gb300")
+    lib = pkg.library()
+    h = ctypes.c_void_p()
+
+    def plan(n=255, **kw):
+        o = pkg.lrp_default_opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return lib.lrp_plan(ctypes.byref(h), n, 1e-8, 8, ctypes.byref(o))
+
+    assert pkg.lrp_default_opts().refine_steps == 1 and pkg.lrp_default_opts().sample_factor == 1.0
+    assert pkg.lrp_default_opts().matrix == pkg.LRP_MAT_POISSON
+    assert plan(selector=7) == pkg.LRP_EINVAL and "selector" in pkg.last_error()
+    assert plan(selector=pkg.LRP_SEL_BERNOULLI, sample_factor=0.0) == pkg.LRP_EINVAL
+    assert plan(selector=pkg.LRP_SEL_BERNOULLI, sample_factor=-1.0) == pkg.LRP_EINVAL
+    assert plan(matrix=9) == pkg.LRP_EINVAL and "matrix" in pkg.last_error()
+    # the test matrices: FP64 only, any n (no transform), K needs two grid points
+    assert plan(matrix=pkg.LRP_MAT_HILBERT, precision=pkg.LRP_MIXED) == pkg.LRP_EINVAL
+    assert "FP64" in pkg.last_error()
+    assert plan(n=1, matrix=pkg.LRP_MAT_K) == pkg.LRP_EINVAL
+    assert plan(precision=pkg.LRP_MIXED, refine_steps=3, m_cap=64) == pkg.LRP_EINVAL
+    assert "refine_steps" in pkg.last_error()
+    # n + 1 need not be a power of two for a matrix given by entries: the host
+    # checks pass and only the device step can fail here (no GPU)
+    assert plan(n=300, matrix=pkg.LRP_MAT_HILBERT) in (pkg.LRP_OK, pkg.LRP_ECUDA)
+    if h.value:
+        lib.lrp_plan_destroy(h)
+
+
 def test_struct_layouts_match_header():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
     assert ctypes.sizeof(pkg.lrp_opts) == 56
@@ -77,6 +108,10 @@ def test_plan_estimate_is_host_only_and_linear_in_batch():
     assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) > sizes[0]
     with pytest.raises(pkg.LrpError):
         pkg.lrp_plan_estimate_bytes(4000, 1e-8, 64, o)
+    # a matrix given by entries: any n, and no transform scratch
+    o.precision, o.matrix = pkg.LRP_FP64, pkg.LRP_MAT_HILBERT
+    assert pkg.lrp_plan_estimate_bytes(4000, 1e-8, 64, o) > 0
+    assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) < sizes[0]
 
 
 def test_request_footprint_formula():
