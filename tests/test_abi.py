@@ -109,9 +109,12 @@ def test_plan_estimate_is_host_only_and_linear_in_batch():
     with pytest.raises(pkg.LrpError):
         pkg.lrp_plan_estimate_bytes(4000, 1e-8, 64, o)
     # a matrix given by entries: any n, and no transform scratch
-    o.precision, o.matrix = pkg.LRP_FP64, pkg.LRP_MAT_HILBERT
+    o.precision = pkg.LRP_FP64
+    poisson_16k = pkg.lrp_plan_estimate_bytes(16383, 1e-8, 64, o)  # multi-pass transform: scratch
+    o.matrix = pkg.LRP_MAT_HILBERT
     assert pkg.lrp_plan_estimate_bytes(4000, 1e-8, 64, o) > 0
-    assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) < sizes[0]
+    assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) == sizes[0]  # shared-memory transform: none
+    assert pkg.lrp_plan_estimate_bytes(16383, 1e-8, 64, o) < poisson_16k
 
 
 def test_request_footprint_formula():
