@@ -179,17 +179,39 @@ struct Vec4<double> {
 // memory in blocks of 64 rows of K (converted to T once per staging): with
 // K <= 64 one staging serves all row tiles.  Each row tile streams In through
 // shared memory in TK-deep slices: 256 threads, each RI consecutive rows x 4
-// consecutive columns, operands read as 4-vectors.
+// consecutive columns, operands read as 4-vectors.  The next slice (of this
+// tile or the next) is loaded into registers, as 4-row vectors, while the
+// current one is multiplied; the output is written as 4-row vectors.
 template <typename T, int TNW>
 __device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
                                            T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
-                                           int rbase, int c0, T (*As)[kGemmRows], T (*Bs)[64]) {
+                                           int rbase, int c0, bool vec, T (*As)[kGemmRows], T (*Bs)[64]) {
   constexpr int TX = TNW / 4;           // threads along columns
   constexpr int TY = NT / TX;           // threads along rows
   constexpr int RI = kGemmRows / TY;    // rows per thread
+  constexpr int QV = kGemmRows / 4;     // 4-row vectors in a slice row
+  constexpr int PV = TK * QV / NT;      // 4-row vectors per thread and slice
   static_assert(RI % 4 == 0, "rows per thread: whole 4-vectors");
+  static_assert(PV * NT == TK * QV, "slice: whole vectors per thread");
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const int nkb = (mi + 63) / 64;
+  T pf[PV][4];
+  // Slice (rows r0.., K rows k0 .. k0 + TK - 1, valid below kend) into pf;
+  // rows past n and K rows past kend read as zero.
+  auto fetch = [&](int r0, int k0, int kend) {
+#pragma unroll
+    for (int v = 0; v < PV; ++v) {
+      const int e = tid + NT * v, kk = e / QV, row = r0 + 4 * (e % QV), k = k0 + kk;
+      const T* src = X + (int64_t)k * g.ld + row;
+      if (vec && k < kend && row + 3 < g.n) {
+        ld4<T>(src, pf[v]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pf[v][u] = (k < kend && row + u < g.n) ? src[u] : (T)0;
+      }
+    }
+  };
+  fetch(rbase, 0, min(mi, 64));
   for (int tile = 0; tile < kGemmTiles; ++tile) {
     const int r0 = rbase + tile * kGemmRows;
     if (r0 >= g.n) break;
@@ -211,11 +233,16 @@ __device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restric
       }
       for (int k0 = kb; k0 < kend; k0 += TK) {
 #pragma unroll
-        for (int q = 0; q < (TK * kGemmRows) / NT; ++q) {
-          const int e = tid + NT * q;
-          const int kk = e / kGemmRows, i = e % kGemmRows;
-          const int row = r0 + i, k = k0 + kk;
-          As[kk][i] = (row < g.n && k < kend) ? X[(int64_t)k * g.ld + row] : (T)0;
+        for (int v = 0; v < PV; ++v) {
+          const int e = tid + NT * v;
+          st4<T>(&As[e / QV][4 * (e % QV)], pf[v]);
+        }
+        if (k0 + TK < kend) {
+          fetch(r0, k0 + TK, kend);
+        } else if (kend < mi) {
+          fetch(r0, kend, min(mi, kend + 64));
+        } else if (tile + 1 < kGemmTiles && r0 + kGemmRows < g.n) {
+          fetch(r0 + kGemmRows, 0, min(mi, 64));
         }
         __syncthreads();
 #pragma unroll
@@ -242,11 +269,27 @@ __device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restric
       const int col = c0 + tx * 4 + j;
       if (col >= mo) continue;
 #pragma unroll
-      for (int i = 0; i < RI; ++i) {
+      for (int i = 0; i < RI; i += 4) {
         const int row = r0 + ty * RI + i;
         if (row >= g.n) continue;
         const int64_t o = (int64_t)col * g.ld + row;
-        O[o] = (mode == 1) ? (T)(Z[o] - acc[i][j]) : acc[i][j];
+        T v[4];
+        if (vec && row + 3 < g.n) {
+          if (mode == 1) {
+            T z[4];
+            ld4<T>(Z + o, z);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = (T)(z[u] - acc[i + u][j]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = acc[i + u][j];
+          }
+          st4<T>(O + o, v);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (row + u < g.n) O[o + u] = (mode == 1) ? (T)(Z[o + u] - acc[i + u][j]) : acc[i + u][j];
+        }
       }
     }
   }
@@ -272,10 +315,13 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   const double* Bm = bm.at(slot, side);
   T* O = out.at(slot, side);
   const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
+  // 4-row vectors need 16-byte aligned columns (ld is a multiple of 32)
+  const bool vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(O) |
+                     reinterpret_cast<uintptr_t>(Z)) & 15) == 0 && (g.ld & 3) == 0;
   if (mo <= 32) {
-    gemm_block<T, 32>(g, X, Bm, O, Z, mode, mi, mo, rbase, 0, As, Bs);
+    gemm_block<T, 32>(g, X, Bm, O, Z, mode, mi, mo, rbase, 0, vec, As, Bs);
   } else {
-    for (int c0 = 0; c0 < mo; c0 += 64) gemm_block<T, 64>(g, X, Bm, O, Z, mode, mi, mo, rbase, c0, As, Bs);
+    for (int c0 = 0; c0 < mo; c0 += 64) gemm_block<T, 64>(g, X, Bm, O, Z, mode, mi, mo, rbase, c0, vec, As, Bs);
   }
 }
 
