@@ -1033,6 +1033,24 @@ cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, 
   return cudaGetLastError();
 }
 
+// dst[0 .. words) = src[0 .. words), 4-byte words; either side may be mapped
+// pinned host memory (its device alias).
+__global__ void k_stage(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, int64_t words) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_stage(const void* src, void* dst, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if (!src || !dst || bytes % 4 != 0 || (reinterpret_cast<uintptr_t>(src) & 3) || (reinterpret_cast<uintptr_t>(dst) & 3))
+    return cudaErrorInvalidValue;
+  const int64_t words = (int64_t)(bytes / 4);
+  const int64_t blocks = (words + 255) / 256;
+  k_stage<<<(unsigned)(blocks < 64 ? blocks : 64), 256, 0, s>>>(static_cast<const uint32_t*>(src),
+                                                               static_cast<uint32_t*>(dst), words);
+  return cudaGetLastError();
+}
+
 #define LRP_INST(T)                                                                                          \
   template cudaError_t launch_chol<T>(const CoreParams&, const CoreBufs<T>&, int, int, cudaStream_t);       \
   template cudaError_t launch_core<T>(const CoreParams&, const CoreBufs<T>&, int, cudaStream_t);            \

@@ -113,5 +113,11 @@ cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t 
 
 // Number of active slots (written to a host-visible counter).
 cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, int32_t* list, cudaStream_t s);
+// Copies `bytes` (a multiple of 4, both ends 4-byte aligned) with a kernel on
+// stream s.  The solve path moves its control data (job descriptors up, active
+// counts down) this way, through the device aliases of mapped pinned host
+// buffers, so that it never waits on a copy engine that a caller's bulk
+// transfers on other streams hold.
+cudaError_t launch_stage(const void* src, void* dst, size_t bytes, cudaStream_t s);
 
 }  // namespace lrp

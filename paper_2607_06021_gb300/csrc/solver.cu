@@ -476,6 +476,9 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->prob_host, sizeof(ProblemDev) * d.B);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_ptrs, (sizeof(void*) * 2 + sizeof(int64_t) * 2) * 2 * d.B);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->active_host, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->prob_host_dev, p->prob_host, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&p->host_ptrs_dev, p->host_ptrs, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->active_host_dev, p->active_host, 0);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) s = set_error(LRP_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
@@ -704,10 +707,15 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
       hout[mat * count + sl] = w.Fh + (int64_t)sl * 2 * fm + (int64_t)mat * fm;
       hldo[mat * count + sl] = d.ld;
     }
-  LRP_CUDA(cudaMemcpyAsync(w.fwd_in, hin, sizeof(void*) * 2 * count, cudaMemcpyHostToDevice, s));
-  LRP_CUDA(cudaMemcpyAsync(w.fwd_out, hout, sizeof(void*) * 2 * count, cudaMemcpyHostToDevice, s));
-  LRP_CUDA(cudaMemcpyAsync(w.fwd_ldi, hldi, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice, s));
-  LRP_CUDA(cudaMemcpyAsync(w.fwd_ldo, hldo, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice, s));
+  // the device alias of a host staging address
+  auto dev = [&](const void* h) {
+    return static_cast<const void*>(static_cast<const char*>(p->host_ptrs_dev) +
+                                    (static_cast<const char*>(h) - static_cast<const char*>(p->host_ptrs)));
+  };
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(dev(hin), w.fwd_in, sizeof(void*) * 2 * count, s));
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(dev(hout), w.fwd_out, sizeof(void*) * 2 * count, s));
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(dev(hldi), w.fwd_ldi, sizeof(int64_t) * 2 * count, s));
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(dev(hldo), w.fwd_ldo, sizeof(int64_t) * 2 * count, s));
   if (do_setup)
     LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_setup<T>(cp, p->prob_dev, w.w, w.rf_cap, count, p->acct, s));
   DstBatch<double, T> job;
@@ -903,9 +911,9 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
     lrp_status st = run_captured<T>(p, w, count, kind, level, s, iteration);
     if (st) return st;
     if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
-      LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->active_dev, p->active_host_dev, sizeof(int32_t), s));
       LRP_CUDA(cudaStreamSynchronize(s));
-      const int na = *p->active_host;
+      const int na = *static_cast<volatile int32_t*>(p->active_host);
       if (na == 0) break;
       int b = 1, l = 1;
       while (b < na) {
@@ -1181,10 +1189,10 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
     if (step == 0 && p->opts.refine_steps >= 2) {
       LRP_CUDA(cudaMemsetAsync(p->active_dev, 0, sizeof(int32_t), s));
       LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_check_refine(ra, count, p->active_dev, s));
-      LRP_CUDA(cudaMemcpyAsync(p->active_host, p->active_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->active_dev, p->active_host_dev, sizeof(int32_t), s));
       LRP_CUDA(cudaStreamSynchronize(s));
       held = true;
-      if (*p->active_host > 0) continue;
+      if (*static_cast<volatile int32_t*>(p->active_host) > 0) continue;
     }
     break;
   }
@@ -1234,7 +1242,7 @@ extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_pro
   }
   p->any_warm = false;
   for (int i = 0; i < count; ++i) p->any_warm = p->any_warm || hp[i].warm != nullptr;
-  LRP_CUDA(cudaMemcpyAsync(p->prob_dev, p->prob_host, sizeof(ProblemDev) * count, cudaMemcpyHostToDevice, s));
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->prob_host_dev, p->prob_dev, sizeof(ProblemDev) * count, s));
   p->last_count = count;
   if (p->opts.precision == LRP_FP64) return run_fp64(p, count, s);
   return run_mixed(p, count, s);

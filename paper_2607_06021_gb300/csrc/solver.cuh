@@ -146,6 +146,11 @@ struct lrp_plan_s {
   double mixed_redundancy = 1e-6;        // redundancy threshold on FP32 data
   double mixed_residual_tol = 1e-7;      // tail-rule truncation of the recompressed residual
   int32_t* active_host = nullptr;        // pinned
+  // Device aliases of the mapped pinned buffers above (control data moves by
+  // kernel, not by copy engine)
+  lrp::ProblemDev* prob_host_dev = nullptr;
+  void* host_ptrs_dev = nullptr;
+  int32_t* active_host_dev = nullptr;
   lrp::Workspace<double> w64;
   lrp::Workspace<float> w32;
   KernelStats stats;

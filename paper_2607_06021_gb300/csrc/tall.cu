@@ -296,8 +296,64 @@ __device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restric
   __syncthreads();  // the next column block restages Bs
 }
 
-// One launch for every output width: a CTA owns kGemmTiles x kGemmRows rows
-// and runs one 32-wide column block when mo <= 32, else 64-wide blocks.
+// Out = In * Bm (or Zsub - In * Bm) for narrow products (mi <= KMAX, mo <= 64),
+// thread per row: each thread holds R rows of In (KMAX values each, zero past
+// mi) in registers and forms their outputs one column at a time against Bm^T,
+// staged in shared memory once per CTA and read by broadcast.  Every output is
+// the same FMA chain as in gemm_block (k = 0, 1, ... from zero; the zero
+// padding of K adds exact zeros, which leave a sum unchanged), so both paths
+// give identical results.  Loads and stores are coalesced along rows.
+template <typename T, int KMAX, int R>
+__device__ __forceinline__ void gemm_rows(const TallGeom& g, const T* __restrict__ X, const double* __restrict__ Bm,
+                                          T* __restrict__ O, const T* __restrict__ Z, int mode, int mi, int mo,
+                                          int rbase, T (*Bt)[KMAX]) {
+  constexpr int kRows = kGemmRows * kGemmTiles;  // rows per CTA
+  static_assert(kRows % (NT * R) == 0, "whole passes");
+  const int tid = threadIdx.x;
+  const int mi4 = (mi + 3) & ~3;
+  for (int e = tid; e < mo * KMAX; e += NT) {
+    const int k = e % KMAX, c = e / KMAX;
+    Bt[c][k] = (k < mi) ? (T)Bm[(int64_t)c * g.M + k] : (T)0;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < kRows / (NT * R); ++pass) {
+    int row[R];
+    T x[R][KMAX];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      row[r] = rbase + pass * NT * R + r * NT + tid;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) x[r][k] = (k < mi && row[r] < g.n) ? X[(int64_t)k * g.ld + row[r]] : (T)0;
+    }
+    for (int c = 0; c < mo; ++c) {
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = (T)0;
+#pragma unroll
+      for (int k = 0; k < KMAX; k += 4) {
+        if (k < mi4) {
+          T b[4];
+          ld4<T>(&Bt[c][k], b);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(x[r][k + u], b[u], acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (row[r] >= g.n) continue;
+        const int64_t o = (int64_t)c * g.ld + row[r];
+        O[o] = (mode == 1) ? (T)(Z[o] - acc[r]) : acc[r];
+      }
+    }
+  }
+}
+
+// One launch for every output width: a CTA owns kGemmTiles x kGemmRows rows.
+// Narrow products (mi <= 32, or <= 64 in FP32, and mo <= 64) run thread per
+// row; wider ones as register tiles, one 32-wide column block when mo <= 32,
+// else 64-wide blocks.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
@@ -318,6 +374,16 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   // 4-row vectors need 16-byte aligned columns (ld is a multiple of 32)
   const bool vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(O) |
                      reinterpret_cast<uintptr_t>(Z)) & 15) == 0 && (g.ld & 3) == 0;
+  if (mo <= 64 && mi <= 32) {
+    gemm_rows<T, 32, sizeof(T) == 4 ? 2 : 1>(g, X, Bm, O, Z, mode, mi, mo, rbase, reinterpret_cast<T(*)[32]>(&Bs[0][0]));
+    return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (mo <= 64 && mi <= 64) {
+      gemm_rows<T, 64, 1>(g, X, Bm, O, Z, mode, mi, mo, rbase, Bs);
+      return;
+    }
+  }
   if (mo <= 32) {
     gemm_block<T, 32>(g, X, Bm, O, Z, mode, mi, mo, rbase, 0, vec, As, Bs);
   } else {
