@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "dfloat.cuh"
 #include "dst.cuh"
@@ -39,6 +41,17 @@ __global__ void k_twiddle(cplx<TC>* tw, int N) {
 }
 
 __device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+// (a, c) <- (a + w c, a - w c), the operations of one radix-2 butterfly below.
+template <typename TC>
+__device__ __forceinline__ void butterfly(cplx<TC>& a, cplx<TC>& c, const cplx<TC>& w) {
+  const TC tr = w.re * c.re - w.im * c.im;
+  const TC ti = w.re * c.im + w.im * c.re;
+  c.re = a.re - tr;
+  c.im = a.im - ti;
+  a.re = a.re + tr;
+  a.im = a.im + ti;
+}
 
 // in_ptrs/out_ptrs: one column-0 pointer per slot; ncols_dev (or fixed_cols) gives
 // the number of columns of each slot; blockIdx.x = column, blockIdx.y = slot,
@@ -81,7 +94,34 @@ __global__ void k_dst1_smem(int n, int logN, const DstBatch<TIn, TOut> job,
   __syncthreads();
 
   // Radix-2 decimation-in-time butterflies; twiddle e^{-2 pi i pos/(2h)} = tw[pos * N / h].
-  for (int s = 1; s <= logN; ++s) {
+  int s = 1;
+  if constexpr (std::is_same<TC, dfloat>::value) {
+    // Double-float steps are explicitly rounded (nothing is contracted), so the
+    // stages can go in pairs with the same operations: the elements i, i+h,
+    // i+2h, i+3h of a 4h block take both stages' butterflies in registers,
+    // with half the barriers and shared-memory round trips.
+    for (; s + 1 <= logN; s += 2) {
+      const int h = 1 << (s - 1);
+      const int st0 = N >> (s - 1), st1 = N >> s;
+      for (int b = threadIdx.x; b < (N >> 2); b += blockDim.x) {
+        const int pos = b & (h - 1);
+        const int i = ((b >> (s - 1)) << (s + 1)) + pos;
+        cplx<TC> a0 = z[i], a1 = z[i + h], a2 = z[i + 2 * h], a3 = z[i + 3 * h];
+        const cplx<TC> w0 = tw[pos * st0];
+        butterfly(a0, a1, w0);
+        butterfly(a2, a3, w0);
+        const cplx<TC> w1 = tw[pos * st1], w2 = tw[(pos + h) * st1];
+        butterfly(a0, a2, w1);
+        butterfly(a1, a3, w2);
+        z[i] = a0;
+        z[i + h] = a1;
+        z[i + 2 * h] = a2;
+        z[i + 3 * h] = a3;
+      }
+      __syncthreads();
+    }
+  }
+  for (; s <= logN; ++s) {
     const int h = 1 << (s - 1);
     const int stride = N >> (s - 1);  // N / h
     for (int b = threadIdx.x; b < half; b += blockDim.x) {
