@@ -76,8 +76,14 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
   const float* Ah = ah.at(slot, side);
   const float* Al = al.base ? al.at(slot, side) : nullptr;
   const double* Bm = bm.at(slot, side);
-  constexpr int TX = 8, TY = DT / TX, RI = DROWS / TY;  // 8 column groups of 4, 32 row groups of 4
-  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  // 8 column groups of 4, one per warp, and 32 row groups of 4, one per lane: a
+  // warp whose columns lie past the product's width, or (upper-triangular Bm)
+  // whose columns all lie before a K slice, skips that work as a whole; it
+  // would only add exact zeros.
+  constexpr int TX = 8, TY = DT / TX, RI = DROWS / TY;
+  static_assert(TX * 32 == DT && TY == 32, "one column group per warp");
+  const int tid = threadIdx.x, tx = tid >> 5, ty = tid & 31;
+  const bool live = c0 + tx * 4 < mo;
   // an upper-triangular Bm: output column c takes rows k <= c only, so the
   // CTA's 32 columns need k < c0 + 32
   const int klim = tri ? min(mi, c0 + 32) : mi;
@@ -115,18 +121,20 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
           Asl[kk][i] = (ok && Al) ? Al[(int64_t)k * g.ld + row] : 0.f;
         }
         __syncthreads();
+        if (live && !(tri && c0 + tx * 4 + 3 < k0)) {
 #pragma unroll 4
-        for (int kk = 0; kk < DK; ++kk) {
-          const float4 a4 = *reinterpret_cast<const float4*>(&Ash[kk][ty * RI]);
-          const float4 l4 = *reinterpret_cast<const float4*>(&Asl[kk][ty * RI]);
-          const float4 b4 = *reinterpret_cast<const float4*>(&Bsh[k0 - kb + kk][tx * 4]);
-          const float4 c4 = *reinterpret_cast<const float4*>(&Bsl[k0 - kb + kk][tx * 4]);
-          const float av[4] = {a4.x, a4.y, a4.z, a4.w}, alv[4] = {l4.x, l4.y, l4.z, l4.w};
-          const float bv[4] = {b4.x, b4.y, b4.z, b4.w}, blv[4] = {c4.x, c4.y, c4.z, c4.w};
+          for (int kk = 0; kk < DK; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&Ash[kk][ty * RI]);
+            const float4 l4 = *reinterpret_cast<const float4*>(&Asl[kk][ty * RI]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bsh[k0 - kb + kk][tx * 4]);
+            const float4 c4 = *reinterpret_cast<const float4*>(&Bsl[k0 - kb + kk][tx * 4]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, alv[4] = {l4.x, l4.y, l4.z, l4.w};
+            const float bv[4] = {b4.x, b4.y, b4.z, b4.w}, blv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-          for (int i = 0; i < RI; ++i)
+            for (int i = 0; i < RI; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) dd_madd(av[i], alv[i], bv[j], blv[j], hi[i][j], lo[i][j]);
+              for (int j = 0; j < 4; ++j) dd_madd(av[i], alv[i], bv[j], blv[j], hi[i][j], lo[i][j]);
+          }
         }
         __syncthreads();
       }
