@@ -5,16 +5,17 @@
 //              right-hand side (Algorithm scross, "C = G(:,J), R = G(I,:)";
 //              entries by Eq. g_for_p at O(r_f) each, Sec. 2.1 / Sec. 3.2).
 //  k_gemm_nn   n x m times m x m' (the triangular applies of CholeskyQR, the
-//              factor update U_k = Q U~ of Algorithm scross, and E = U' - U X).
-//  k_gram      per-row-block partial products X^T Y in FP64 (Gram matrices of
-//              CholeskyQR, cross-Grams of consecutive iterates).
+//              factor update U_k = Q U~ of Algorithm scross, and E = U' - U X):
+//              thread per row for narrow products, register tiles otherwise.
+//  k_gram_*    per-row-block partial products X^T Y (Gram matrices of
+//              CholeskyQR, cross-Grams of consecutive iterates): FP64, FP32 or
+//              double-float accumulation.
 //  k_reduce    deterministic sum of the partials.
 //  k_leverage  leverage scores pi_i = sum_c U(i,c)^2 / c (Algorithm
 //              LeverageScores) and per-block top-c candidates.
 //
 // All kernels read their data-dependent sizes (|I|, |J|, ranks) from the
-// per-slot SolveState and return early for finished slots.  Tiles are 64 rows
-// x 64 columns with 256 threads, each thread owning a 4 x 4 strided block.
+// per-slot SolveState and return early for finished slots; 256 threads per CTA.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
