@@ -104,3 +104,15 @@ def test_second_refinement_step_only_touches_flagged_problems():
         err = po.rel_error_vs_exact(to_np(o2[0][:, :r]), to_np(o2[1][:r]), to_np(o2[2][:, :r]), G)
         assert err <= 1e-6, (i, err, inf2)
     assert flagged < K // 4, flagged
+
+
+@pytest.mark.parametrize("n", [511, 2047, 8191])
+def test_mixed_odd_log_sizes(n):
+    """Grids with n + 1 = 2^odd: the double-float transforms end on a single
+    radix-2 stage after the paired ones; the result stays within the 1e-6 bar
+    of the exact solution."""
+    rhs = li.gaussian_eigen_rhs(n, 300 + n % 97, 8)
+    G = po.SpectralSolution(rhs.U, rhs.s, rhs.V)
+    U, S, V, info = _solve(rhs, 1e-8, 64, m_cap=64)
+    assert info["status"] in (0, 5), info
+    assert po.rel_error_vs_exact(U, S, V, G) <= 1e-6, info
