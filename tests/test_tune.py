@@ -1,0 +1,59 @@
+"""Lane-count autotuner, host logic (CPU): candidate filtering, the choice by
+median with ties to fewer lanes, rank classes and table keys, and the JSON
+table's round trip.  The timing itself is a function passed in; here a fake
+one with known costs."""
+import json
+
+import pytest
+
+from paper_2607_06021_gb300 import tune
+
+
+def test_rank_class_and_key():
+    assert [tune.rank_class(r) for r in (0, 1, 2, 3, 20, 32, 33)] == [1, 1, 2, 4, 32, 32, 64]
+    assert tune.table_key("mixed", 4095, 20, 1024) == "mixed/n4095/rf32/b1024"
+    assert tune.table_key("mixed", 4095, 17, 1024) == tune.table_key("mixed", 4095, 32, 1024)
+
+
+def test_candidates_leave_no_lane_empty():
+    assert tune.candidate_lanes(1024) == [1, 2, 4, 8]
+    assert tune.candidate_lanes(3) == [1, 2]
+    assert tune.candidate_lanes(6, (8, 4, 4, 0, -1, 2)) == [2, 4]
+
+
+def test_choice_by_median_with_ties_to_fewer_lanes():
+    # median, not mean: one slow outlier does not decide
+    assert tune.choose({1: [10.0, 10.0, 10.0], 4: [8.0, 8.0, 100.0]}) == 4
+    # within 1% of the fastest: the fewest lanes win
+    assert tune.choose({2: [100.5], 4: [100.0], 8: [99.8]}) == 2
+    assert tune.choose({2: [103.0], 4: [100.0], 8: [99.8]}) == 4
+    with pytest.raises(ValueError):
+        tune.choose({4: []})
+
+
+def test_tune_lanes_times_every_candidate_once():
+    cost = {1: 300.0, 2: 220.0, 4: 200.0, 8: 230.0}
+    seen = []
+
+    def measure(lanes):
+        seen.append(lanes)
+        return [cost[lanes], cost[lanes] * 1.001, cost[lanes] * 0.999]
+
+    lanes, times = tune.tune_lanes(measure, 1024)
+    assert lanes == 4 and sorted(seen) == [1, 2, 4, 8]
+    assert set(times) == {1, 2, 4, 8} and len(times[4]) == 3
+
+
+def test_table_round_trip(tmp_path):
+    path = str(tmp_path / "lanes.json")
+    t = tune.TuneTable(path)
+    assert t.get("mixed", 4095, 20, 1024) is None
+    t.put("mixed", 4095, 20, 1024, 4, {1: [300.0], 4: [200.0, 210.0, 190.0]})
+    t.save()
+    data = json.load(open(path))
+    assert data["mixed/n4095/rf32/b1024"] == {"lanes": 4, "ms": {"1": 300.0, "4": 200.0}}
+    t2 = tune.TuneTable(path)
+    assert t2.get("mixed", 4095, 24, 1024) == 4  # same rank class
+    assert t2.get("fp64", 4095, 20, 1024) is None
+    t2.put("mixed", 4095, 20, 1024, 2, {2: [150.0]})
+    assert t2.get("mixed", 4095, 20, 1024) == 2
