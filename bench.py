@@ -117,6 +117,26 @@ def whole_job_value(batch: int, world: int, steps: int, total_ms: float) -> floa
     return batch * world * steps / (total_ms / 1e3)
 
 
+def to_dev(a):
+    """A host NumPy array as a CUDA float64 tensor (2-D: column-major)."""
+    import numpy as np
+    import torch
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        return torch.from_numpy(a.copy()).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+
+def to_np(t):
+    import numpy as np
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rhs_dev(rhs):
+    """Device copies of a right-hand side's factors (U_f, s_f, V_f)."""
+    return to_dev(rhs.U), to_dev(rhs.s), to_dev(rhs.V)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -689,7 +709,6 @@ def sweep(args):
     import lrp_inputs as li
     import paper_2607_06021_gb300 as lrp
     from oracle import poisson as po
-    from tests.gpu_util import rhs_dev, to_np
     tol, rmax = 1e-6, 64
     rows = []
     for k in range(args.sweep_kmin, args.sweep_kmax + 1):
@@ -739,7 +758,6 @@ def test_matrices(args):
     import lrp_inputs as li
     import paper_2607_06021_gb300 as lrp
     from oracle import matrices as om
-    from tests.gpu_util import rhs_dev, to_np
     out = []
     for kind, tol in (("hilbert", 1e-9), ("k", 1e-6)):
         for n in (1024, 8192, 65536):

@@ -279,3 +279,38 @@ def test_bernoulli_cross_deim_small_grid_within_tolerance():
     W = po.full_grid_solve(rhs.dense())
     err = np.linalg.norm((U * S) @ V.T - W) / np.linalg.norm(W)
     assert err < 10 * tol
+
+
+def test_inv_smin_is_inverse_smallest_singular_value():
+    # A matrix with known singular values 4, 2, 0.5 (orthogonal factors from a
+    # seeded QR): ||M^+||_2 = 1 / 0.5.  Reading eta as 1/sigma_max (the literal
+    # ||(I(:,I_k))^T U_k||_2^{-1}) would give 0.25 and fail here.
+    rng = np.random.default_rng(11)
+    Qa, _ = np.linalg.qr(rng.standard_normal((7, 3)))
+    Qb, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    M = (Qa * np.array([4.0, 2.0, 0.5])) @ Qb.T
+    assert abs(cd.inv_smin(M) - 2.0) < 1e-13
+    # invariant: M^+ M = I for full column rank, and ||M^+||_2 bounds ||M^+ x|| / ||x||
+    x = rng.standard_normal(7)
+    assert np.linalg.norm(np.linalg.pinv(M) @ x) <= cd.inv_smin(M) * np.linalg.norm(x) * (1 + 1e-13)
+    # a rank-deficient square matrix has no finite bound
+    assert cd.inv_smin(np.diag([1.0, 0.0])) == float("inf")
+
+
+def test_diff_norm_against_dense_difference():
+    # ||U_a S_a V_a^T - U_b S_b V_b^T||_F from the stacked-factor QR equals the
+    # norm of the explicitly formed difference; with B = None it is ||S_a||_F.
+    rng = np.random.default_rng(12)
+    Ua, _ = np.linalg.qr(rng.standard_normal((40, 4)))
+    Va, _ = np.linalg.qr(rng.standard_normal((30, 4)))
+    Ub, _ = np.linalg.qr(rng.standard_normal((40, 3)))
+    Vb, _ = np.linalg.qr(rng.standard_normal((30, 3)))
+    Sa, Sb = np.array([3.0, 1.0, 0.2, 0.01]), np.array([2.0, 0.7, 0.1])
+    dense = np.linalg.norm((Ua * Sa) @ Va.T - (Ub * Sb) @ Vb.T)
+    assert abs(cd.diff_norm((Ua, Sa, Va), (Ub, Sb, Vb)) - dense) < 1e-13 * dense
+    assert abs(cd.diff_norm((Ua, Sa, Va), None) - np.linalg.norm(Sa)) < 1e-15
+    # a nearly equal pair: the small difference keeps its relative accuracy
+    # (the dense difference of two O(1) matrices loses ~1e-16 absolute only)
+    Sc = Sa * (1 + 1e-9 * np.arange(1, 5))
+    small = np.linalg.norm((Ua * (Sa - Sc)) @ Va.T)
+    assert abs(cd.diff_norm((Ua, Sa, Va), (Ua, Sc, Va)) - small) < 1e-6 * small
