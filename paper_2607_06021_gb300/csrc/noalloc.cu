@@ -87,14 +87,16 @@ extern "C" lrp_status lrp_dst1_noalloc(int64_t n, int32_t ncols, const double* d
     std::lock_guard<std::mutex> lock(g_addr.mu);
     if (!g_addr.ptr[dev]) {
       SetupGuard guard;
-      cudaError_t e = cudaGetSymbolAddress(&g_addr.ptr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_addr.ptr[dev] = nullptr;
+      void* addr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess)
         return set_error(LRP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      }
-      // The DST kernel needs more than the default dynamic shared memory.
+      // The DST kernel needs more than the default dynamic shared memory.  The
+      // address is cached only once this has succeeded too, so a failed set-up
+      // is retried in full by the next call.
       e = dst_configure();
       if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
+      g_addr.ptr[dev] = addr;
     }
     base = g_addr.ptr[dev];
   }
