@@ -2,18 +2,18 @@
 // Z symmetric orthogonal, applied to n x r factors "in batches along dimensions
 // independently without any global transpose", Sec. 1 / Sec. 3.2).
 //
-// Method (standard real-FFT packing, written from the DFT definition): with
-// N = n+1 a power of two, the odd extension y = [0, x_1..x_n, 0, -x_n..-x_1]
-// of length 2N has DFT Y_k = -2i S_k, S_k = sum_j x_j sin(pi j k / N).  Packing
-// z_j = y_{2j} + i y_{2j+1} (j < N) gives one complex FFT of length N; the
-// even/odd split E_k = (Z_k + conj Z_{N-k})/2, O_k = (Z_k - conj Z_{N-k})/(2i)
-// recovers Y_k = E_k + e^{-i pi k/N} O_k, so S_k = -Im(Y_k)/2 and
-// (Z x)_k = sqrt(2/N) S_k.
+// Two methods, both written from the DFT definition.  N = n+1 <= 8192 (FP64,
+// double-float) or 16384 (FP32): one column per group of threads in shared
+// memory, through a real FFT of length N (a complex FFT of length N/2), see
+// k_dst1_half.  Larger N: the odd extension y = [0, x_1..x_n, 0, -x_n..-x_1] of
+// length 2N has DFT Y_k = -2i S_k, S_k = sum_j x_j sin(pi j k / N); packing
+// z_j = y_{2j} + i y_{2j+1} (j < N) gives one complex FFT of length N, run as a
+// four-step FFT through HBM (k_dst1_passA/B); the even/odd split E_k = (Z_k +
+// conj Z_{N-k})/2, O_k = (Z_k - conj Z_{N-k})/(2i) recovers Y_k = E_k +
+// e^{-i pi k/N} O_k, so S_k = -Im(Y_k)/2 and (Z x)_k = sqrt(2/N) S_k.
 //
-// One CTA per column; the length-N complex sequence lives in shared memory
-// (N * 2 * sizeof(T) bytes: 128 KB at N = 8192 in FP64).  Loads of the
-// column-major input are contiguous; the twiddle table e^{-i pi k/N} (length N,
-// FP64 or FP32) is built once per size and stays L2-resident.
+// The twiddle table e^{-i pi k/N} (length N, FP64, FP32 or double-float) is
+// built once per size and stays cache-resident.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -40,8 +40,6 @@ __global__ void k_twiddle(cplx<TC>* tw, int N) {
   tw[k].im = (TC)(-s);
 }
 
-__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
-
 // (a, c) <- (a + w c, a - w c), the operations of one radix-2 butterfly below.
 template <typename TC>
 __device__ __forceinline__ void butterfly(cplx<TC>& a, cplx<TC>& c, const cplx<TC>& w) {
@@ -53,115 +51,335 @@ __device__ __forceinline__ void butterfly(cplx<TC>& a, cplx<TC>& c, const cplx<T
   a.im = a.im + ti;
 }
 
-// in_ptrs/out_ptrs: one column-0 pointer per slot; ncols_dev (or fixed_cols) gives
-// the number of columns of each slot; blockIdx.x = column, blockIdx.y = slot,
-// blockIdx.z selects one of two matrices of the slot (e.g. U and V).
+// ---------------------------------------------------------------- shared memory
+// For N = n+1 <= 8192 (FP64, double-float) or 16384 (FP32) one column is
+// transformed in shared memory by a real FFT of HALF the length of the odd
+// extension (written from the DFT definition; the pre-processing is the
+// classical one for the sine transform, see e.g. Numerical Recipes, "sine
+// transform").  With x_0 = x_N = 0, a_j = x_j + x_{N-j}, b_j = x_j - x_{N-j}:
+//
+//   u_j = sin(pi j / N) a_j + b_j / 2,                   j = 0..N-1,
+//   U_k = sum_j u_j e^{-2 pi i j k / N} = R_k - i I_k,   k = 0..N/2,
+//
+// and the symmetries of a_j (even about N/2), b_j (odd) and the sines give
+//
+//   S_{2k}   = I_k,                      S_{2k+1} = S_{2k-1} + R_k,  S_1 = R_0 / 2,
+//
+// for S_k = sum_j x_j sin(pi j k / N); (Z x)_k = sqrt(2/N) S_k.  The real DFT
+// U of length N is one complex FFT of length L = N/2 of v_m = u_{2m} + i
+// u_{2m+1}, unpacked with U_k = E_k + e^{-2 pi i k/N} O_k, E_k = (V_k +
+// conj V_{L-k}) / 2, O_k = (V_k - conj V_{L-k}) / (2i).  The odd outputs are a
+// prefix sum, taken as a sequential sum over each thread's 8 consecutive terms
+// plus a shuffle-tree scan of the thread totals (error ~ (8 + 2 log2 T) ulp of
+// the partial sums).
+//
+// The complex FFT runs Stockham stages of radix 8 (a last radix-4 or radix-2
+// stage when log2 L is not a multiple of 3): each thread holds 8 elements in
+// registers per stage, so a stage is one read of the shared buffer, a barrier
+// and one write; twiddles e^{-i pi u / N} come from the L1-resident table.
+// T_c = L/8 threads serve one column; columns with L < 2048 share a CTA of 256
+// threads (2048 / L columns).  Global loads and stores are coalesced along the
+// column (the pre-processing reads x_j and x_{N-j} as a forward and a backward
+// run; the outputs are staged in shared memory and written in order).
+template <typename TC> struct TwVec;
+template <> struct TwVec<float> { using V = float2; };
+template <> struct TwVec<double> { using V = double2; };
+template <> struct TwVec<dfloat> { using V = float4; };
+
+template <typename TC>
+__device__ __forceinline__ cplx<TC> tw_load(const cplx<TC>* __restrict__ tw, int k) {
+  using V = typename TwVec<TC>::V;
+  const V v = __ldg(reinterpret_cast<const V*>(tw) + k);
+  cplx<TC> w;
+  if constexpr (std::is_same<TC, dfloat>::value) {
+    w.re = dfloat(v.x, v.y);
+    w.im = dfloat(v.z, v.w);
+  } else {
+    w.re = v.x;
+    w.im = v.y;
+  }
+  return w;
+}
+
+// e^{-i pi u / N} for any integer u >= 0 from the table e^{-i pi t / N}, t < N.
+template <typename TC>
+__device__ __forceinline__ cplx<TC> tw_any(const cplx<TC>* __restrict__ tw, int u, int N) {
+  u &= 2 * N - 1;
+  if (u < N) return tw_load(tw, u);
+  const cplx<TC> w = tw_load(tw, u - N);
+  return {-w.re, -w.im};
+}
+
+template <typename TC>
+__device__ __forceinline__ cplx<TC> cmul(const cplx<TC>& a, const cplx<TC>& b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename TC>
+__device__ __forceinline__ void bfly2(cplx<TC>& a, cplx<TC>& b) {
+  const cplx<TC> t = a;
+  a = {t.re + b.re, t.im + b.im};
+  b = {t.re - b.re, t.im - b.im};
+}
+template <typename TC>
+__device__ __forceinline__ cplx<TC> mul_mi(const cplx<TC>& a) {  // a * (-i)
+  return {a.im, -a.re};
+}
+
+// In-register DFT of length R (2, 4 or 8), e^{-2 pi i / R}; a radix-2
+// decimation-in-frequency network, outputs returned in natural order.
+template <typename TC, int R>
+__device__ __forceinline__ void dft_small(cplx<TC>* v) {
+  if constexpr (R == 2) {
+    bfly2(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    bfly2(v[0], v[2]);
+    bfly2(v[1], v[3]);
+    v[3] = mul_mi(v[3]);
+    bfly2(v[0], v[1]);
+    bfly2(v[2], v[3]);
+    const cplx<TC> t = v[1];
+    v[1] = v[2];
+    v[2] = t;
+  } else {
+    const TC c = TC(0.70710678118654752440);
+    bfly2(v[0], v[4]);
+    bfly2(v[1], v[5]);
+    bfly2(v[2], v[6]);
+    bfly2(v[3], v[7]);
+    v[5] = {c * (v[5].re + v[5].im), c * (v[5].im - v[5].re)};     // * (1 - i)/sqrt(2)
+    v[6] = mul_mi(v[6]);                                             // * (-i)
+    v[7] = {c * (v[7].im - v[7].re), TC(0) - c * (v[7].re + v[7].im)};  // * (-1 - i)/sqrt(2)
+    bfly2(v[0], v[2]);
+    bfly2(v[1], v[3]);
+    bfly2(v[4], v[6]);
+    bfly2(v[5], v[7]);
+    v[3] = mul_mi(v[3]);
+    v[7] = mul_mi(v[7]);
+    bfly2(v[0], v[1]);
+    bfly2(v[2], v[3]);
+    bfly2(v[4], v[5]);
+    bfly2(v[6], v[7]);
+    // bit-reversed -> natural: X0 v0, X1 v4, X2 v2, X3 v6, X4 v1, X5 v5, X6 v3, X7 v7
+    cplx<TC> t = v[1];
+    v[1] = v[4];
+    v[4] = t;
+    t = v[3];
+    v[3] = v[6];
+    v[6] = t;
+  }
+}
+
+// One Stockham stage of radix R on the column's L complex values in z: the
+// group's T_c = L/8 threads take butterflies j = t + q T_c (8/R each): inputs
+// z[j + r L/R], twiddles e^{-2 pi i r k / (Ns R)} (k = j mod Ns), outputs
+// z[(j - k) R + k + r Ns].  Reads complete before writes (barrier).
+template <typename TC, int R>
+__device__ __forceinline__ void stockham_stage(cplx<TC>* z, int L, int Ns, int N, int t, int Tc,
+                                               const cplx<TC>* __restrict__ tw) {
+  constexpr int P = 8 / R;
+  cplx<TC> v[P][R];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int j = t + q * Tc;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q][r] = z[j + r * (L / R)];
+  }
+  __syncthreads();
+  const int step = 2 * N / (Ns * R);  // e^{-2 pi i r k / (Ns R)} = e^{-i pi (r k step) / N}
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int j = t + q * Tc;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tw_any(tw, r * k * step, N));
+    }
+    dft_small<TC, R>(v[q]);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[base + r * Ns] = v[q][r];
+  }
+  __syncthreads();
+}
+
+template <typename TC>
+__device__ __forceinline__ TC shfl_up_tc(TC v, int d, int width) {
+  if constexpr (std::is_same<TC, dfloat>::value) {
+    return dfloat(__shfl_up_sync(0xffffffffu, v.hi, d, width), __shfl_up_sync(0xffffffffu, v.lo, d, width));
+  } else {
+    return __shfl_up_sync(0xffffffffu, v, d, width);
+  }
+}
+template <typename TC>
+__device__ __forceinline__ TC shfl_idx_tc(TC v, int src, int width) {
+  if constexpr (std::is_same<TC, dfloat>::value) {
+    return dfloat(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
+  } else {
+    return __shfl_sync(0xffffffffu, v, src, width);
+  }
+}
+
+// Exclusive scan of one value per thread over a column group of Tc threads
+// (Tc a power of two; groups are warp-aligned when Tc >= 32).  wt: shared
+// scratch of 32 values per group.  Every thread of the CTA must call it.
+template <typename TC>
+__device__ __forceinline__ TC group_exclusive_scan(TC v, int t, int Tc, TC* wt) {
+  const int width = Tc < 32 ? Tc : 32;
+  const int lane = t & (width - 1);
+  TC s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    if (o < width) {
+      const TC y = shfl_up_tc(s, o, width);
+      if (lane >= o) s = s + y;
+    }
+  }
+  TC ex = shfl_up_tc(s, 1, width);
+  if (lane == 0) ex = TC(0);
+  if (Tc > 32) {
+    const int w = t >> 5, nw = Tc >> 5;
+    if (lane == 31) wt[w] = s;
+    __syncthreads();
+    // inclusive scan of the warp totals in every warp, then the prefix before w
+    TC a = (lane < nw) ? wt[lane] : TC(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const TC y = shfl_up_tc(a, o, 32);
+      if (lane >= o) a = a + y;
+    }
+    TC before = shfl_idx_tc(a, (w > 0 ? w - 1 : 0), 32);
+    if (w == 0) before = TC(0);
+    ex = before + ex;
+  } else {
+    __syncthreads();  // keep the CTA's barrier count uniform across group sizes
+  }
+  return ex;
+}
+
+constexpr int kDstMinN = 128;  // smaller N: the direct O(N^2) sum (k_dst1_direct)
+
+template <typename TC>
+constexpr int dst_max_threads() { return sizeof(TC) == 4 ? 1024 : 512; }
+
+// in/out pointers per (mat, slot); blockIdx.x = column group, .y = slot, .z = matrix.
 template <typename TIn, typename TOut, typename TC>
-__global__ void k_dst1_smem(int n, int logN, const DstBatch<TIn, TOut> job,
-                            const cplx<TC>* __restrict__ tw) {
-  extern __shared__ unsigned char smem_raw[];
-  cplx<TC>* z = reinterpret_cast<cplx<TC>*>(smem_raw);
-  const int N = n + 1;
-  const int col = blockIdx.x;
-  const int slot = blockIdx.y;
-  const int mat = blockIdx.z;
+__global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int logL, int cols_per_cta,
+                                                                   const DstBatch<TIn, TOut> job,
+                                                                   const cplx<TC>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = n + 1, L = N >> 1, Tc = L >> 3;
+  const int g = threadIdx.x / Tc, t = threadIdx.x - g * Tc;
+  const int slot = blockIdx.y, mat = blockIdx.z;
+  const int col = blockIdx.x * cols_per_cta + g;
+  // per column: z (L complex = N scalars), R (L + L/32 scalars); per group 32 scan values
+  const int per_col = N + L + (L >> 5);
+  TC* colbuf = reinterpret_cast<TC*>(smem_raw) + (int64_t)g * per_col;
+  cplx<TC>* z = reinterpret_cast<cplx<TC>*>(colbuf);
+  TC* Rb = colbuf + N;
+  TC* wt = reinterpret_cast<TC*>(smem_raw) + (int64_t)cols_per_cta * per_col + 32 * g;
   int ncols = job.fixed_cols;
   if (job.ncols_dev) ncols = job.ncols_dev[slot * job.ncols_stride + mat * job.ncols_mat_stride];
-  if (job.active_dev && job.active_dev[slot * job.active_stride] == 0 && job.require_active) return;
-  if (col >= ncols) return;
-  const TIn* x = job.in[mat * job.nslots + slot] + (int64_t)col * job.ld_in[mat * job.nslots + slot];
-  TOut* y = job.out[mat * job.nslots + slot] + (int64_t)col * job.ld_out[mat * job.nslots + slot];
-  if (x == nullptr || y == nullptr) return;
+  bool live = col < ncols;
+  if (job.active_dev && job.require_active && job.active_dev[slot * job.active_stride] == 0) live = false;
+  const TIn* x = job.in[mat * job.nslots + slot];
+  TOut* y = job.out[mat * job.nslots + slot];
+  if (x == nullptr || y == nullptr) live = false;
+  // A CTA whose columns are all idle leaves before its first barrier; otherwise
+  // idle groups run the barriers on zeros and store nothing.
+  if (__syncthreads_count(live ? 1 : 0) == 0) return;
+  if (live) {
+    x += (int64_t)col * job.ld_in[mat * job.nslots + slot];
+    y += (int64_t)col * job.ld_out[mat * job.nslots + slot];
+  }
 
-  // Pack: z_j = y_{2j} + i y_{2j+1}; y_0 = y_N = 0, y_i = x_i (1 <= i <= n),
-  // y_{2N-i} = -x_i.  x is 1-based in the formulas, x[i-1] in memory.
-  const int half = N >> 1;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    TC re, im;
-    if (j < half) {
-      const int e = 2 * j, o = 2 * j + 1;
-      re = (e == 0) ? (TC)0 : (TC)x[e - 1];
-      im = (TC)x[o - 1];
-    } else {
-      const int e = 2 * N - 2 * j, o = 2 * N - 2 * j - 1;  // e in [2, N], o in [1, N-1]
-      re = (e == N) ? (TC)0 : -(TC)x[e - 1];
-      im = -(TC)x[o - 1];
+  // Pre-processing: u_j and u_{N-j} for j = 1..N/2-1 (x_j = x[j-1]); u_0 = 0,
+  // u_{N/2} = 2 x_{N/2}.  u_j goes to v_{j/2}.re (j even) or .im (j odd).
+  TC* zs = colbuf;  // z as scalars: zs[j] = u_j
+  const TC half = TC(0.5);
+  for (int j = 1 + t; j < L; j += Tc) {
+    TC xa = TC(0), xb = TC(0);
+    if (live) {
+      xa = TC(x[j - 1]);
+      xb = TC(x[N - j - 1]);
     }
-    const int p = bitrev(j, logN);
-    z[p].re = re;
-    z[p].im = im;
+    const TC sj = TC(0) - tw_load(tw, j).im;  // sin(pi j / N)
+    const TC a = xa + xb, b = xa - xb;
+    zs[j] = sj * a + half * b;
+    zs[N - j] = sj * a - half * b;
+  }
+  if (t == 0) {
+    zs[0] = TC(0);
+    const TC xm = live ? TC(x[L - 1]) : TC(0);
+    zs[L] = xm + xm;
   }
   __syncthreads();
 
-  // Radix-2 decimation-in-time butterflies; twiddle e^{-2 pi i pos/(2h)} = tw[pos * N / h].
-  int s = 1;
-  if constexpr (std::is_same<TC, dfloat>::value) {
-    // Double-float steps are explicitly rounded (nothing is contracted), so the
-    // stages can go in pairs with the same operations: the elements i, i+h,
-    // i+2h, i+3h of a 4h block take both stages' butterflies in registers,
-    // with half the barriers and shared-memory round trips.
-    for (; s + 1 <= logN; s += 2) {
-      const int h = 1 << (s - 1);
-      const int st0 = N >> (s - 1), st1 = N >> s;
-      for (int b = threadIdx.x; b < (N >> 2); b += blockDim.x) {
-        const int pos = b & (h - 1);
-        const int i = ((b >> (s - 1)) << (s + 1)) + pos;
-        cplx<TC> a0 = z[i], a1 = z[i + h], a2 = z[i + 2 * h], a3 = z[i + 3 * h];
-        const cplx<TC> w0 = tw[pos * st0];
-        butterfly(a0, a1, w0);
-        butterfly(a2, a3, w0);
-        const cplx<TC> w1 = tw[pos * st1], w2 = tw[(pos + h) * st1];
-        butterfly(a0, a2, w1);
-        butterfly(a1, a3, w2);
-        z[i] = a0;
-        z[i + h] = a1;
-        z[i + 2 * h] = a2;
-        z[i + 3 * h] = a3;
-      }
-      __syncthreads();
-    }
-  }
-  for (; s <= logN; ++s) {
-    const int h = 1 << (s - 1);
-    const int stride = N >> (s - 1);  // N / h
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const int pos = b & (h - 1);
-      const int i0 = ((b >> (s - 1)) << s) + pos;
-      const int i1 = i0 + h;
-      const cplx<TC> w = tw[pos * stride];
-      const cplx<TC> a = z[i0], c = z[i1];
-      const TC tr = w.re * c.re - w.im * c.im;
-      const TC ti = w.re * c.im + w.im * c.re;
-      z[i1].re = a.re - tr;
-      z[i1].im = a.im - ti;
-      z[i0].re = a.re + tr;
-      z[i0].im = a.im + ti;
-    }
-    __syncthreads();
-  }
+  // Complex FFT of length L (natural order in, natural order out).
+  int Ns = 1, bits = logL;
+  for (; bits >= 3; bits -= 3, Ns <<= 3) stockham_stage<TC, 8>(z, L, Ns, N, t, Tc, tw);
+  if (bits == 2) stockham_stage<TC, 4>(z, L, Ns, N, t, Tc, tw);
+  else if (bits == 1) stockham_stage<TC, 2>(z, L, Ns, N, t, Tc, tw);
 
-  // Unpack pairs (k, N-k), k = 1..N/2.
-  const TC scale = (TC)sqrt(2.0 / (double)N);
-  for (int k = 1 + threadIdx.x; k <= half; k += blockDim.x) {
-    const int m = N - k;
-    const cplx<TC> Zk = z[k], Zm = z[m];
-    // E_k = (Zk + conj Zm)/2 ; O_k = (Zk - conj Zm)/(2i)
-    const TC Er = (Zk.re + Zm.re) * (TC)0.5, Ei = (Zk.im - Zm.im) * (TC)0.5;
-    const TC Dr = (Zk.re - Zm.re) * (TC)0.5, Di = (Zk.im + Zm.im) * (TC)0.5;  // (Zk - conj Zm)/2
-    const TC Or = Di, Oi = -Dr;                                               // divide by i
-    const cplx<TC> w = tw[k];
-    // Y_k = E_k + w O_k; S_k = -Im(Y_k)/2
-    const TC Yk_im = Ei + (w.re * Oi + w.im * Or);
-    y[k - 1] = (TOut)(-(TC)0.5 * Yk_im * scale);
-    if (m != k) {
-      // E_{N-k} = conj(E_k); O_{N-k} = (Zm - conj Zk)/(2i) = conj(O_k) * (-1)... computed directly
-      const TC Emi = -Ei;
-      const TC D2r = (Zm.re - Zk.re) * (TC)0.5, D2i = (Zm.im + Zk.im) * (TC)0.5;
-      const TC O2r = D2i, O2i = -D2r;
-      const cplx<TC> w2 = {-w.re, w.im};  // e^{-i pi (N-k)/N} = -conj(e^{-i pi k/N})
-      const TC Ym_im = Emi + (w2.re * O2i + w2.im * O2r);
-      y[m - 1] = (TOut)(-(TC)0.5 * Ym_im * scale);
-    }
+  // Unpack (strided k = t + e Tc): R_k, I_k of the real DFT of u.
+  TC Rr[8], Ir[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = t + e * Tc;
+    const cplx<TC> Vk = z[k], Vm = z[(L - k) & (L - 1)];
+    const TC Er = (Vk.re + Vm.re) * half, Ei = (Vk.im - Vm.im) * half;
+    const TC Or = (Vk.im + Vm.im) * half, Oi = (Vm.re - Vk.re) * half;  // (Vk - conj Vm) / (2i)
+    const cplx<TC> w = tw_load(tw, 2 * k);                                // e^{-2 pi i k / N}
+    Rr[e] = Er + (w.re * Or - w.im * Oi);
+    Ir[e] = TC(0) - (Ei + (w.re * Oi + w.im * Or));
+  }
+  __syncthreads();
+  TC* Y = zs;  // staged outputs: Y[k' - 1] = S_{k'}
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = t + e * Tc;
+    if (k > 0) Y[2 * k - 1] = Ir[e];
+    Rb[k + (k >> 5)] = (k == 0) ? Rr[e] * half : Rr[e];
+  }
+  __syncthreads();
+  // S_{2k+1} = sum_{m <= k} R'_m over the thread's 8 consecutive k, then the
+  // group's exclusive scan of the thread totals.
+  TC acc[8];
+  TC run = TC(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = 8 * t + e;
+    run = run + Rb[k + (k >> 5)];
+    acc[e] = run;
+  }
+  const TC before = group_exclusive_scan(run, t, Tc, wt);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) Y[2 * (8 * t + e)] = before + acc[e];
+  __syncthreads();
+  if (live) {
+    const TC scale = TC(sqrt(2.0 / (double)N));
+    for (int i = t; i < n; i += Tc) y[i] = (TOut)(scale * Y[i]);
+  }
+}
+
+// Small N (< kDstMinN): one thread per output, the defining sum.
+template <typename TIn, typename TOut, typename TC>
+__global__ void k_dst1_direct(int n, const DstBatch<TIn, TOut> job, const cplx<TC>* __restrict__ tw) {
+  const int N = n + 1;
+  const int col = blockIdx.x, slot = blockIdx.y, mat = blockIdx.z;
+  int ncols = job.fixed_cols;
+  if (job.ncols_dev) ncols = job.ncols_dev[slot * job.ncols_stride + mat * job.ncols_mat_stride];
+  if (col >= ncols) return;
+  if (job.active_dev && job.require_active && job.active_dev[slot * job.active_stride] == 0) return;
+  const TIn* x = job.in[mat * job.nslots + slot];
+  TOut* y = job.out[mat * job.nslots + slot];
+  if (x == nullptr || y == nullptr) return;
+  x += (int64_t)col * job.ld_in[mat * job.nslots + slot];
+  y += (int64_t)col * job.ld_out[mat * job.nslots + slot];
+  const TC scale = TC(sqrt(2.0 / (double)N));
+  for (int k = 1 + threadIdx.x; k <= n; k += blockDim.x) {
+    TC s = TC(0);
+    for (int j = 1; j <= n; ++j) s = s + TC(x[j - 1]) * (TC(0) - tw_any(tw, j * k, N).im);  // sin(pi j k / N)
+    y[k - 1] = (TOut)(scale * s);
   }
 }
 
@@ -353,6 +571,14 @@ size_t dst_temp_bytes(int64_t n, bool fp64) {
   return dst_smem_supported(n, fp64) ? 0 : (size_t)(n + 1) * (fp64 ? 16 : 8);
 }
 
+// Shared memory of k_dst1_half: per column N + L + L/32 values, plus 32 scan
+// values per column group.
+template <typename TC>
+static size_t dst_half_smem(int N, int cols_per_cta) {
+  const int L = N / 2;
+  return sizeof(TC) * ((size_t)cols_per_cta * (N + L + L / 32) + 32 * (size_t)cols_per_cta);
+}
+
 template <typename TIn, typename TOut, typename TC>
 cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols, int nslots, int nmats,
                         const void* tw, cudaStream_t st, void* temp, size_t temp_bytes) {
@@ -382,26 +608,25 @@ cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols,
                                                          (const cplx<TC>*)tw, (const cplx<TC>*)temp, (int64_t)N);
     return cudaGetLastError();
   }
-  const int logN = ilog2(N);
-  const size_t smem = (size_t)N * sizeof(cplx<TC>);
-  auto kern = k_dst1_smem<TIn, TOut, TC>;
-  int threads = N >= 2048 ? 512 : (N >= 512 ? 256 : 128);
-  dim3 grid(max_cols, nslots, nmats);
   if (max_cols <= 0 || nslots <= 0) return cudaSuccess;
-  kern<<<grid, threads, smem, st>>>((int)n, logN, job, (const cplx<TC>*)tw);
+  if (N < kDstMinN) {
+    dim3 grid(max_cols, nslots, nmats);
+    k_dst1_direct<TIn, TOut, TC><<<grid, 64, 0, st>>>((int)n, job, (const cplx<TC>*)tw);
+    return cudaGetLastError();
+  }
+  const int L = N / 2, logL = ilog2(L);
+  const int Tc = L / 8;
+  const int cols_per_cta = Tc >= 256 ? 1 : 256 / Tc;
+  const int threads = Tc * cols_per_cta;
+  const size_t smem = dst_half_smem<TC>(N, cols_per_cta);
+  dim3 grid((max_cols + cols_per_cta - 1) / cols_per_cta, nslots, nmats);
+  k_dst1_half<TIn, TOut, TC><<<grid, threads, smem, st>>>((int)n, logL, cols_per_cta, job, (const cplx<TC>*)tw);
   return cudaGetLastError();
 }
 
 cudaError_t dst_configure() {
   const int bytes = 200 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_dst1_smem<double, double, double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dst1_smem<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dst1_smem<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dst1_smem<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaSuccess;
 #define LRP_CFG(K)                                                                              \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   LRP_CFG((k_dst1_passA<double, double, double>))
@@ -412,7 +637,11 @@ cudaError_t dst_configure() {
   LRP_CFG((k_dst1_passB<double, float, float>))
   LRP_CFG((k_dst1_passB<float, double, float>))
   LRP_CFG((k_dst1_passB<float, float, float>))
-  LRP_CFG((k_dst1_smem<double, double, dfloat>))
+  LRP_CFG((k_dst1_half<double, double, double>))
+  LRP_CFG((k_dst1_half<double, float, float>))
+  LRP_CFG((k_dst1_half<float, double, float>))
+  LRP_CFG((k_dst1_half<float, float, float>))
+  LRP_CFG((k_dst1_half<double, double, dfloat>))
   LRP_CFG((k_dst1_passA<double, double, dfloat>))
   LRP_CFG((k_dst1_passB<double, double, dfloat>))
 #undef LRP_CFG
