@@ -8,12 +8,13 @@ Library primitives serve as single steps (Householder QR, SVD, pinv, pivoted
 QR); nothing is blocked, fused or reordered.
 
 Readings where the paper is silent or garbled:
-  * initial guess U_{-1}, V_{-1}: orthonormal bases of the transformed RHS
-    factors (the paper only says "warm started");
-  * leverage scores select the top-c rows deterministically (c = columns of the
-    input basis), ties to the lower index, in place of Bernoulli sampling; the
-    Bernoulli form of Algorithm LeverageScores is the selector "bernoulli", its
-    c = sample_factor x columns and its draws from Philox4x32-10;
+  * initial guess U_{-1}, V_{-1}: orthonormal bases of the numerical range of
+    the transformed RHS factors (the paper only says "warm started"), columns
+    whose Householder |R(l,l)| falls below 1e-12 max|diag R| dropped;
+  * leverage scores: Algorithm LeverageScores as printed, Bernoulli sampling
+    (the default selector "bernoulli"), c = sample_factor x columns, draws from
+    Philox4x32-10; the selector "ls" takes the top-c rows deterministically
+    instead (c = columns of the input basis), ties to the lower index;
   * new indices are appended after the previous ones in descending score;
   * the growth safeguard adds one index to I_k (not to I_k^*), drawn from the
     SplitMix64 generator (Steele, Lea, Flood 2014) keyed by (seed, k, side),
@@ -245,7 +246,7 @@ class CrossDEIMInfo:
 
 
 def cross_deim(G, U0, V0, tol: float, r_max: int, maxiter: int = 30,
-               selector: str = "ls", seed: int = 0, m_cap: int | None = None,
+               selector: str = "bernoulli", seed: int = 0, m_cap: int | None = None,
                inloop_rel: float | None = None, redundancy: float = 1e-12,
                I0=None, J0=None, A0=None, sample_factor: float = 1.0):
     """Algorithm Cross-DEIM on a matrix given by entry access (G.cols / G.rows).
@@ -313,14 +314,22 @@ def cross_deim(G, U0, V0, tol: float, r_max: int, maxiter: int = 30,
     return res.U[:, :r], res.S[:r], res.V[:, :r], info
 
 
-def orth(X: np.ndarray) -> np.ndarray:
-    """Orthonormal basis of range(X) (Householder QR)."""
-    Q, _ = np.linalg.qr(X)
-    return Q
+def orth(X: np.ndarray, tau: float = 1e-12) -> np.ndarray:
+    """Orthonormal basis of the numerical range of X: Householder QR, keeping
+    the columns l of Q with |R(l,l)| >= tau max|diag R| (the relative reading of
+    the paper's numerical-zero threshold 1e-12, the test of the redundancy
+    removal).  A numerically dependent column of X (say, two equal terms of the
+    right-hand side) would otherwise add a direction of pure rounding noise to
+    the initial basis and to its leverage scores.  At least one column is kept."""
+    Q, R = np.linalg.qr(X)
+    d = np.abs(np.diag(R))
+    if d.size == 0 or d.max() <= 0:
+        return Q[:, :1]
+    return Q[:, d >= tau * d.max()]
 
 
 def poisson_solve(U_f, s_f, V_f, tol: float, r_max: int, maxiter: int = 30,
-                  selector: str = "ls", seed: int = 0, m_cap: int | None = None,
+                  selector: str = "bernoulli", seed: int = 0, m_cap: int | None = None,
                   inloop_rel: float | None = None, warm=None, sample_factor: float = 1.0):
     """Low-rank Poisson solve of Sec. 3.2.
 

@@ -18,12 +18,15 @@ from oracle import poisson as po  # noqa: E402
 
 def main():
     out = {}
-    for seed in (0, 1):
+    runs = [(seed, sel, suffix, what) for seed in (0, 1)
+            for sel, suffix, what in (("ls", "", "leverage scores, top-c"),
+                                      ("bernoulli", "_bernoulli", "leverage scores, Bernoulli sampling"))]
+    for seed, sel, suffix, what in runs:
         rhs = li.workload_single_small(seed)
         U, S, V, info, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, 1e-10, 32, seed=seed,
-                                            m_cap=2 * 32 + 4)
-        out[f"n255_seed{seed}"] = {
-            "workload": "n=255, 4 Gaussians, tol 1e-10, max rank 32, leverage scores, m_cap 68",
+                                            m_cap=2 * 32 + 4, selector=sel)
+        out[f"n255_seed{seed}{suffix}"] = {
+            "workload": f"n=255, 4 Gaussians, tol 1e-10, max rank 32, {what}, m_cap 68",
             "iterations": info.iterations,
             "converged": info.converged,
             "rank": int(S.shape[0]),
