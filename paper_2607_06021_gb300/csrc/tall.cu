@@ -34,13 +34,6 @@ constexpr int NT = 256;
 constexpr int kSmallGram = 64;
 constexpr int kSmallRows = 32;
 
-// Cross tile: XR rows x XC columns per CTA, 256 threads; warp w owns columns
-// 8w..8w+7 of the tile and its 32 four-row groups, so that every store of a
-// column segment is 512 contiguous bytes (FP32).
-constexpr int XR = 128;
-constexpr int XC = 64;
-constexpr int XK = 16;
-
 template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
   if constexpr (sizeof(T) == 4) {
@@ -68,6 +61,17 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 
+// Sampled columns / rows of the transformed solution (Eq. g_for_p), one thread
+// per output row: C(i, q) = (sum_k Fs(i,k) w_k Fo(J_q,k)) / (lambda_i + lambda_{J_q})
+// for q < m.  The CTA stages B(k, q) = w_k Fo(J_q, k) for a chunk of KC x QC
+// entries in shared memory (read by broadcast); each thread keeps QC sums in
+// registers and reads its row's Fs(i, k) once per column chunk (coalesced
+// across the warp); the outputs leave as one coalesced store per column.  Each
+// sum runs over k in ascending order with one FMA per term, as the earlier
+// tiled form did, so the values are the same bit for bit.
+constexpr int XQ = 32;  // columns per register block
+constexpr int XK = 32;  // k per shared-memory chunk
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __restrict__ st_all, CrossArgs<T> a) {
   const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
@@ -75,81 +79,60 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int m = st.cnt[1 - side];
-  const int r0 = blockIdx.x * XR, c0 = blockIdx.y * XC;
-  if (c0 >= m || r0 >= g.n) return;
+  const int row = blockIdx.x * NT + threadIdx.x;
+  if (blockIdx.x * NT >= g.n || m < 1) return;
   const int rf = st.rf;
   const T* Fs = a.F.at(slot, side);
   const T* Fo = a.F.at(slot, 1 - side);
   const int32_t* ix = a.idx.at(slot, 1 - side);
   const T* w = a.w + (int64_t)slot * a.wstride;
-
-  __shared__ __align__(16) T As[XK][XR];
-  __shared__ __align__(16) T Bs[XK][XC];
-  __shared__ int jc[XC];
-  __shared__ T lamc[XC];
-  const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;  // rows 4 ty.., columns 8 tx..
-  if (tid < XC) {
-    const int c = c0 + tid;
-    const int j = (c < m) ? ix[c] : -1;
-    jc[tid] = j;
-    lamc[tid] = (j >= 0) ? a.lam[j] : (T)1;
-  }
-  __syncthreads();
-  T acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = (T)0;
-
-  for (int k0 = 0; k0 < rf; k0 += XK) {
-#pragma unroll
-    for (int q = 0; q < (XK * XR) / NT; ++q) {
-      const int e = tid + NT * q;
-      const int kk = e / XR, i = e % XR;
-      const int row = r0 + i, k = k0 + kk;
-      As[kk][i] = (row < g.n && k < rf) ? Fs[(int64_t)k * g.ld + row] : (T)0;
+  T* A = a.A.at(slot, side);
+  __shared__ __align__(16) T Bs[XK][XQ];
+  __shared__ int jc[XQ];
+  __shared__ T lamc[XQ];
+  const bool live = row < g.n;
+  const T li = live ? a.lam[row] : T(1);
+  for (int q0 = 0; q0 < m; q0 += XQ) {
+    const int qn = min(XQ, m - q0);
+    __syncthreads();  // the previous block's jc / lamc are read no more
+    if (threadIdx.x < XQ) {
+      const int j = (threadIdx.x < qn) ? ix[q0 + threadIdx.x] : -1;
+      jc[threadIdx.x] = j;
+      lamc[threadIdx.x] = (j >= 0) ? a.lam[j] : T(1);
     }
+    T acc[XQ];
 #pragma unroll
-    for (int q = 0; q < (XK * XC) / NT; ++q) {
-      const int e = tid + NT * q;
-      const int kk = e / XC, c = e % XC;
-      const int k = k0 + kk, j = jc[c];
-      Bs[kk][c] = (j >= 0 && k < rf) ? w[k] * Fo[(int64_t)k * g.ld + j] : (T)0;
-    }
-    __syncthreads();
-    const int kn = min(XK, rf - k0);
-    for (int kk = 0; kk < kn; ++kk) {
-      T av[4], b0[4], b1[4];
-      ld4<T>(&As[kk][4 * ty], av);
-      ld4<T>(&Bs[kk][8 * tx], b0);
-      ld4<T>(&Bs[kk][8 * tx + 4], b1);
+    for (int q = 0; q < XQ; ++q) acc[q] = T(0);
+    for (int k0 = 0; k0 < rf; k0 += XK) {
+      const int kn = min(XK, rf - k0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < XK * XQ; e += NT) {
+        const int kk = e / XQ, q = e % XQ, k = k0 + kk;
+        const int j = jc[q];
+        Bs[kk][q] = (j >= 0 && kk < kn) ? w[k] * Fo[(int64_t)k * g.ld + j] : T(0);
+      }
+      __syncthreads();
+      if (live) {
+        for (int kk = 0; kk < kn; ++kk) {
+          const T av = Fs[(int64_t)(k0 + kk) * g.ld + row];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+          for (int q = 0; q < XQ; q += 4) {
+            T b[4];
+            ld4<T>(&Bs[kk][q], b);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[i][j] = fma(av[i], b0[j], acc[i][j]);
-          acc[i][j + 4] = fma(av[i], b1[j], acc[i][j + 4]);
+            for (int t = 0; t < 4; ++t) acc[q + t] = fma(av, b[t], acc[q + t]);
+          }
         }
       }
     }
-    __syncthreads();
-  }
-  T* A = a.A.at(slot, side);
-  const int row0 = r0 + 4 * ty;
-  if (row0 >= g.n) return;
-  T li[4];
+    if (live) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) li[i] = (row0 + i < g.n) ? a.lam[row0 + i] : (T)1;
-  // ld is a multiple of 32 and row0 of 4: whole 4-row segments stay inside the
-  // padded column (rows n..ld-1 are padding)
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int c = 8 * tx + j;
-    if (c0 + c >= m) continue;
-    T v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = (row0 + i < g.n) ? acc[i][j] * recip(li[i] + lamc[c]) : (T)0;
-    st4<T>(&A[(int64_t)(c0 + c) * g.ld + row0], v);
+      for (int q = 0; q < XQ; ++q)
+        if (q < qn) A[(int64_t)(q0 + q) * g.ld + row] = acc[q] * recip(li + lamc[q]);
+    } else if (row < g.ld) {
+      // the padding rows n..ld-1 of each column hold zeros
+      for (int q = 0; q < qn; ++q) A[(int64_t)(q0 + q) * g.ld + row] = T(0);
+    }
   }
 }
 
@@ -826,22 +809,60 @@ __global__ void k_leverage(TallGeom g, const SolveState* __restrict__ st_all, St
   const int rbeg = blk * rows_per_cand_block;
   const int rend = min(g.n, rbeg + rows_per_cand_block);
   const T* U = us.at(slot, side);
+  if (ls.on) {
+    // Bernoulli: keep row i with probability min(1, c pi_i) = min(1, factor s_i).
+    // Only the kept rows are sorted (best first, ties to the lower index): they
+    // are appended to the front of key / id, then sorted over the next power
+    // of two, which orders them exactly as a sort of the whole block would.
+    __shared__ int kept;
+    if (threadIdx.x == 0) kept = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
+      const int row = rbeg + t;
+      if (row >= rend) continue;
+      T s = T(0);
+#pragma unroll 4
+      for (int q = 0; q < c; ++q) {
+        const T v = U[(int64_t)q * g.ld + row];
+        s = fma(v, v, s);
+      }
+      const double pr = fmin(1.0, ls.factor * (double)s);
+      if (philox_uniform(ls.seed, (uint32_t)(st.k + ls.k_ofs), (uint32_t)side, (uint32_t)row) < pr) {
+        const int at = atomicAdd(&kept, 1);
+        key[at] = s;
+        id[at] = row;
+      }
+    }
+    __syncthreads();
+    const int nk = kept;
+    int len = 1;
+    while (len < nk) len <<= 1;
+    for (int t = nk + threadIdx.x; t < len; t += blockDim.x) {
+      key[t] = T(-1);
+      id[t] = 0x7fffffff;
+    }
+    __syncthreads();
+    bitonic_sort<T>(key, id, len);
+    const int64_t base = ((int64_t)(slot * 2 + side) * cand_blocks + blk) * cand_per_block;
+    for (int t = threadIdx.x; t < cand_per_block; t += blockDim.x) {
+      const bool ok = t < nk;
+      cscore[base + t] = ok ? (double)key[t] : -1.0;
+      cidx[base + t] = ok ? id[t] : -1;
+    }
+    return;
+  }
   for (int t = threadIdx.x; t < sort_len; t += blockDim.x) {
     const int row = rbeg + t;
     T s = T(-1);
     int ii = 0x7fffffff;
     if (row < rend) {
       s = T(0);
+#pragma unroll 4
       for (int q = 0; q < c; ++q) {
         const T v = U[(int64_t)q * g.ld + row];
         s = fma(v, v, s);
       }
       ii = row;
-      // Bernoulli: keep the row with probability min(1, c pi_i) = min(1, factor s)
-      if (ls.on) {
-        const double pr = fmin(1.0, ls.factor * (double)s);
-        if (!(philox_uniform(ls.seed, (uint32_t)(st.k + ls.k_ofs), (uint32_t)side, (uint32_t)row) < pr)) s = T(-1);
-      }
     }
     key[t] = s;
     id[t] = ii;
@@ -862,7 +883,7 @@ static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 template <typename T>
 cudaError_t launch_cross(const TallGeom& g, const SolveState* st, const CrossArgs<T>& a, cudaStream_t s) {
-  dim3 grid(cdiv(g.n, XR), cdiv(g.M, XC), g.nslots * 2);
+  dim3 grid(cdiv(g.n, NT), 1, g.nslots * 2);
   k_cross<T><<<grid, NT, 0, s>>>(g, st, a);
   return cudaGetLastError();
 }
