@@ -1,14 +1,24 @@
-"""Lane-count autotuning of batched solves (lrp_group).
+"""Autotuning of batched solves: lane count and loop placement (lrp_group).
 
 A batch solved as `lanes` concurrent sub-batches returns exactly the results of
-one plan (same per-problem kernels and arithmetic), so the lane count is a pure
-performance knob: more lanes let one lane's latency-bound per-problem kernels
-overlap another lane's tall products, at the cost of smaller launches.  The
-autotuner times each candidate lane count on the caller's own inputs (one
-untimed warm-up that also captures the iteration graphs, then timed runs with
+one plan (same per-problem kernels and arithmetic), and a plan whose iteration
+loops run on the device (`loop_on_device`, conditional graph nodes) returns
+exactly the results of the host-driven loop.  Both are therefore pure
+performance knobs: more lanes let one lane's latency-bound per-problem kernels
+overlap another lane's tall products, at the cost of smaller launches; device
+loops remove the host's read between iterations but launch every iteration over
+the whole batch (finished problems exit at once instead of being compacted
+away).  The autotuner times each candidate configuration on the caller's own
+inputs (one untimed warm-up that also captures the graphs, then timed runs with
 CUDA events on the caller's stream) and keeps the fastest in a JSON table keyed
 by precision, n, right-hand-side rank class and batch size.  Only the timing
 runs touch the GPU; the selection and the table are host logic.
+
+    python -m paper_2607_06021_gb300.tune --write TABLE.json
+
+tunes the bench workload (n = 4095, rank-20 right-hand sides, tol 1e-8, rank
+cap 64, index capacity 64; both precisions, batches of 256 and 1024) on the
+current GPU and writes the table.
 """
 from __future__ import annotations
 
@@ -18,7 +28,10 @@ import statistics
 from typing import Callable, Dict, Iterable, List, Optional, Tuple
 
 DEFAULT_LANES = (1, 2, 4, 8)
+# (lanes, loop on the device)
+DEFAULT_CONFIGS = ((1, False), (2, False), (4, False), (8, False), (1, True), (2, True), (4, True))
 TIE = 0.01  # candidates within 1% of the fastest count as ties
+TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
 def rank_class(r_f: int) -> int:
@@ -33,20 +46,31 @@ def table_key(precision: str, n: int, r_f: int, batch: int) -> str:
     return f"{precision}/n{int(n)}/rf{rank_class(r_f)}/b{int(batch)}"
 
 
+def config_name(cfg) -> str:
+    """'4' for 4 lanes with host loops, '4d' with device loops (a bare int is host loops)."""
+    lanes, dev = (cfg, False) if isinstance(cfg, int) else cfg
+    return f"{int(lanes)}{'d' if dev else ''}"
+
+
 def candidate_lanes(batch: int, candidates: Iterable[int] = DEFAULT_LANES) -> List[int]:
     """Lane counts worth timing: every lane gets at least one problem."""
     return sorted({int(c) for c in candidates if 1 <= int(c) <= int(batch)})
 
 
-def choose(times: Dict[int, List[float]]) -> int:
-    """The lane count with the smallest median time; candidates within TIE of
-    it count as ties, which go to the fewest lanes (less memory, fewer
-    streams)."""
-    med = {lanes: statistics.median(ts) for lanes, ts in times.items() if ts}
+def candidate_configs(batch: int, candidates=DEFAULT_CONFIGS) -> List[Tuple[int, bool]]:
+    """(lanes, device loop) configurations worth timing: every lane gets a problem."""
+    return sorted({(int(l), bool(d)) for l, d in candidates if 1 <= int(l) <= int(batch)})
+
+
+def choose(times: Dict) -> object:
+    """The configuration with the smallest median time; candidates within TIE
+    of it count as ties, which go to the smallest configuration (fewest lanes,
+    then host loops: less memory, fewer streams)."""
+    med = {c: statistics.median(ts) for c, ts in times.items() if ts}
     if not med:
         raise ValueError("no timed candidate")
     best = min(med.values())
-    return min(lanes for lanes, m in med.items() if m <= best * (1.0 + TIE))
+    return min(c for c, m in med.items() if m <= best * (1.0 + TIE))
 
 
 def tune_lanes(measure: Callable[[int], List[float]], batch: int,
@@ -57,8 +81,16 @@ def tune_lanes(measure: Callable[[int], List[float]], batch: int,
     return choose(times), times
 
 
+def tune_configs(measure: Callable[[Tuple[int, bool]], List[float]], batch: int, candidates=DEFAULT_CONFIGS):
+    """measure((lanes, device_loop)) -> timed runs (ms); returns the chosen
+    configuration and every candidate's times."""
+    times = {cfg: list(measure(cfg)) for cfg in candidate_configs(batch, candidates)}
+    return choose(times), times
+
+
 class TuneTable:
-    """Chosen lane counts, persisted as JSON ({key: {"lanes": L, "ms": {L: median}}})."""
+    """Chosen configurations, persisted as JSON
+    ({key: {"lanes": L, "loop_on_device": bool, "ms": {name: median}}})."""
 
     def __init__(self, path: Optional[str] = None):
         self.path = path
@@ -67,14 +99,22 @@ class TuneTable:
             with open(path) as f:
                 self.entries = json.load(f)
 
-    def get(self, precision: str, n: int, r_f: int, batch: int) -> Optional[int]:
+    def get_config(self, precision: str, n: int, r_f: int, batch: int) -> Optional[Tuple[int, bool]]:
         e = self.entries.get(table_key(precision, n, r_f, batch))
-        return int(e["lanes"]) if e else None
+        return (int(e["lanes"]), bool(e.get("loop_on_device", False))) if e else None
 
-    def put(self, precision: str, n: int, r_f: int, batch: int, lanes: int,
-            times: Dict[int, List[float]]) -> None:
-        self.entries[table_key(precision, n, r_f, batch)] = {
-            "lanes": int(lanes), "ms": {str(k): statistics.median(v) for k, v in times.items() if v}}
+    def get(self, precision: str, n: int, r_f: int, batch: int) -> Optional[int]:
+        c = self.get_config(precision, n, r_f, batch)
+        return c[0] if c else None
+
+    def put(self, precision: str, n: int, r_f: int, batch: int, cfg, times: Dict, extra: Optional[dict] = None):
+        lanes, dev = (cfg, False) if isinstance(cfg, int) else cfg
+        e = {"lanes": int(lanes), "ms": {config_name(k): statistics.median(v) for k, v in times.items() if v}}
+        if dev or not isinstance(cfg, int):
+            e["loop_on_device"] = bool(dev)
+        if extra:
+            e.update(extra)
+        self.entries[table_key(precision, n, r_f, batch)] = e
 
     def save(self) -> None:
         if not self.path:
@@ -86,26 +126,30 @@ class TuneTable:
 
 
 def autotune_group(n: int, tol: float, max_rank: int, inputs, precision: str = "mixed",
-                   candidates: Iterable[int] = DEFAULT_LANES, reps: int = 3,
-                   table: Optional[TuneTable] = None, stream=None, **group_kw):
-    """Lane count for solving `inputs` (a list of (U_f, s_f, V_f) device
-    tensors, one problem each) with lrp_group.  A table hit returns at once;
-    otherwise each candidate gets its own group (created, warmed up, timed
+                   candidates=DEFAULT_CONFIGS, reps: int = 3,
+                   table: Optional[TuneTable] = None, stream=None, extra: Optional[dict] = None, **group_kw):
+    """(lanes, device_loop) for solving `inputs` (a list of (U_f, s_f, V_f)
+    device tensors, one problem each) with lrp_group.  A table hit returns at
+    once; otherwise each candidate gets its own group (created, warmed up, timed
     `reps` times, closed before the next, so that only one workspace is held)
-    and the choice is recorded in the table.  Returns (lanes, {lanes: [ms]})."""
+    and the choice is recorded in the table.  Candidates are (lanes, device
+    loop) pairs or bare lane counts (host loops).  Returns (config, {config: [ms]})."""
     import torch
 
     from .api import Group
     batch = len(inputs)
     r_f = max(int(U.shape[1]) for U, _, _ in inputs)
     if table is not None:
-        hit = table.get(precision, n, r_f, batch)
+        hit = table.get_config(precision, n, r_f, batch)
         if hit is not None:
             return hit, {}
     s = torch.cuda.current_stream() if stream is None else stream
+    cands = [(c, False) if isinstance(c, int) else tuple(c) for c in candidates]
 
-    def measure(lanes: int) -> List[float]:
-        g = Group(n, tol, max_rank, lanes=lanes, precision=precision, batch=batch, max_rhs_rank=r_f, **group_kw)
+    def measure(cfg) -> List[float]:
+        lanes, dev = cfg
+        g = Group(n, tol, max_rank, lanes=lanes, precision=precision, batch=batch, max_rhs_rank=r_f,
+                  loop_on_device=dev, **group_kw)
         try:
             outs = [g.alloc_outputs() for _ in inputs]
             g.solve_batch_into(inputs, outs, s)  # warm-up: workspace touched, graphs captured
@@ -122,8 +166,46 @@ def autotune_group(n: int, tol: float, max_rank: int, inputs, precision: str = "
         finally:
             g.close()
 
-    lanes, times = tune_lanes(measure, batch, candidates)
+    cfg, times = tune_configs(measure, batch, cands)
     if table is not None:
-        table.put(precision, n, r_f, batch, lanes, times)
+        table.put(precision, n, r_f, batch, cfg, times, extra)
         table.save()
-    return lanes, times
+    return cfg, times
+
+
+def _main():
+    import argparse
+    import sys
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--write", default=TABLE_PATH)
+    ap.add_argument("--batches", default="256,1024")
+    a = ap.parse_args()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import lrp_inputs as li
+
+    def dev(x):
+        import numpy as np
+        x = np.asarray(x, dtype=np.float64)
+        return torch.from_numpy(x.copy()).cuda() if x.ndim == 1 else torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+
+    table = TuneTable(a.write)
+    gpu = torch.cuda.get_device_name(0)
+    for B in [int(b) for b in a.batches.split(",")]:
+        rhss = [li.workload_n4095(seed=s) for s in range(B)]
+        inputs = [(dev(r.U), dev(r.s), dev(r.V)) for r in rhss]
+        for prec in ("mixed", "fp64"):
+            t0 = time.time()
+            cfg, times = autotune_group(4095, 1e-8, 64, inputs, precision=prec, table=None, m_cap=64,
+                                        max_iter=30)
+            table.put(prec, 4095, 20, B, cfg, times, {"gpu": gpu, "tuned_s": round(time.time() - t0, 1)})
+            table.save()
+            print(prec, B, config_name(cfg), {config_name(k): round(statistics.median(v), 2) for k, v in times.items()},
+                  flush=True)
+
+
+if __name__ == "__main__":
+    _main()

@@ -57,3 +57,33 @@ def test_table_round_trip(tmp_path):
     assert t2.get("fp64", 4095, 20, 1024) is None
     t2.put("mixed", 4095, 20, 1024, 2, {2: [150.0]})
     assert t2.get("mixed", 4095, 20, 1024) == 2
+
+
+def test_configs_with_loop_placement():
+    # (lanes, device loop): every candidate timed once; ties go to the smallest
+    # configuration (fewest lanes, then host loops)
+    cost = {(1, False): 300.0, (2, False): 220.0, (4, False): 200.0, (8, False): 230.0,
+            (1, True): 260.0, (2, True): 199.5, (4, True): 210.0}
+    seen = []
+
+    def measure(cfg):
+        seen.append(cfg)
+        return [cost[cfg]]
+
+    cfg, times = tune.tune_configs(measure, 1024)
+    assert cfg == (2, True) and sorted(seen) == sorted(cost)
+    assert tune.choose({(4, False): [100.0], (4, True): [100.5]}) == (4, False)
+    assert tune.candidate_configs(3) == [(1, False), (1, True), (2, False), (2, True)]
+    assert tune.config_name((4, True)) == "4d" and tune.config_name(2) == "2"
+
+
+def test_table_round_trip_with_loop_placement(tmp_path):
+    path = str(tmp_path / "cfg.json")
+    t = tune.TuneTable(path)
+    t.put("mixed", 4095, 20, 256, (2, True), {(2, True): [150.0], (4, False): [160.0]}, {"gpu": "x"})
+    t.save()
+    data = json.load(open(path))
+    assert data["mixed/n4095/rf32/b256"] == {"lanes": 2, "loop_on_device": True, "ms": {"2d": 150.0, "4": 160.0},
+                                             "gpu": "x"}
+    t2 = tune.TuneTable(path)
+    assert t2.get_config("mixed", 4095, 20, 256) == (2, True) and t2.get("mixed", 4095, 20, 256) == 2
