@@ -40,7 +40,8 @@ typedef enum lrp_status {
   LRP_ENOMEM = 2,          /* device or host allocation failed */
   LRP_ECUDA = 3,           /* a CUDA runtime call failed (see lrp_last_error) */
   LRP_ETIMEDOUT = 4,       /* a bounded wait gave up (server drain, device flag) */
-  LRP_NOT_CONVERGED = 5,   /* max_iter reached; a valid result was still written */
+  LRP_NOT_CONVERGED = 5,   /* the stop test was not met (max_iter reached, or a mixed-precision
+                              correction solve stalled first); a valid result was still written */
   LRP_RANK_CAPPED = 6,     /* tolerance needs rank > max_rank; result truncated */
   LRP_EAGAIN = 7,          /* lrp_poll: not finished yet; lrp_submit: server full, retry */
   LRP_ECAPACITY = 8        /* server admission: request larger than the memory cap */
@@ -53,11 +54,12 @@ typedef enum lrp_precision {
 } lrp_precision;
 
 typedef enum lrp_selector {
-  LRP_SEL_LEVERAGE = 0,  /* Algorithm LeverageScores, deterministic top-c (Sec. 2.2.2) */
+  LRP_SEL_LEVERAGE = 0,  /* leverage scores, deterministic top-c: the c = columns rows of largest
+                            score (Sec. 2.2.2 with the sampling replaced by a selection) */
   LRP_SEL_QDEIM = 1,     /* Algorithm (Q)DEIM: pivoted QR of U^T (Sec. 2.2.1) */
-  LRP_SEL_BERNOULLI = 2  /* Algorithm LeverageScores as printed (Sec. 2.2.2): row i sampled with
-                            probability min(1, c pi_i), c = sample_factor x columns; draws from
-                            Philox4x32-10 keyed by seed, counter (row, iteration, side, 0) */
+  LRP_SEL_BERNOULLI = 2  /* the default: Algorithm LeverageScores as printed (Sec. 2.2.2): row i
+                            sampled with probability min(1, c pi_i), c = sample_factor x columns;
+                            draws from Philox4x32-10 keyed by seed, counter (row, iteration, side, 0) */
 } lrp_selector;
 
 /* The matrix Cross-DEIM approximates.  LRP_MAT_POISSON: the transformed solution
@@ -75,10 +77,10 @@ typedef enum lrp_matrix {
 /* Solver options.  lrp_default_opts fills the defaults noted here. */
 typedef struct lrp_opts {
   int32_t precision;     /* lrp_precision, default LRP_FP64 */
-  int32_t selector;      /* lrp_selector, default LRP_SEL_LEVERAGE */
+  int32_t selector;      /* lrp_selector, default LRP_SEL_BERNOULLI */
   int32_t max_iter;      /* Cross-DEIM iterations, default 30 */
-  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps: 0 (the FP32 result), 1 (default),
-                            or 2: a second step for the problems whose first correction looks
+  int32_t refine_steps;  /* LRP_MIXED only: residual-correction steps: 0 (the FP32 result), 1, or 2
+                            (default): a second step for the problems whose first step looks
                             unreliable (LRP_FLAG_REFINED_TWICE; the others are unchanged) */
   int32_t max_rhs_rank;  /* capacity for r_f, default 64 (<= 256) */
   int32_t batch;         /* max problems per lrp_solve_batch call, default 1 */
@@ -90,12 +92,19 @@ typedef struct lrp_opts {
   double sample_factor;  /* LRP_SEL_BERNOULLI: c / columns, the expected sample size over the
                             basis width (> 0), default 1 */
   int32_t matrix;        /* lrp_matrix, default LRP_MAT_POISSON */
-  int32_t reserved0;     /* 0 */
+  int32_t loop_on_device; /* 0 (default): the host reads the count of still-iterating problems after
+                            every Cross-DEIM iteration and launches the next one over the active ones;
+                            1: the whole solve is one captured CUDA graph whose iteration loops are
+                            conditional while-nodes, continued by the device while any problem is
+                            active (bounded by max_iter), so a solve is one graph launch and the call
+                            returns without waiting for it (the mixed path's second refinement step
+                            is a conditional if-node of the same graph). */
 } lrp_opts;
 
 /* Per-problem report, written by the device into caller memory. */
 /* lrp_info.flags */
-#define LRP_FLAG_CONVERGED 1   /* the stop test passed (mixed: in every solve, or a stall below) */
+#define LRP_FLAG_CONVERGED 1   /* the stop test passed (mixed: the FP32 trial passed it or stalled at its
+                                  noise floor, and every correction solve passed it) */
 #define LRP_FLAG_RANK_CAPPED 2 /* r* > max_rank */
 #define LRP_FLAG_CAPACITY 4    /* an index set reached m_cap */
 #define LRP_FLAG_BAD_INPUT 8   /* non-finite data met */
@@ -366,25 +375,70 @@ lrp_status lrp_group_pack(lrp_group_t group, double* d_packed, int64_t capacity,
 /* Stop the workers and free the lanes' plans. */
 lrp_status lrp_group_destroy(lrp_group_t group);
 
+/* ------------------------------------------------------------------ mixed sizes, one launch
+ *
+ * A multi-size set: one plan per grid size (each with loop_on_device), solved
+ * together as ONE CUDA graph launch.  lrp_multi_solve sorts a call's problems
+ * into their size's plan and runs every size's whole solve (forward DST,
+ * Cross-DEIM, refinement, back DST) as one concurrent branch of the graph; each
+ * branch continues its iteration loops on the device while any of its problems
+ * is active, so the host neither waits nor launches between iterations.  The
+ * graph is captured on first use for each vector of per-size problem counts
+ * (and warm-record / trace use) and replayed afterwards.  Results are those of
+ * each size's plan alone (the branches share no workspace).
+ */
+typedef struct lrp_multi_s* lrp_multi_t;
+
+/*
+ * Create a set for nsizes distinct grid sizes ns[i] (n+1 powers of two), with
+ * room for batches[i] problems of size ns[i] per call; tol, max_rank and opts
+ * (NULL = defaults; opts->batch and opts->loop_on_device are ignored) are shared.
+ * Errors: as lrp_plan, plus LRP_EINVAL for a repeated size or nsizes outside 1..64.
+ */
+lrp_status lrp_multi_create(lrp_multi_t* out, int32_t nsizes, const int64_t* ns, const int32_t* batches,
+                            double tol, int32_t max_rank, const lrp_opts* opts);
+
+/*
+ * Solve `count` problems in one graph launch on `stream`: problem i has grid
+ * size ns[i] (HOST array) and descriptor problems[i] (HOST array, device
+ * factors as in lrp_solve_batch); at most batches[b] problems per size.  The
+ * call returns once the launch is enqueued; results are complete when `stream`
+ * reaches it.  Errors: LRP_EINVAL (a size not in the set, too many problems of
+ * one size, a bad descriptor), LRP_ECUDA.
+ */
+lrp_status lrp_multi_solve(lrp_multi_t m, int32_t count, const int64_t* ns, const lrp_problem* problems,
+                           void* stream);
+
+/* The plan of size index b (statistics, traces, packing; owned by the set). */
+lrp_status lrp_multi_plan(lrp_multi_t m, int32_t size_index, lrp_plan_t* out);
+
+/* Free the set and its plans (synchronises the device first). */
+lrp_status lrp_multi_destroy(lrp_multi_t m);
+
 /* ------------------------------------------------------------------ serving
  *
  * A request server over the batched solver for streams of independent
  * problems of varying n, precision and tolerance (one GPU, one process).
  * Admission: each request's working set is estimated as
- * 8 n (2 r_f + 4 m_cap + 2 max_rank) bytes (m_cap = min(2 max_rank + r_f', 256),
- * r_f' = r_f rounded up to a multiple of 64); a request is refused with
- * LRP_ECAPACITY when it alone exceeds the memory cap, and with LRP_EAGAIN when
- * the queued and running requests' estimates plus its own would exceed the cap
- * or the queue is full (retry later).  Scheduling: worker lanes (one host thread
- * and one CUDA stream each) take the oldest waiting request whose bucket
- * (n, precision, tol, max_rank, r_f') has no batch running and solve it with up
- * to a plan's batch of waiting requests of that bucket, in arrival order
- * (continuous batching: later arrivals join the next batch).  One plan per
- * bucket is created on first use with as many batch slots as fit a quarter of
- * the cap, and idle plans are destroyed least recently used when a new plan or
- * warm-start record would not fit.  Warm start: requests that name the same
- * nonzero warm_key share a warm-start record of their bucket's plan (created
- * by the first, reused by later ones; at most warm_capacity records per plan,
+ * 8 n (2 r_f + 4 m_cap + 2 max_rank) bytes, with r_f' = r_f rounded up to a
+ * multiple of 16 and m_cap the index-set capacity of its bucket's plan:
+ * min(2 max_rank + r_f', 256) in FP64; in mixed precision 64 while r_f' + 16 <=
+ * 64 (else r_f' + 16), which keeps the refinement in double-float arithmetic; a
+ * request is refused with LRP_ECAPACITY when it alone exceeds the memory cap,
+ * and with LRP_EAGAIN when the queued and running requests' estimates plus its
+ * own would exceed the cap or the queue is full (retry later).  Scheduling:
+ * worker lanes (one host thread and one CUDA stream each) take the oldest
+ * waiting request that can start and solve it with up to a plan's batch of
+ * waiting requests of its bucket (n, precision, tol, max_rank, r_f'), in
+ * arrival order, as one graph launch (the plans run their iteration loops on
+ * the device).  A bucket holds up to one plan per lane, so a request that
+ * arrives while a batch of its bucket runs starts on another lane (continuous
+ * batching: later arrivals join the next batch).  Plans are created on first
+ * use with as many batch slots as fit a quarter of the cap, and idle plans are
+ * destroyed least recently used when a new plan or warm-start record would not
+ * fit.  Warm start: requests that name the same nonzero warm_key share a
+ * warm-start record of a plan of their bucket (created by the first, reused by
+ * later ones that run on that plan; at most warm_capacity records per plan,
  * least recently used dropped); a batch holds at most one request per key.
  */
 typedef struct lrp_server_s* lrp_server_t;
@@ -433,7 +487,8 @@ typedef struct lrp_server_stats {
 /* Fill *opts with the defaults.  Returns LRP_EINVAL for NULL. */
 lrp_status lrp_server_default_opts(lrp_server_opts* opts);
 
-/* The admission estimate above in bytes (0 for out-of-range arguments). */
+/* The admission estimate above in bytes for an FP64 request (an upper bound for mixed
+   precision); 0 for out-of-range arguments. */
 size_t lrp_request_footprint(int64_t n, int32_t r_f, int32_t max_rank);
 
 /*

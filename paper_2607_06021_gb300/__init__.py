@@ -35,7 +35,7 @@ class lrp_opts(ctypes.Structure):
                 ("max_rhs_rank", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("m_cap", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sample_factor", ctypes.c_double),
-                ("matrix", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("matrix", ctypes.c_int32), ("loop_on_device", ctypes.c_int32)]
 
 
 class lrp_info(ctypes.Structure):
@@ -116,6 +116,11 @@ def _load():
         "lrp_group_plan": ([P, I32, ctypes.POINTER(P)], I32),
         "lrp_group_pack": ([P, VP, I64, VP, VP], I32),
         "lrp_group_destroy": ([P], I32),
+        "lrp_multi_create": ([ctypes.POINTER(P), I32, ctypes.POINTER(I64), ctypes.POINTER(I32), D, I32,
+                              ctypes.POINTER(lrp_opts)], I32),
+        "lrp_multi_solve": ([P, I32, ctypes.POINTER(I64), ctypes.POINTER(lrp_problem), VP], I32),
+        "lrp_multi_plan": ([P, I32, ctypes.POINTER(P)], I32),
+        "lrp_multi_destroy": ([P], I32),
         "lrp_plan_estimate_bytes": ([I64, D, I32, ctypes.POINTER(lrp_opts), ctypes.POINTER(ctypes.c_size_t)], I32),
         "lrp_server_default_opts": ([ctypes.POINTER(lrp_server_opts)], I32),
         "lrp_request_footprint": ([I64, I32, I32], ctypes.c_size_t),
@@ -195,6 +200,31 @@ def lrp_group_pack(group, d_packed, capacity: int, d_offsets, stream) -> None:
 
 def lrp_group_destroy(group) -> None:
     _check(_lib.lrp_group_destroy(group), "lrp_group_destroy")
+
+
+def lrp_multi_create(ns, batches, tol: float, max_rank: int, opts: lrp_opts):
+    h = ctypes.c_void_p()
+    a = (ctypes.c_int64 * len(ns))(*[int(v) for v in ns])
+    b = (ctypes.c_int32 * len(batches))(*[int(v) for v in batches])
+    _check(_lib.lrp_multi_create(ctypes.byref(h), len(ns), a, b, float(tol), int(max_rank), ctypes.byref(opts)),
+           "lrp_multi_create")
+    return h
+
+
+def lrp_multi_solve(multi, ns, problems, stream) -> int:
+    a = (ctypes.c_int64 * len(ns))(*[int(v) for v in ns])
+    arr = (lrp_problem * len(problems))(*problems)
+    return _check(_lib.lrp_multi_solve(multi, len(problems), a, arr, stream), "lrp_multi_solve")
+
+
+def lrp_multi_plan(multi, index: int):
+    h = ctypes.c_void_p()
+    _check(_lib.lrp_multi_plan(multi, int(index), ctypes.byref(h)), "lrp_multi_plan")
+    return h
+
+
+def lrp_multi_destroy(multi) -> None:
+    _check(_lib.lrp_multi_destroy(multi), "lrp_multi_destroy")
 
 
 def lrp_plan_pack(plan, d_packed, capacity: int, d_offsets, stream) -> None:
@@ -356,4 +386,4 @@ def lrp_plan_reset_stats(plan) -> None:
     _check(_lib.lrp_plan_reset_stats(plan), "lrp_plan_reset_stats")
 
 
-from .api import Group, Plan, Server, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401
+from .api import Group, Multi, Plan, Server, WarmRecord, dst1, colmajor, parse_info, solve  # noqa: E402,F401

@@ -15,7 +15,8 @@ from . import (INFO_BYTES, KERNEL_CLASSES, LRP_FP64, LRP_MIXED, LRP_NOT_CONVERGE
                lrp_plan_workspace_bytes, lrp_problem, lrp_solve_batch, lrp_warm_create,
                lrp_warm_destroy, lrp_warm_reset, lrp_poll, lrp_request, lrp_server_create,
                lrp_server_default_opts, lrp_server_destroy, lrp_server_get_stats, lrp_server_reset_stats,
-               lrp_server_last_error, lrp_submit, lrp_wait)
+               lrp_server_last_error, lrp_submit, lrp_wait, lrp_multi_create, lrp_multi_solve, lrp_multi_plan,
+               lrp_multi_destroy)
 
 
 def colmajor(x: torch.Tensor) -> torch.Tensor:
@@ -47,8 +48,8 @@ class Plan:
 
     def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
-                 check_every: int = 1, refine_steps: int = 1, selector: str = "ls", sample_factor: float = 1.0,
-                 matrix: str = "poisson"):
+                 check_every: int = 1, refine_steps: int = 2, selector: str = "bernoulli", sample_factor: float = 1.0,
+                 matrix: str = "poisson", loop_on_device: bool = False):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch = batch
@@ -61,6 +62,7 @@ class Plan:
         o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
         o.sample_factor = sample_factor
         o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
+        o.loop_on_device = 1 if loop_on_device else 0
         self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
         self.handle = lrp_plan(n, tol, max_rank, o)
 
@@ -192,7 +194,7 @@ def dst1(X: torch.Tensor, stream=None) -> torch.Tensor:
     return Y
 
 
-__all__ = ["Group", "Plan", "Server", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
+__all__ = ["Group", "Multi", "Plan", "Server", "WarmRecord", "solve", "dst1", "colmajor", "parse_info", "LRP_OK", "LRP_NOT_CONVERGED", "LRP_RANK_CAPPED"]
 
 
 class Server:
@@ -278,8 +280,9 @@ class Group:
     """lrp_group_*: one batch solved as `lanes` concurrent sub-batches."""
 
     def __init__(self, n: int, tol: float, max_rank: int, lanes: int, precision: str = "fp64", batch: int = 1,
-                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "ls",
-                 sample_factor: float = 1.0, matrix: str = "poisson", refine_steps: int = 1):
+                 max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "bernoulli",
+                 sample_factor: float = 1.0, matrix: str = "poisson", refine_steps: int = 2,
+                 loop_on_device: bool = False):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.refine_steps = refine_steps
@@ -287,6 +290,7 @@ class Group:
         o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
         o.sample_factor = sample_factor
         o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
+        o.loop_on_device = 1 if loop_on_device else 0
         self.n, self.tol, self.max_rank, self.batch, self.lanes = n, tol, max_rank, batch, lanes
         self.handle = lrp_group_create(n, tol, max_rank, o, lanes)
         per = (batch + lanes - 1) // lanes
@@ -335,6 +339,68 @@ class Group:
             for p in self.plans:
                 p.close()
             lrp_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """lrp_multi_*: problems of several grid sizes solved as one CUDA graph launch."""
+
+    def __init__(self, ns, batches, tol: float, max_rank: int, precision: str = "mixed", max_rhs_rank: int = 64,
+                 max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "bernoulli", sample_factor: float = 1.0,
+                 refine_steps: int = 2):
+        o = lrp_default_opts()
+        o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
+        o.refine_steps = refine_steps
+        o.max_rhs_rank, o.max_iter, o.m_cap, o.seed = max_rhs_rank, max_iter, m_cap, seed
+        o.selector = {"ls": LRP_SEL_LEVERAGE, "qdeim": LRP_SEL_QDEIM, "bernoulli": LRP_SEL_BERNOULLI}[selector]
+        o.sample_factor = sample_factor
+        self.ns, self.tol, self.max_rank = list(ns), tol, max_rank
+        self.handle = lrp_multi_create(self.ns, batches, tol, max_rank, o)
+        self.plans = [_LanePlan(lrp_multi_plan(self.handle, i), n, tol, max_rank, b)
+                      for i, (n, b) in enumerate(zip(self.ns, batches))]
+
+    def alloc_outputs(self, n: int, device="cuda"):
+        r = self.max_rank
+        U = torch.zeros((r, n), dtype=torch.float64, device=device).t()
+        V = torch.zeros((r, n), dtype=torch.float64, device=device).t()
+        S = torch.zeros(r, dtype=torch.float64, device=device)
+        info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=device)
+        return U, S, V, info
+
+    def solve_batch_into(self, inputs, outputs, stream=None) -> None:
+        """inputs: list of (U_f, s_f, V_f) of any sizes in the set; outputs: alloc_outputs(n) each."""
+        probs = [self.plans[0].problem(*i, o) for i, o in zip(inputs, outputs)]
+        lrp_multi_solve(self.handle, [int(i[0].shape[0]) for i in inputs], probs, _stream(stream))
+
+    def solve_batch(self, inputs, stream=None):
+        outs = [self.alloc_outputs(int(i[0].shape[0])) for i in inputs]
+        self.solve_batch_into(inputs, outs, stream)
+        torch.cuda.synchronize()
+        res = []
+        for U, S, V, info in outs:
+            inf = parse_info(info)
+            r = inf["rank"]
+            res.append((U[:, :r], S[:r], V[:, :r], inf))
+        return res
+
+    def kernel_stats(self) -> dict:
+        tot = None
+        for p in self.plans:
+            st = p.kernel_stats()
+            tot = st if tot is None else {k: tuple(a + b for a, b in zip(tot[k], st[k])) for k in tot}
+        return tot
+
+    def close(self) -> None:
+        if self.handle is not None:
+            for p in self.plans:
+                p.close()
+            lrp_multi_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

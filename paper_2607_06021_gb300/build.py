@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dst.cu", "tall.cu", "core.cu", "refine.cu", "solver.cu", "noalloc.cu", "server.cu", "qdeim.cu", "pack.cu", "dfmat.cu", "group.cu", "matrix.cu"]
+SOURCES = ["dst.cu", "tall.cu", "core.cu", "refine.cu", "solver.cu", "noalloc.cu", "server.cu", "qdeim.cu", "pack.cu", "dfmat.cu", "group.cu", "matrix.cu", "multi.cu"]
 
 
 def nvcc() -> str:

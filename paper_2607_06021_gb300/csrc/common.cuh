@@ -43,7 +43,7 @@ struct SolveState {
   int32_t upar;          // ping-pong parity of the FP32 iterate being stacked
   int32_t rd;            // rank of the correction
   int32_t first_converged;  // the first (FP32) solve met its stop test
-  int32_t c0;            // columns of U_{-1}, V_{-1}: r_f (cold) or the warm iterate's rank
+  int32_t c0[2];         // columns of U_{-1}, V_{-1}: their numerical rank (cold) or the warm iterate's rank
   int32_t warm_ok;       // this solve may load a warm-start record
   double rho;
   double eta_smin;
@@ -54,6 +54,7 @@ struct SolveState {
   double tol_abs;        // > 0: also accept changes below tol_abs in absolute terms (correction solves)
   double rho_best;       // smallest rho of this solve after its first iteration (0: none yet)
   int32_t stall;         // iterations since rho last fell below half of rho_best
+  int32_t is_corr;       // this solve is a refinement correction (mixed precision)
   double rho_jump;       // largest rho / rho_best seen after rho_best was first set
 };
 
@@ -85,7 +86,7 @@ __host__ __device__ inline int dim_of(const SolveState& st, int side, int sel) {
     case kDimR: return st.r;
     case kDimRPrev: return st.r_prev;
     case kDimX: return st.mx[side];
-    case kDimC0: return st.c0;
+    case kDimC0: return st.c0[side];
     default: return st.rf;
   }
 }

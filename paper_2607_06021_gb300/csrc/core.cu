@@ -39,9 +39,12 @@ __device__ inline void acct_add(double* row, int cls, double flops, double bytes
   row[2 * cls + 1] += bytes;
 }
 
+// Algorithmic flops of one orthonormal DST-I column: a real FFT of length N
+// (one complex FFT of length N/2, 2.5 N log2 N), the count of a transform that
+// uses the odd symmetry (the pre- and post-processing add O(N)).
 __device__ inline double dst_col_flops(int n) {
   const double N = (double)(n + 1);
-  return 5.0 * N * log2(N);  // one complex FFT of length N per column
+  return 2.5 * N * log2(N);
 }
 
 // Three symmetric Gram passes, two triangular applies, on side sizes m0, m1.
@@ -828,7 +831,7 @@ __global__ void k_setup(CoreParams p, const ProblemDev* prob, T* w, int wstride,
     st.valid = act ? 1 : 0;
     st.rf = rf;
     st.rf0 = rf;
-    st.c0 = rf;
+    st.c0[0] = st.c0[1] = rf;
     st.warm_ok = (act && prob[slot].warm != nullptr) ? 1 : 0;
     st.tol = p.tol;
     *stp = st;
@@ -857,9 +860,37 @@ __global__ void k_warm_load(CoreParams p, CoreBufs<T> b, Strided<T> U1) {
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) set[t] = w->idx[side * M + t];
     if (threadIdx.x == 0) {
       stp->cnt[side] = cnt;
-      if (side == 0) stp->c0 = r;
+      stp->c0[side] = r;
     }
   }
+}
+
+// Numerical range of the initial bases: after the CholeskyQR of the
+// transformed right-hand side X = Q R, keep the columns l of Q = Q2 P with
+// |R(l,l)| >= redundancy max|diag R| (the threshold of the redundancy removal),
+// moved to the front of P in order, and c0 = their count, so that a
+// numerically dependent factor column adds no noise direction to U_{-1}.
+template <typename T>
+__global__ void k_orth_keep(CoreParams p, CoreBufs<T> b) {
+  const int slot = slot_of(p.g, blockIdx.x >> 1), side = blockIdx.x & 1;
+  if (slot < 0) return;
+  SolveState* stp = p.st + slot;
+  if (!stp->active || threadIdx.x != 0) return;
+  const int M = p.g.M;
+  const int m = stp->rf;
+  const double* R = b.Racc.at(slot, side);
+  double* P = b.P.at(slot, side);
+  double mx = 0.0;
+  for (int l = 0; l < m; ++l) mx = fmax(mx, fabs(R[(int64_t)l * M + l]));
+  int c = 0;
+  for (int l = 0; l < m; ++l) {
+    if (!(mx > 0.0) || fabs(R[(int64_t)l * M + l]) < p.redundancy * mx) continue;
+    if (c != l)
+      for (int i = 0; i < m; ++i) P[(int64_t)c * M + i] = P[(int64_t)l * M + i];
+    ++c;
+  }
+  if (c == 0) c = 1;  // a zero right-hand side keeps one (zero) column
+  stp->c0[side] = c;
 }
 
 template <typename T>
@@ -1017,6 +1048,12 @@ cudaError_t launch_warm_load(const CoreParams& p, const CoreBufs<T>& b, Strided<
 }
 
 template <typename T>
+cudaError_t launch_orth_keep(const CoreParams& p, const CoreBufs<T>& b, cudaStream_t s) {
+  k_orth_keep<T><<<p.g.nslots * 2, 32, 0, s>>>(p, b);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_warm_store(const CoreParams& p, const CoreBufs<T>& b, T* const* ubufs, int64_t side_stride,
                               int64_t slot_stride, cudaStream_t s) {
   k_warm_store<T><<<dim3((p.g.n + 255) / 256, p.g.nslots * 2), 256, 0, s>>>(p, b, ubufs, side_stride, slot_stride);
@@ -1030,6 +1067,46 @@ cudaError_t launch_eigenvalues(int n, double* lam64, float* lam32, cudaStream_t 
 
 cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, int32_t* list, cudaStream_t s) {
   k_count_active<<<1, 256, 0, s>>>(st, nslots, out, list);
+  return cudaGetLastError();
+}
+
+// Device-side loop control of a conditional while-node: k_loop_begin runs
+// before the node (the body runs only if a problem is still active), k_loop_next
+// ends each trip of the body.  The trip bound keeps the loop finite whatever
+// the per-problem state holds.
+__global__ void k_loop_begin(const int32_t* active, int32_t* trips, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *trips = 0;
+    cudaGraphSetConditional(h, *active > 0 ? 1u : 0u);
+  }
+}
+
+__global__ void k_loop_next(const int32_t* active, int32_t* trips, int max_trips, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int t = *trips + 1;
+    *trips = t;
+    cudaGraphSetConditional(h, (*active > 0 && t < max_trips) ? 1u : 0u);
+  }
+}
+
+// Condition of a conditional if-node: a positive device count.
+__global__ void k_cond_positive(const int32_t* count, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, *count > 0 ? 1u : 0u);
+}
+
+cudaError_t launch_cond_positive(const int32_t* count, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_cond_positive<<<1, 32, 0, s>>>(count, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_begin(const int32_t* active, int32_t* trips, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_begin<<<1, 32, 0, s>>>(active, trips, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_next(const int32_t* active, int32_t* trips, int max_trips, cudaGraphConditionalHandle h,
+                             cudaStream_t s) {
+  k_loop_next<<<1, 32, 0, s>>>(active, trips, max_trips, h);
   return cudaGetLastError();
 }
 
@@ -1061,6 +1138,7 @@ cudaError_t launch_stage(const void* src, void* dst, size_t bytes, cudaStream_t 
                                                cudaStream_t);                                                 \
   template cudaError_t launch_setup<T>(const CoreParams&, const ProblemDev*, T*, int, int, double*, cudaStream_t); \
   template cudaError_t launch_warm_load<T>(const CoreParams&, const CoreBufs<T>&, Strided<T>, cudaStream_t);      \
+  template cudaError_t launch_orth_keep<T>(const CoreParams&, const CoreBufs<T>&, cudaStream_t);                   \
   template cudaError_t launch_warm_store<T>(const CoreParams&, const CoreBufs<T>&, T* const*, int64_t, int64_t,    \
                                             cudaStream_t);
 LRP_INST(double)

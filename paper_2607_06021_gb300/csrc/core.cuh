@@ -105,6 +105,8 @@ cudaError_t core_configure();
 template <typename T>
 cudaError_t launch_warm_load(const CoreParams& p, const CoreBufs<T>& b, Strided<T> U1, cudaStream_t s);
 template <typename T>
+cudaError_t launch_orth_keep(const CoreParams& p, const CoreBufs<T>& b, cudaStream_t s);
+template <typename T>
 cudaError_t launch_warm_store(const CoreParams& p, const CoreBufs<T>& b, T* const* ubufs, int64_t side_stride,
                               int64_t slot_stride, cudaStream_t s);
 
@@ -119,5 +121,11 @@ cudaError_t launch_count_active(const SolveState* st, int nslots, int32_t* out, 
 // buffers, so that it never waits on a copy engine that a caller's bulk
 // transfers on other streams hold.
 cudaError_t launch_stage(const void* src, void* dst, size_t bytes, cudaStream_t s);
+// Condition of a conditional if-node: *count > 0.
+cudaError_t launch_cond_positive(const int32_t* count, cudaGraphConditionalHandle h, cudaStream_t s);
+// Loop control of a device-side (conditional while-node) iteration loop.
+cudaError_t launch_loop_begin(const int32_t* active, int32_t* trips, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_loop_next(const int32_t* active, int32_t* trips, int max_trips, cudaGraphConditionalHandle h,
+                             cudaStream_t s);
 
 }  // namespace lrp

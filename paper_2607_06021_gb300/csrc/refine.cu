@@ -102,9 +102,9 @@ __global__ void k_prepare_refine(RefineArgs a) {
     const double m = rf + 2.0 * r0, n = a.n;
     // stacked blocks: read Uh_f (FP64) and Uh0 (FP32), write X and the FP64 stash
     racct(a, slot, LRP_K_REFINE, 2.0 * n * r0, 2.0 * n * (rf * 8.0 + r0 * 4.0 + m * 8.0 + r0 * 8.0));
-    // the FP64 forward transform of the right-hand side (double-float), one FFT of length N per column
+    // the FP64 forward transform of the right-hand side (double-float), a real FFT of length N per column
     const double N = n + 1.0;
-    racct(a, slot, LRP_K_DST_DF, 2.0 * rf * 5.0 * N * log2(N), 2.0 * rf * n * 16.0);
+    racct(a, slot, LRP_K_DST_DF, 2.0 * rf * 2.5 * N * log2(N), 2.0 * rf * n * 16.0);
     if (a.X32lo.base) racct_cholqr(a, slot, 2, m, true, 8.0);
     else racct_cholqr(a, slot, 1, m);
   }
@@ -270,13 +270,18 @@ __global__ void k_setup_correction(RefineArgs a) {
     z.active = 1;
     z.valid = 1;
     z.rf = rR;
-    z.c0 = rR;
+    z.c0[0] = z.c0[1] = rR;
     z.warm_ok = 0;
     z.rf0 = rf0;
     z.r0 = r0;
     z.total_iters = total;
     z.flags = st->flags & ~kFlagConverged;
-    z.first_converged = (st->flags & (kFlagConverged | kFlagStalled)) ? 1 : 0;
+    // The first correction requires the FP32 trial to have finished, by its
+    // stop test or at its noise floor (the correction compensates a stalled
+    // trial).  A second correction corrects whatever the first step left, so
+    // its own stop test alone decides.
+    z.first_converged = (st->is_corr || (st->flags & (kFlagConverged | kFlagStalled))) ? 1 : 0;
+    z.is_corr = 1;
     z.tol = a.corr_tol;
     z.tol_abs = a.final_tol * sqrt(s0n);
     *st = z;
@@ -371,7 +376,10 @@ __global__ void k_final_state(RefineArgs a) {
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
   if (!st->valid || threadIdx.x != 0) return;
-  const bool conv = st->first_converged && (st->flags & (kFlagConverged | kFlagStalled));
+  // The last correction must pass its own stop test: one that stalled (its
+  // change stopped halving above the tolerance it was given) leaves an error
+  // the method cannot bound, and the result is reported as not converged.
+  const bool conv = st->first_converged && (st->flags & kFlagConverged);
   st->k = 1;
   st->iters = st->total_iters;
   st->flags = conv ? (st->flags | kFlagConverged) : (st->flags & ~kFlagConverged);
@@ -385,7 +393,8 @@ __global__ void k_final_state(RefineArgs a) {
 //       10 tol: ||dS|| / ||S0|| max(rho_c, 1e-5) > 10 tol, or
 //   (b) the correction solve jumped (its change rose more than tenfold above
 //       its best value, itself below 1e-2) and may have settled on a poor
-//       index set.
+//       index set, or
+//   (c) (see below) a rollback or an unfinished correction.
 // The others are held: valid = 0 until k_release_held, so that no kernel of
 // the second step touches them.
 __global__ void k_check_refine(RefineArgs a, int nslots, int32_t* count) {
@@ -398,7 +407,11 @@ __global__ void k_check_refine(RefineArgs a, int nslots, int32_t* count) {
   s0n = sqrt(s0n);
   const double est = s0n > 0.0 ? st->snorm / s0n * fmax(st->rho, 1e-5) : 0.0;
   const bool jumped = st->rho_jump > 10.0 && st->rho_best > 0.0 && st->rho_best < 1e-2;
-  if (est > 10.0 * a.final_tol || jumped) {
+  // (c) a solve of the first step rolled back an FP32 update that grew its
+  //     change, or the correction ended without passing its stop test: its
+  //     iterate may sit on a poor index set whatever its last change says.
+  const bool unclean = (st->flags & kFlagRolledBack) || !(st->flags & kFlagConverged);
+  if (est > 10.0 * a.final_tol || jumped || unclean) {
     st->flags |= kFlagRefinedTwice;
     atomicAdd(count, 1);
   } else {

@@ -297,6 +297,9 @@ void DeviceArena::release() {
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Bytes of one region of a plan's pinned forward-DST staging (see forward_stage_host).
+static size_t forward_stage_bytes(const PlanDims& d) { return (sizeof(void*) * 2 + sizeof(int64_t) * 2) * 2 * d.B; }
+
 // Kernel attributes (dynamic shared-memory limits) are set once per device,
 // never during a stream capture.
 static lrp_status ensure_configured(int device) {
@@ -316,12 +319,12 @@ static lrp_status ensure_configured(int device) {
 extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   if (!o) return set_error(LRP_EINVAL, "opts is NULL");
   o->precision = LRP_FP64;
-  o->selector = LRP_SEL_LEVERAGE;
+  o->selector = LRP_SEL_BERNOULLI;
   o->sample_factor = 1.0;
   o->matrix = LRP_MAT_POISSON;
-  o->reserved0 = 0;
+  o->loop_on_device = 0;
   o->max_iter = 30;
-  o->refine_steps = 1;
+  o->refine_steps = 2;
   o->max_rhs_rank = 64;
   o->batch = 1;
   o->m_cap = 0;
@@ -353,6 +356,7 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
     return set_error(LRP_EINVAL, "the test matrices are solved in FP64 only");
   if (o.matrix == LRP_MAT_K && n < 2) return set_error(LRP_EINVAL, "the K matrix needs n >= 2");
   if (o.check_every < 1) o.check_every = 1;
+  if (o.loop_on_device != 0 && o.loop_on_device != 1) return set_error(LRP_EINVAL, "loop_on_device must be 0 or 1");
   const bool fp64 = (o.precision == LRP_FP64);
   if (poisson && !dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
   if (!fp64 && (o.refine_steps < 0 || o.refine_steps > 2))
@@ -364,6 +368,7 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   p->mixed_residual_tol = 1e-7;
   p->r_max = max_rank;
   p->opts = o;
+  p->device_loop = o.loop_on_device != 0;
   PlanDims& d = p->dims;
   d.n = (int)n;
   d.ld = (n + 31) / 32 * 32;
@@ -418,6 +423,7 @@ static lrp_status plan_layout(lrp_plan_s* p) {
     if (p->dst_temp_bytes) p->dst_temp = p->arena.get<unsigned char>(p->dst_temp_bytes);
   }
   p->s0 = p->arena.get<double>((size_t)d.B * d.M);
+  p->loop_trips = p->arena.get<int32_t>(4);
   if (!p->arena.ok()) s = set_error(LRP_ENOMEM, "plan allocation failed");
   if (s == LRP_OK) s = p->w64.allocate(d, p->arena, d.RF);
   // the FP32 workspace also holds the recompressed residual (up to m_cap columns)
@@ -474,12 +480,15 @@ extern "C" lrp_status lrp_plan(lrp_plan_t* out, int64_t n, double tol, int32_t m
   if (s == LRP_OK) {
     cudaError_t e = launch_eigenvalues(d.n, p->lam64, p->lam32, st0);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->prob_host, sizeof(ProblemDev) * d.B);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_ptrs, (sizeof(void*) * 2 + sizeof(int64_t) * 2) * 2 * d.B);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_ptrs, forward_stage_bytes(d) * 2);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->active_host, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->prob_host_dev, p->prob_host, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&p->host_ptrs_dev, p->host_ptrs, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->active_host_dev, p->active_host, 0);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && p->device_loop) e = cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && p->device_loop) e = cudaStreamCreateWithFlags(&p->if_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && p->device_loop) e = cudaEventCreateWithFlags(&p->solve_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) s = set_error(LRP_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
   }
@@ -551,6 +560,10 @@ static void plan_free(lrp_plan_s* p) {
   p->w64.release_graphs();
   p->w32.release_graphs();
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->solve_exec) cudaGraphExecDestroy(p->solve_exec);
+  if (p->body_stream) cudaStreamDestroy(p->body_stream);
+  if (p->if_stream) cudaStreamDestroy(p->if_stream);
+  if (p->solve_done) cudaEventDestroy(p->solve_done);
   delete p;
 }
 
@@ -686,19 +699,19 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   return cp;
 }
 
-// Forward DST of the caller's factors into w.Fh (type T); with do_setup the
-// per-slot state and the h^2-scaled weights are initialised too.
+// Pinned staging of one forward DST job: input/output pointers and leading
+// dimensions of both factors of every slot.  Region 0 serves the iteration
+// precision's transform, region 1 the mixed path's FP64 transform, so that a
+// captured solve reads both from distinct host memory.
+
 template <typename T>
-static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, bool do_setup, bool df,
-                                cudaStream_t s) {
+static void forward_stage_host(lrp_plan_s* p, Workspace<T>& w, int count, int region) {
   const PlanDims& d = p->dims;
   const int64_t fm = d.ld * w.rf_cap;
-  const double** hin = (const double**)p->host_ptrs;
+  const double** hin = (const double**)((char*)p->host_ptrs + region * forward_stage_bytes(d));
   T** hout = (T**)(hin + 2 * d.B);
   int64_t* hldi = (int64_t*)(hout + 2 * d.B);
   int64_t* hldo = hldi + 2 * d.B;
-  // The pinned staging is shared by both precisions: wait for earlier copies from it.
-  LRP_CUDA(cudaStreamSynchronize(s));
   for (int mat = 0; mat < 2; ++mat)
     for (int sl = 0; sl < count; ++sl) {
       const ProblemDev& pr = p->prob_host[sl];
@@ -707,6 +720,23 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
       hout[mat * count + sl] = w.Fh + (int64_t)sl * 2 * fm + (int64_t)mat * fm;
       hldo[mat * count + sl] = d.ld;
     }
+}
+
+// Forward DST of the caller's factors into w.Fh (type T); with do_setup the
+// per-slot state and the h^2-scaled weights are initialised too.
+template <typename T>
+static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams& cp, int count, bool do_setup, bool df,
+                                cudaStream_t s, int region) {
+  const PlanDims& d = p->dims;
+  const double** hin = (const double**)((char*)p->host_ptrs + region * forward_stage_bytes(d));
+  T** hout = (T**)(hin + 2 * d.B);
+  int64_t* hldi = (int64_t*)(hout + 2 * d.B);
+  int64_t* hldo = hldi + 2 * d.B;
+  if (!p->capturing_solve) {
+    // The pinned staging is reused by the next solve: wait for earlier copies from it.
+    LRP_CUDA(cudaStreamSynchronize(s));
+    forward_stage_host<T>(p, w, count, region);
+  }
   // the device alias of a host staging address
   auto dev = [&](const void* h) {
     return static_cast<const void*>(static_cast<const char*>(p->host_ptrs_dev) +
@@ -784,7 +814,7 @@ static lrp_status select_rows(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g,
 template <typename T, typename Body>
 static lrp_status run_captured(lrp_plan_s* p, Workspace<T>& w, int count, int kind, int level, cudaStream_t s,
                                Body body) {
-  if (!p->use_graphs || p->stats.timing || !p->cap_stream) return body(s);
+  if (!p->use_graphs || p->stats.timing || !p->cap_stream || p->capturing_solve) return body(s);
   if (w.graph_count != count) {
     SetupGuard guard;
     w.release_graphs();
@@ -836,9 +866,10 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   auto init = [&](cudaStream_t s) -> lrp_status {
     lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.Fh, fm, 2 * fm, kDimRF, s);
     if (st) return st;
+    LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_orth_keep<T>(cp, cb, s));
     LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
                launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
-                                 kDimRF, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
+                                 kDimC0, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
     // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
     LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_warm_load<T>(cp, cb, Strided<T>{w.U[1], nm, 2 * nm}, s));
     lrp_status sr = select_rows<T>(p, w, g, cs<T>(w.U[1], nm, 2 * nm), kDimC0, s);
@@ -861,54 +892,97 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
   // Each iteration launches over the compacted list of the slots still active
   // (k_count_active), in a bucket of the whole batch (level 0) or 2^(level-1)
   // entries, chosen from the count the host reads back.
-  int level = 0;
-  for (int k = 0; k < p->opts.max_iter; ++k) {
+  auto iteration = [&](int k, int level, cudaStream_t s) -> lrp_status {
     const int par = k & 1;
     CoreParams cpi = cp;
     cpi.g.act = p->act_list;
     cpi.g.nslots = level == 0 ? count : (1 << (level - 1));
     const TallGeom& gi = cpi.g;
-    auto iteration = [&](cudaStream_t s) -> lrp_status {
-      LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cpi, cb, k == 0 ? kDimC0 : kDimR, s));
-      if constexpr (sizeof(T) == 8) {
-        if (p->opts.matrix != LRP_MAT_POISSON) {
-          LRP_LAUNCH(p, LRP_K_CROSS, 1, s,
-                     launch_cross_matrix(gi, p->st, p->opts.matrix, Strided<double>{(double*)w.A, nm, 2 * nm},
-                                         Strided<const int32_t>{w.idx, d.M, 2 * (int64_t)d.M}, s));
-        } else {
-          LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
-        }
+    LRP_LAUNCH(p, LRP_K_SELECT, 1, s, launch_select<T>(cpi, cb, k == 0 ? kDimC0 : kDimR, s));
+    if constexpr (sizeof(T) == 8) {
+      if (p->opts.matrix != LRP_MAT_POISSON) {
+        LRP_LAUNCH(p, LRP_K_CROSS, 1, s,
+                   launch_cross_matrix(gi, p->st, p->opts.matrix, Strided<double>{(double*)w.A, nm, 2 * nm},
+                                       Strided<const int32_t>{w.idx, d.M, 2 * (int64_t)d.M}, s));
       } else {
         LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
       }
-      lrp_status st = cholqr3<T>(p, w, gi, cpi, cb, w.A, nm, 2 * nm, kDimOther, s);
+    } else {
+      LRP_LAUNCH(p, LRP_K_CROSS, 1, s, launch_cross<T>(gi, p->st, ca, s));
+    }
+    lrp_status st = cholqr3<T>(p, w, gi, cpi, cb, w.A, nm, 2 * nm, kDimOther, s);
+    if (st) return st;
+    LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cpi, cb, par, s));
+    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+               launch_gemm_nn<T>(gi, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
+                                 Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
+                                 none, 0, s));
+    st = select_rows<T>(p, w, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, s);
+    if (st) return st;
+    if (k > 0) {
+      // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
+      st = gram_reduce<T>(p, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
+                          w.part, Gx, false, s, sizeof(T) == 8);
       if (st) return st;
-      LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cpi, cb, par, s));
       LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
-                 launch_gemm_nn<T>(gi, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
-                                   Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
-                                   none, 0, s));
-      st = select_rows<T>(p, w, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, s);
+                 launch_gemm_nn<T>(gi, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
+                                   Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
+                                   Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
+      st = gram_reduce<T>(p, gi, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part,
+                          Ge, true, s, sizeof(T) == 8);
       if (st) return st;
-      if (k > 0) {
-        // X = U_k^T U_{k-1}; E = U_{k-1} - U_k X; GE = E^T E  (terms of rho)
-        st = gram_reduce<T>(p, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
-                            w.part, Gx, false, s, sizeof(T) == 8);
-        if (st) return st;
-        LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
-                   launch_gemm_nn<T>(gi, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
-                                     Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
-                                     Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
-        st = gram_reduce<T>(p, gi, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, cs<T>(w.Q1, nm, 2 * nm), kDimRPrev, w.part,
-                            Ge, true, s, sizeof(T) == 8);
-        if (st) return st;
-      }
-      LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cpi, cb, par, s));
-      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, p->act_list, s));
-      return LRP_OK;
-    };
+    }
+    LRP_LAUNCH(p, LRP_K_STOP, 1, s, launch_stop<T>(cpi, cb, par, s));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_count_active(p->st, count, p->active_dev, p->act_list, s));
+    return LRP_OK;
+  };
+  if (p->capturing_solve) {
+    // The loop runs on the device: iteration 0, then a conditional while-node
+    // whose body is one odd and one even iteration (the kernels' parity is fixed
+    // at capture); k_loop_next continues it while a problem is active.  Slots
+    // that finish within a trip are skipped by every later kernel (their act
+    // list entries are -1), and k_stop ends every slot at max_iter.
+    lrp_status st = iteration(0, 0, s);
+    if (st) return st;
+    if (p->opts.max_iter < 2) return LRP_OK;
+    const int max_trips = p->opts.max_iter / 2 + 1;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    LRP_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h;
+    LRP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_loop_begin(p->active_dev, p->loop_trips, h, s));
+    LRP_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    LRP_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    LRP_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    LRP_CUDA(cudaStreamBeginCaptureToGraph(p->body_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    st = iteration(1, 0, p->body_stream);
+    if (st == LRP_OK) st = iteration(2, 0, p->body_stream);
+    if (st == LRP_OK) {
+      cudaError_t e = launch_loop_next(p->active_dev, p->loop_trips, max_trips, h, p->body_stream);
+      if (e != cudaSuccess) st = set_error(LRP_ECUDA, std::string("loop control: ") + cudaGetErrorString(e));
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->body_stream, &captured);
+    if (st) return st;
+    if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
+    return LRP_OK;
+  }
+  int level = 0;
+  for (int k = 0; k < p->opts.max_iter; ++k) {
     const int kind = (k == 0) ? 0 : ((k & 1) ? 1 : 2);
-    lrp_status st = run_captured<T>(p, w, count, kind, level, s, iteration);
+    lrp_status st = run_captured<T>(p, w, count, kind, level, s,
+                                    [&](cudaStream_t cs_) { return iteration(k, level, cs_); });
     if (st) return st;
     if ((k + 1) % p->opts.check_every == 0 || k + 1 == p->opts.max_iter) {
       LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->active_dev, p->active_host_dev, sizeof(int32_t), s));
@@ -978,7 +1052,7 @@ static lrp_status warm_store(lrp_plan_s* p, Workspace<T>& w, const CoreParams& c
 static lrp_status run_fp64(lrp_plan_s* p, int count, cudaStream_t s) {
   CoreParams cp = make_core_params<double>(p, count, p->tol, 2.220446049250313e-16, 1e-12);
   lrp_status st;
-  if ((st = phase_forward<double>(p, p->w64, cp, count, true, false, s))) return st;
+  if ((st = phase_forward<double>(p, p->w64, cp, count, true, false, s, 0))) return st;
   if ((st = phase_iterate<double>(p, p->w64, cp, count, s))) return st;
   if ((st = warm_store<double>(p, p->w64, cp, s))) return st;
   return phase_finalize<double>(p, p->w64, cp, count, s);
@@ -1053,9 +1127,9 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   const TallGeom& g = c64.g;
   const Strided<const double> none{nullptr, 0, 0};
   lrp_status st;
-  if ((st = phase_forward<float>(p, p->w32, c32, count, true, false, s))) return st;
+  if ((st = phase_forward<float>(p, p->w32, c32, count, true, false, s, 0))) return st;
   // FP64 transform of the right-hand side for the residual, in double-float
-  if (p->opts.refine_steps > 0 && (st = phase_forward<double>(p, p->w64, c64, count, false, true, s))) return st;
+  if (p->opts.refine_steps > 0 && (st = phase_forward<double>(p, p->w64, c64, count, false, true, s, 1))) return st;
   if ((st = phase_iterate<float>(p, p->w32, c32, count, s))) return st;
   if ((st = warm_store<float>(p, p->w32, c32, s))) return st;
   // Without refinement the FP32 solution is the result (truncated at tol_in).
@@ -1064,8 +1138,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
   // Step 0 refines the FP32 trial; step 1 (refine_steps == 2) refines the FP64
   // result of step 0 for the problems whose first correction looks unreliable
   // (k_check_refine), the others held out of it.
-  bool held = false;
-  for (int step = 0; step < 2; ++step) {
+  auto refine_step = [&](int step, cudaStream_t s) -> lrp_status {
     RefineArgs rstep = ra;
     if (step) rstep.U64 = {p->w64.U[0], nm, 2 * nm};
     // Residual of the trial solution, recompressed with FP64 accuracy.  One
@@ -1186,20 +1259,118 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
                                         Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                         Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));
     }
-    if (step == 0 && p->opts.refine_steps >= 2) {
-      LRP_CUDA(cudaMemsetAsync(p->active_dev, 0, sizeof(int32_t), s));
-      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_check_refine(ra, count, p->active_dev, s));
+    return LRP_OK;
+  };
+  if ((st = refine_step(0, s))) return st;
+  if (p->opts.refine_steps >= 2) {
+    // The problems whose first step looks unreliable take a second one
+    // (k_check_refine holds the others out); it runs when any is flagged: a
+    // host decision, or a conditional node when the solve is one graph.
+    LRP_CUDA(cudaMemsetAsync(p->active_dev, 0, sizeof(int32_t), s));
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_check_refine(ra, count, p->active_dev, s));
+    if (p->capturing_solve) {
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t graph = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      LRP_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+      cudaGraphConditionalHandle h;
+      LRP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+      LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_cond_positive(p->active_dev, h, s));
+      LRP_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      LRP_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      LRP_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      LRP_CUDA(cudaStreamBeginCaptureToGraph(p->if_stream, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      st = refine_step(1, p->if_stream);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(p->if_stream, &captured);
+      if (st) return st;
+      if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("second step capture: ") + cudaGetErrorString(e));
+    } else {
       LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->active_dev, p->active_host_dev, sizeof(int32_t), s));
       LRP_CUDA(cudaStreamSynchronize(s));
-      held = true;
-      if (*static_cast<volatile int32_t*>(p->active_host) > 0) continue;
+      if (*static_cast<volatile int32_t*>(p->active_host) > 0 && (st = refine_step(1, s))) return st;
     }
-    break;
+    LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_release_held(ra, count, s));
   }
-  if (held) LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_release_held(ra, count, s));
   LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_final_state(ra, count, s));
   return phase_finalize<double>(p, p->w64, c64, count, s, true);
 }
+}  // namespace lrp
+
+namespace lrp {
+
+// Enqueue the whole solve of `count` staged problems into the capturing
+// stream s (device-side iteration loops).
+lrp_status enqueue_solve(lrp_plan_s* p, int count, cudaStream_t s) {
+  p->capturing_solve = true;
+  const lrp_status st = (p->opts.precision == LRP_FP64) ? run_fp64(p, count, s) : run_mixed(p, count, s);
+  p->capturing_solve = false;
+  return st;
+}
+
+// Host staging of a device-loop solve: the forward DST job arrays (the problem
+// descriptors are staged by lrp_solve_batch).
+void stage_solve(lrp_plan_s* p, int count) {
+  if (p->opts.precision == LRP_FP64) {
+    forward_stage_host<double>(p, p->w64, count, 0);
+  } else {
+    forward_stage_host<float>(p, p->w32, count, 0);
+    if (p->opts.refine_steps > 0) forward_stage_host<double>(p, p->w64, count, 1);
+  }
+}
+
+// One graph launch per solve: captured on first use for (count, warm records,
+// tracing), replayed on the caller's stream afterwards.
+static lrp_status solve_device(lrp_plan_s* p, int count, cudaStream_t s) {
+  stage_solve(p, count);
+  const int key[3] = {count, p->any_warm ? 1 : 0, p->trace_on ? 1 : 0};
+  if (!p->solve_exec || key[0] != p->solve_key[0] || key[1] != p->solve_key[1] || key[2] != p->solve_key[2]) {
+    if (p->solve_exec) {
+      SetupGuard guard;
+      cudaGraphExecDestroy(p->solve_exec);
+      p->solve_exec = nullptr;
+    }
+    int64_t before[LRP_K_COUNT];
+    for (int c = 0; c < LRP_K_COUNT; ++c) before[c] = p->stats.launches[c];
+    cudaGraph_t graph = nullptr;
+    {
+      CaptureGuard capture;
+      LRP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const lrp_status st = enqueue_solve(p, count, p->cap_stream);
+      const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+      if (st != LRP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("solve capture: ") + cudaGetErrorString(e));
+    }
+    const cudaError_t e = cudaGraphInstantiate(&p->solve_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      p->solve_exec = nullptr;
+      return set_error(LRP_ECUDA, std::string("solve graph instantiate: ") + cudaGetErrorString(e));
+    }
+    for (int c = 0; c < LRP_K_COUNT; ++c) {
+      p->solve_launches[c] = p->stats.launches[c] - before[c];
+      p->stats.launches[c] = before[c];
+    }
+    for (int i = 0; i < 3; ++i) p->solve_key[i] = key[i];
+  }
+  LRP_CUDA(cudaGraphLaunch(p->solve_exec, s));
+  LRP_CUDA(cudaEventRecord(p->solve_done, s));
+  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += p->solve_launches[c];
+  return LRP_OK;
+}
+
 }  // namespace lrp
 
 static lrp_status validate_problem(const lrp_plan_s* p, const lrp_problem& pr) {
@@ -1212,17 +1383,20 @@ static lrp_status validate_problem(const lrp_plan_s* p, const lrp_problem& pr) {
   return LRP_OK;
 }
 
-extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_problem* hp, void* stream) {
-  if (!p || !hp) return set_error(LRP_EINVAL, "NULL argument");
+namespace lrp {
+
+// Validate a batch and write its descriptors to the plan's pinned staging
+// (the caller holds p->mu).  A device-loop solve returns before it has run, so
+// its staging is rewritten only after the previous solve has finished with it.
+lrp_status stage_problems(lrp_plan_s* p, int32_t count, const lrp_problem* hp) {
   if (count < 1 || count > p->dims.B) return set_error(LRP_EINVAL, "count out of range [1, batch]");
-  std::lock_guard<std::mutex> lock(p->mu);
   for (int i = 0; i < count; ++i) {
     lrp_status s = validate_problem(p, hp[i]);
     if (s != LRP_OK) return s;
     for (int j = 0; j < i && hp[i].warm; ++j)
       if (hp[j].warm == hp[i].warm) return set_error(LRP_EINVAL, "one warm-start record used twice in a batch");
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  if (p->device_loop) LRP_CUDA(cudaEventSynchronize(p->solve_done));
   for (int i = 0; i < count; ++i) {
     ProblemDev& d = p->prob_host[i];
     d.rf = hp[i].r_f;
@@ -1242,8 +1416,26 @@ extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_pro
   }
   p->any_warm = false;
   for (int i = 0; i < count; ++i) p->any_warm = p->any_warm || hp[i].warm != nullptr;
-  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->prob_host_dev, p->prob_dev, sizeof(ProblemDev) * count, s));
   p->last_count = count;
+  return LRP_OK;
+}
+
+// The staged descriptors to device memory (a kernel reading the mapped pinned staging).
+lrp_status launch_problems(lrp_plan_s* p, int32_t count, cudaStream_t s) {
+  LRP_LAUNCH(p, LRP_K_OTHER, 1, s, launch_stage(p->prob_host_dev, p->prob_dev, sizeof(ProblemDev) * count, s));
+  return LRP_OK;
+}
+
+}  // namespace lrp
+
+extern "C" lrp_status lrp_solve_batch(lrp_plan_t p, int32_t count, const lrp_problem* hp, void* stream) {
+  if (!p || !hp) return set_error(LRP_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(p->mu);
+  lrp_status st = stage_problems(p, count, hp);
+  if (st != LRP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = launch_problems(p, count, s)) != LRP_OK) return st;
+  if (p->device_loop && !p->stats.timing) return solve_device(p, count, s);
   if (p->opts.precision == LRP_FP64) return run_fp64(p, count, s);
   return run_mixed(p, count, s);
 }

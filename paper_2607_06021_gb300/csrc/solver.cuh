@@ -158,6 +158,17 @@ struct lrp_plan_s {
   int last_count = 0;                    // problems of the most recent lrp_solve_batch
   double* trace_dev = nullptr;           // [B][kTraceLen][kTraceWidth], allocated on first use
   bool trace_on = false;
+  // Device-side iteration loops (opts.loop_on_device): the whole solve is one
+  // captured graph; its Cross-DEIM loops are conditional while-nodes.
+  bool device_loop = false;
+  bool capturing_solve = false;          // a whole-solve capture is open (no host sync or staging)
+  cudaStream_t body_stream = nullptr;    // captures the loop bodies
+  cudaStream_t if_stream = nullptr;      // captures the mixed path's second refinement step
+  int32_t* loop_trips = nullptr;         // device: trips of the running device-side loop
+  cudaGraphExec_t solve_exec = nullptr;  // the captured solve
+  int solve_key[3] = {-1, -1, -1};       // (count, any_warm, trace_on) it was captured for
+  int64_t solve_launches[LRP_K_COUNT] = {};  // kernel nodes of the captured solve (loop bodies once)
+  cudaEvent_t solve_done = nullptr;      // completion of the last enqueued solve
   std::mutex mu;
 };
 

@@ -16,3 +16,22 @@ def to_np(t: torch.Tensor) -> np.ndarray:
 
 def rhs_dev(rhs):
     return to_dev(rhs.U), to_dev(rhs.s), to_dev(rhs.V)
+
+
+def _exact_error_n4095(job):
+    import lrp_inputs as li
+    from oracle import poisson as po
+    seed, U, S, V = job
+    r = li.workload_n4095(seed=seed)
+    return po.rel_error_vs_exact(U, S, V, po.SpectralSolution(r.U, r.s, r.V))
+
+
+def exact_errors_n4095(seeds, results, procs=16):
+    """Exact relative errors of n = 4095 bench-workload results (U, S, V as CUDA
+    tensors, rank columns only) against the oracle's exact solution, computed in
+    a pool of spawned worker processes (never forked from this CUDA process)."""
+    import multiprocessing as mp
+    import os
+    jobs = [(sd, to_np(U), to_np(S), to_np(V)) for sd, (U, S, V) in zip(seeds, results)]
+    with mp.get_context("spawn").Pool(max(1, min(procs, os.cpu_count() or 1))) as pool:
+        return np.array(pool.map(_exact_error_n4095, jobs, chunksize=4))

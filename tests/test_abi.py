@@ -58,8 +58,11 @@ def test_option_checks_need_no_gpu():
             setattr(o, k, v)
         return lib.lrp_plan(ctypes.byref(h), n, 1e-8, 8, ctypes.byref(o))
 
-    assert pkg.lrp_default_opts().refine_steps == 1 and pkg.lrp_default_opts().sample_factor == 1.0
+    assert pkg.lrp_default_opts().refine_steps == 2 and pkg.lrp_default_opts().sample_factor == 1.0
     assert pkg.lrp_default_opts().matrix == pkg.LRP_MAT_POISSON
+    assert pkg.lrp_default_opts().selector == pkg.LRP_SEL_BERNOULLI
+    assert pkg.lrp_default_opts().loop_on_device == 0
+    assert plan(loop_on_device=2) == pkg.LRP_EINVAL and "loop_on_device" in pkg.last_error()
     assert plan(selector=7) == pkg.LRP_EINVAL and "selector" in pkg.last_error()
     assert plan(selector=pkg.LRP_SEL_BERNOULLI, sample_factor=0.0) == pkg.LRP_EINVAL
     assert plan(selector=pkg.LRP_SEL_BERNOULLI, sample_factor=-1.0) == pkg.LRP_EINVAL
@@ -119,7 +122,8 @@ def test_plan_estimate_is_host_only_and_linear_in_batch():
 
 def test_request_footprint_formula():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
-    # 8 n (2 r_f + 4 m_cap + 2 max_rank), m_cap = min(2 max_rank + r_f rounded up to 64, 256)
-    assert pkg.lrp_request_footprint(4095, 20, 64) == 8 * 4095 * (40 + 4 * 192 + 128)
+    # 8 n (2 r_f + 4 m_cap + 2 max_rank), m_cap = min(2 max_rank + r_f rounded up to 16, 256)
+    assert pkg.lrp_request_footprint(4095, 20, 64) == 8 * 4095 * (40 + 4 * 160 + 128)
     assert pkg.lrp_request_footprint(262143, 48, 128) == 8 * 262143 * (96 + 4 * 256 + 256)
+    assert pkg.lrp_request_footprint(1023, 2, 8) == 8 * 1023 * (4 + 4 * 32 + 16)
     assert pkg.lrp_request_footprint(255, 0, 8) == 0

@@ -38,7 +38,7 @@ def test_bernoulli_fp64_trace_matches_oracle(seed, factor):
         assert (row["size_I"], row["size_J"]) == tuple(oinfo.sizes[k]), (k, row, oinfo.sizes[k])
         assert row["rank"] == oinfo.ranks[k], (k, row)
         assert abs(row["rho"] - oinfo.rho[k]) <= 1e-6 * oinfo.rho[k] + 1e-13, (k, row["rho"], oinfo.rho[k])
-    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) < 1e-9
+    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) <= 1e-10
     assert po.rel_error_vs_exact(U, S, V, G) < 1e-9
 
 
@@ -52,6 +52,6 @@ def test_bernoulli_n4095_fp64_and_mixed():
     assert info["iterations"] == oinfo.iterations
     assert [(r["size_I"], r["size_J"]) for r in tr] == [tuple(s) for s in oinfo.sizes]
     assert po.rel_error_vs_exact(U, S, V, G) < 10 * tol
-    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) < 10 * tol
+    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) <= 1e-10
     Um, Sm, Vm, infom, _ = _gpu(rhs, tol, r_max, m_cap=64, seed=key, sample_factor=1.5, precision="mixed")
     assert po.rel_error_vs_exact(Um, Sm, Vm, G) <= 1e-6, infom

@@ -33,7 +33,7 @@ def test_qdeim_fp64_matches_oracle(seed):
     assert info["iterations"] == oinfo.iterations, (info, oinfo.iterations)
     for k, row in enumerate(tr):
         assert (row["size_I"], row["size_J"]) == tuple(oinfo.sizes[k]), (k, row, oinfo.sizes[k])
-    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) < 1e-9
+    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) <= 1e-10
     assert po.rel_error_vs_exact(U, S, V, G) < 10 * tol
 
 
@@ -45,7 +45,7 @@ def test_qdeim_edge_sizes(n):
     Uo, So, Vo, oinfo, G = cd.poisson_solve(rhs.U, rhs.s, rhs.V, tol, r_max, m_cap=2 * r_max + rhs.rank,
                                             selector="qdeim")
     assert info["iterations"] == oinfo.iterations
-    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) < 1e-9
+    assert po.lowrank_rel_diff(U, S, V, Uo, So, Vo) <= 1e-10
 
 
 def test_qdeim_mixed_n4095_accuracy():
