@@ -32,7 +32,9 @@ TOL = 1e-8
 RMAX = 64
 RF = 20
 M_CAP = 64  # index-set capacity; the sets reach at most ~35 on this workload
-ERR_SAMPLE = 48  # problems whose error against the exact solution is checked
+ERR_CHECK = 256  # problems of the timed batch whose error against the exact solution is checked
+ERR_BAR = 1e-6   # the metric's accuracy bar
+STATUS_NAMES = {0: "LRP_OK", 5: "LRP_NOT_CONVERGED", 6: "LRP_RANK_CAPPED"}
 WORKLOAD = ("n=4095 (h=1/4096), RHS rank 20 = 16 seeded Gaussians + 4 eigenfunctions "
             "(p,q in 1..64), tol 1e-8, max rank 64, index-set capacity 64")
 METRIC = "Poisson solves/s & p50/p99 latency at rel err<=1e-6, mixed vs plain FP64"
@@ -60,20 +62,28 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrp", choices=["lrp", "reference"])
     ap.add_argument("--batch", type=int, default=1024, help="problems per step (per GPU)")
-    ap.add_argument("--lanes", type=int, default=4, help="concurrent sub-batches (lrp_group), 1 = one plan")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="concurrent sub-batches (lrp_group), 1 = one plan; 0 = the tuned table's choice, else 4")
+    ap.add_argument("--loop-on-device", type=int, default=-1,
+                    help="1: iteration loops on the device (one graph per solve); -1 = the tuned table's choice")
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--err-check", type=int, default=ERR_CHECK,
+                    help="problems of the batch checked against the exact solution (0: all)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--refine-steps", type=int, default=1,
+    ap.add_argument("--refine-steps", type=int, default=2,
                     help="mixed precision: 1 residual-correction step, or 2 (a second one where the first looks unreliable)")
+    ap.add_argument("--selector", default="bernoulli", choices=["ls", "bernoulli", "qdeim"],
+                    help="index selector: leverage top-c, leverage Bernoulli sampling, or QDEIM")
+    ap.add_argument("--sample-factor", type=float, default=1.0, help="Bernoulli c / columns")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line: solve time, rank and iterations against n (Sec. 4.2 scaling)")
     ap.add_argument("--sweep-kmin", type=int, default=10)
     ap.add_argument("--sweep-kmax", type=int, default=20)
     ap.add_argument("--sweep-seeds", type=int, default=3, help="growth-index seeds per size")
-    ap.add_argument("--sweep-selectors", default="ls,bernoulli,qdeim", help="index selectors of the sweep")
-    ap.add_argument("--sweep-sample-factor", type=float, default=4.0, help="Bernoulli c / columns in the sweep")
+    ap.add_argument("--sweep-selectors", default="bernoulli,ls,qdeim", help="index selectors of the sweep")
+    ap.add_argument("--sweep-sample-factor", type=float, default=1.0, help="Bernoulli c / columns in the sweep")
     ap.add_argument("--test-matrices", action="store_true",
                     help="instead of the bench line: Cross-DEIM on the test matrices of Sec. 4.1")
     ap.add_argument("--serve-requests", type=int, default=800,
@@ -81,6 +91,12 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-kmax", type=int, default=14, help="largest n = 2^k - 1 of the stream")
     ap.add_argument("--mixed-sizes", type=int, default=512, help="solves of the mixed-size batch (0: skip)")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="instead of the bench line: the serving stream at several offered rates (n up to 2^18-1)")
+    ap.add_argument("--serve-sweep-rates", default="1000,2000,5000,10000,20000")
+    ap.add_argument("--serve-sweep-requests", type=int, default=4000, help="requests per offered rate")
+    ap.add_argument("--serve-sweep-kmax", type=int, default=18)
+    ap.add_argument("--serve-lanes", type=int, default=4)
     return ap.parse_args()
 
 
@@ -359,13 +375,23 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         return replica_max(v, world, device)
 
     results = {}
+    from paper_2607_06021_gb300 import tune
+    table = tune.TuneTable(tune.TABLE_PATH)
     for prec in precisions:
-        if args.lanes > 1:
-            plan = lrp.Group(N, TOL, RMAX, lanes=args.lanes, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
-                             refine_steps=args.refine_steps)
+        # lanes and loop placement: the command line, else the tuned table (both
+        # leave the results unchanged), else 4 lanes with host loops
+        cfg = table.get_config(prec, N, RF, B)
+        lanes = args.lanes if args.lanes > 0 else (cfg[0] if cfg else 4)
+        dev = bool(args.loop_on_device) if args.loop_on_device >= 0 else (cfg[1] if cfg else False)
+        src = "table" if (cfg and args.lanes <= 0 and args.loop_on_device < 0) else "command line / default"
+        if lanes > 1:
+            plan = lrp.Group(N, TOL, RMAX, lanes=lanes, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
+                             refine_steps=args.refine_steps, selector=args.selector,
+                             sample_factor=args.sample_factor, loop_on_device=dev)
         else:
             plan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
-                            refine_steps=args.refine_steps)
+                            refine_steps=args.refine_steps, selector=args.selector, sample_factor=args.sample_factor,
+                            loop_on_device=dev)
 
         def step():
             with torch.cuda.stream(stream):
@@ -393,7 +419,8 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         launches = plan.kernel_stats()["all"][0]
         total_ms = max_over_ranks(sum(ms))
         res = {"ms": ms, "total_ms": total_ms, "wall_s": wall, "clocks": clk, "launches": launches,
-               "value": whole_job_value(B, world, args.steps, total_ms)}
+               "value": whole_job_value(B, world, args.steps, total_ms),
+               "tuning": {"lanes": lanes, "loop_on_device": dev, "source": src}}
         # End to end through the public call with host buffers (pinned), copies inside the timed region.
         if not args.no_e2e:
             barrier()
@@ -416,7 +443,7 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         # another lane's (concurrent lanes would fold their waits into each
         # launch's event interval).
         tplan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
-                         refine_steps=args.refine_steps)
+                         refine_steps=args.refine_steps, selector=args.selector, sample_factor=args.sample_factor)
         with torch.cuda.stream(stream):
             tplan.solve_batch_into(batch.inputs, batch.outputs, stream)
         tplan.set_timing(True)
@@ -500,18 +527,22 @@ def class_rooflines(res, prec, hbm_peak):
     return out
 
 
-def serving_stream(args, rank):
+def serving_stream(args, rank, rate=None, requests=None, kmax=None, lanes=2, cap_gb=40, keep=32):
     """Poisson arrivals of independent requests through the request server:
     n = 2^k - 1 with k uniform in 8..kmax, r_f uniform in 2..48 Gaussians, 80%
     mixed precision at tol 1e-6 and 20% FP64 at tol 1e-10 (rank cap 64), 10% of
     requests perturbed repeats of an earlier one that reuse its warm-start key.
-    Latency runs from the request's arrival time to its completion."""
+    Latency runs from the request's arrival time to its completion.  Returns the
+    record and up to `keep` served results with n <= 4095 (for the accuracy
+    check of the CPU leg)."""
     import numpy as np
 
     import lrp_inputs as li
     import paper_2607_06021_gb300 as lrp
+    rate = args.serve_rate if rate is None else rate
+    R = args.serve_requests if requests is None else requests
+    kmax = args.serve_kmax if kmax is None else kmax
     rng = np.random.default_rng(7 + rank)
-    R = args.serve_requests
     specs = []
     for i in range(R):
         if i > 0 and rng.random() < 0.10:
@@ -521,7 +552,7 @@ def serving_stream(args, rank):
             specs[j]["warm_key"] = j + 1
             s = dict(specs[j], repeat_of=j, warm_key=j + 1, pert=int(rng.integers(1 << 30)))
         else:
-            k = int(rng.integers(8, args.serve_kmax + 1))
+            k = int(rng.integers(8, kmax + 1))
             mixed = rng.random() < 0.8
             s = {"n": (1 << k) - 1, "r_f": int(rng.integers(2, 49)), "seed": int(rng.integers(1 << 30)),
                  "prec": "mixed" if mixed else "fp64", "tol": 1e-6 if mixed else 1e-10, "repeat_of": -1,
@@ -531,13 +562,13 @@ def serving_stream(args, rank):
     for s in specs:
         base = li.gaussian_eigen_rhs(s["n"], s["seed"], s["r_f"])
         rhss.append(li.perturb_amplitudes(base, s["pert"]) if s["repeat_of"] >= 0 else base)
-    gaps = rng.exponential(1.0 / args.serve_rate, size=R)
+    gaps = rng.exponential(1.0 / rate, size=R)
     arrivals = np.cumsum(gaps)
-    sv = lrp.Server(lanes=2, max_batch=32, warm_capacity=64)
+    sv = lrp.Server(memory_cap_bytes=int(cap_gb) << 30, lanes=lanes, max_batch=32, warm_capacity=64)
     # warm the server's plans on one request per bucket (untimed)
     seen = set()
     for s, r in zip(specs, rhss):
-        key = (s["n"], s["prec"], (s["r_f"] + 63) // 64)
+        key = (s["n"], s["prec"], (s["r_f"] + 15) // 16)
         if key in seen:
             continue
         seen.add(key)
@@ -557,27 +588,56 @@ def serving_stream(args, rank):
             time.sleep(1e-4)  # server full: retry
         tickets[i] = t
         delay_us[i] = max(0.0, (time.perf_counter() - t0 - arrivals[i]) * 1e6)
-    lat, warm_hits, statuses = np.zeros(R), 0, {}
+    lat, warm_hits, statuses, by_class = np.zeros(R), 0, {}, {}
+    kept = []
     for i, t in enumerate(tickets):
         res = sv.wait(t, 600.0)
         info = res[3]
         lat[i] = info["latency_us"] + delay_us[i]
         warm_hits += info["warm_used"]
         statuses[info["status"]] = statuses.get(info["status"], 0) + 1
+        cls = f"n={specs[i]['n']},{specs[i]['prec']}"
+        c = by_class.setdefault(cls, {})
+        nm = lrp.status_string(info["status"])
+        c[nm] = c.get(nm, 0) + 1
+        if len(kept) < keep and specs[i]["n"] <= 4095 and i % 3 == 0:
+            kept.append((rhss[i], specs[i]["prec"], specs[i]["tol"], res[0], res[1], res[2]))
     wall = time.perf_counter() - t0
     st = sv.stats()
     last_error = sv.last_error()
     sv.close()
     failed = sum(v for k, v in statuses.items() if k not in (lrp.LRP_OK, lrp.LRP_NOT_CONVERGED, lrp.LRP_RANK_CAPPED))
-    return {"requests": R, "rate_per_s": args.serve_rate, "wall_s": round(wall, 3), "failed": failed,
-            "last_error": last_error or None,
-            "throughput_solves_per_s": R / wall,
-            "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
-            "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,
-            "status_counts": {lrp.status_string(k): v for k, v in statuses.items()},
-            "workload": f"n=2^k-1, k~U{{8..{args.serve_kmax}}}, r_f~U{{2..48}} Gaussians, 80% mixed/1e-6, "
-                        "20% FP64/1e-10, rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
-                        "latency from arrival to completion, plans warmed per bucket beforehand"}
+    rec = {"requests": R, "rate_per_s": rate, "wall_s": round(wall, 3), "failed": failed,
+           "last_error": last_error or None,
+           "throughput_solves_per_s": R / wall,
+           "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+           "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,
+           "status_counts": {lrp.status_string(k): v for k, v in statuses.items()},
+           "status_by_class": by_class, "lanes": lanes, "memory_cap_gb": cap_gb,
+           "workload": f"n=2^k-1, k~U{{8..{kmax}}}, r_f~U{{2..48}} Gaussians, 80% mixed/1e-6, "
+                       "20% FP64/1e-10, rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
+                       "latency from arrival to completion, plans warmed per bucket beforehand"}
+    return rec, kept
+
+
+def _served_error_job(job):
+    """Exact relative error of one served result (pool worker)."""
+    from oracle import poisson as po
+    rhs, U, S, V = job
+    return po.rel_error_vs_exact(U, S, V, po.SpectralSolution(rhs.U, rhs.s, rhs.V))
+
+
+def check_served(kept, pool, sample="every third served request with n <= 4095, exact sums"):
+    """Exact errors of a sample of results against the oracle (CPU leg)."""
+    import numpy as np
+    if not kept:
+        return None
+    jobs = [(r, U, S, V) for r, _, _, U, S, V in kept]
+    e = np.array(pool.map(_served_error_job, jobs) if pool else [_served_error_job(j) for j in jobs])
+    bars = np.array([max(10 * tol, 1e-6) if prec == "mixed" else 10 * tol for _, prec, tol, *_ in kept])
+    return {"checked": len(kept), "max": float(e.max()), "median": float(np.median(e)),
+            "above_bar": int((e > bars).sum()), "bar": "max(10 tol, 1e-6) mixed, 10 tol FP64",
+            "sample": sample}
 
 
 def mixed_sizes_batch(args, rank):
@@ -611,12 +671,77 @@ def mixed_sizes_batch(args, rank):
                         "host factors in, host factors out, median of 3 runs"}
 
 
-def cpu_baseline(rhss, seconds, gpu_results=None):
-    """The CPU oracle as it stands, on a bounded sample of the same workload."""
+def _exact_error_job(job):
+    """Relative error of one GPU result against the exact solution (pool worker)."""
+    from oracle import poisson as po
+    seed, U, S, V = job
+    import lrp_inputs as li
+    r = li.workload_n4095(seed=seed)
+    return po.rel_error_vs_exact(U, S, V, po.SpectralSolution(r.U, r.s, r.V))
+
+
+def start_error_pool():
+    """Worker processes for the exact-error check, started (spawn) before any
+    GPU work so that no worker is forked from a process holding a CUDA context."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+
+
+def mixed_sizes_one_launch(args, rank):
+    """The same 512 mixed-size solves as one CUDA graph launch (lrp_multi):
+    inputs resident on the device, one branch per grid size, the iteration
+    loops on the device; time per launch by CUDA events after warm-up."""
+    import numpy as np
+    import torch
+
+    import lrp_inputs as li
+    import paper_2607_06021_gb300 as lrp
+    rhss = li.batch_mixed_sizes(args.mixed_sizes, seed=11 + rank)
+    sizes = sorted({r.n for r in rhss})
+    counts = [sum(1 for r in rhss if r.n == n) for n in sizes]
+    multi = lrp.Multi(sizes, counts, 1e-6, 64, precision="mixed", max_rhs_rank=24, m_cap=64,
+                      selector=args.selector, sample_factor=args.sample_factor)
+    ins = [rhs_dev(r) for r in rhss]
+    outs = [multi.alloc_outputs(r.n) for r in rhss]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            multi.solve_batch_into(ins, outs, stream)  # capture, then one replay
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            multi.solve_batch_into(ins, outs, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    infos = [lrp.parse_info(o[3]) for o in outs]
+    kept = []
+    for b, (r, o, inf) in enumerate(zip(rhss, outs, infos)):
+        if r.n <= 4095 and b % 8 == 0:
+            rk = inf["rank"]
+            kept.append((r, "mixed", 1e-6, to_np(o[0][:, :rk]), to_np(o[1][:rk]), to_np(o[2][:, :rk])))
+    multi.close()
+    st = {}
+    for i in infos:
+        nm = STATUS_NAMES.get(i["status"], str(i["status"]))
+        st[nm] = st.get(nm, 0) + 1
+    t = statistics.median(ms) / 1e3
+    return kept, {"solves": len(rhss), "launches_per_batch": 1, "ms": round(1e3 * t, 3), "solves_per_s": len(rhss) / t,
+            "iterations_mean": float(np.mean([i["total_iterations"] for i in infos])), "status_counts": st,
+            "sizes": dict(zip([str(n) for n in sizes], counts)),
+            "workload": "as mixed_sizes_batch, device-resident inputs, one graph launch per batch (lrp_multi), "
+                        "median of 5 launches after warm-up"}
+
+
+def cpu_baseline(rhss, seeds, seconds, gpu_results=None, check=ERR_CHECK, pool=None):
+    """The CPU oracle as it stands, on a bounded sample of the same workload;
+    and the exact error of `check` of the last step's GPU results (0: all)."""
     import numpy as np
 
     from oracle import cross_deim as cd
-    from oracle import poisson as po
     try:
         from threadpoolctl import threadpool_info
         cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
@@ -635,20 +760,24 @@ def cpu_baseline(rhss, seconds, gpu_results=None):
            "sample": f"{done} of the batch's problems, solved one after another ({dt:.1f} s)"}
     errs = {}
     if gpu_results:
-        # exact errors of ERR_SAMPLE problems spread over the batch (last step's results)
-        import numpy as np
-        picks = sorted(set(int(b) for b in np.linspace(0, len(rhss) - 1, min(ERR_SAMPLE, len(rhss)))))
+        B = len(rhss)
+        k = B if check <= 0 else min(check, B)
+        picks = sorted(set(int(b) for b in np.linspace(0, B - 1, k)))
         for prec, res in gpu_results.items():
-            e = []
+            jobs = []
             for b in picks:
-                G = po.SpectralSolution(rhss[b].U, rhss[b].s, rhss[b].V)
-                inf = res["infos"][b]
+                rk = res["infos"][b]["rank"]
                 U, S, V = res["results"][b]
-                rk = inf["rank"]
-                e.append(po.rel_error_vs_exact(U[:, :rk], S[:rk], V[:, :rk], G))
-            e = np.array(e)
-            errs[prec] = {"checked": len(picks), "max": float(e.max()), "p90": float(np.quantile(e, 0.9)),
-                          "median": float(np.median(e)), "above_1e-6": int((e > 1e-6).sum())}
+                jobs.append((seeds[b], np.ascontiguousarray(U[:, :rk]), S[:rk].copy(), np.ascontiguousarray(V[:, :rk])))
+            t1 = time.perf_counter()
+            e = np.array(pool.map(_exact_error_job, jobs, chunksize=4) if pool else [_exact_error_job(j) for j in jobs])
+            st = {}
+            for b in range(B):
+                nm = STATUS_NAMES.get(res["infos"][b]["status"], str(res["infos"][b]["status"]))
+                st[nm] = st.get(nm, 0) + 1
+            errs[prec] = {"checked": len(picks), "of": B, "max": float(e.max()), "p90": float(np.quantile(e, 0.9)),
+                          "median": float(np.median(e)), "above_1e-6": int((e > 1e-6).sum()),
+                          "status_counts": st, "check_s": round(time.perf_counter() - t1, 1)}
     return out, errs
 
 
@@ -790,10 +919,20 @@ def main():
         if rank == 0:
             print(json.dumps(sweep(args) if args.sweep else test_matrices(args)))
         return
+    if args.serve_sweep:
+        if rank == 0:
+            rows = []
+            for rate in [float(v) for v in args.serve_sweep_rates.split(",")]:
+                rec, _ = serving_stream(args, rank, rate=rate, requests=args.serve_sweep_requests,
+                                        kmax=args.serve_sweep_kmax, lanes=args.serve_lanes, cap_gb=40)
+                rows.append(rec)
+            print(json.dumps({"mode": "serving_sweep", "rates": rows}))
+        return
     if args.precision == "both":
         precisions = ["fp64", "mixed"]
     else:
         precisions = [args.precision]
+    pool = start_error_pool() if (rank == 0 and world == 1 and not args.no_cpu) else None
     results, rhss, hbm_peak, peak_src = gpu_arm(args, rank, world, local_rank, precisions)
     if rank != 0:
         return
@@ -804,7 +943,9 @@ def main():
         "metric": METRIC, "value": res["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": args.batch, "lanes": args.lanes, "precision": head,
+        "config": {"workload": WORKLOAD, "batch_per_gpu": args.batch, "lanes": res["tuning"]["lanes"],
+                   "loop_on_device": res["tuning"]["loop_on_device"], "tuning": res["tuning"]["source"],
+                   "selector": args.selector, "precision": head,
                    "refine_steps": args.refine_steps,
                    "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"},
         "latency_ms": {"p50": statistics.median(ms), "p99": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
@@ -827,12 +968,29 @@ def main():
                                 if k != "all" and v[2] + v[3] == 0 and v[1] > 0}
     if args.mixed_sizes > 0:
         line["mixed_sizes_batch"] = mixed_sizes_batch(args, rank)
+        kept_multi, line["mixed_sizes_one_launch"] = mixed_sizes_one_launch(args, rank)
+    kept = []
+    if args.mixed_sizes <= 0:
+        kept_multi = []
     if args.serve_requests > 0:
-        line["serving"] = serving_stream(args, rank)
+        line["serving"], kept = serving_stream(args, rank)
     if not args.no_cpu and world == 1:
-        cb, errs = cpu_baseline(rhss, args.cpu_seconds, results)
+        cb, errs = cpu_baseline(rhss, replica_seeds(rank, args.batch), args.cpu_seconds, results,
+                                args.err_check, pool)
+        if kept:
+            line["serving"]["accuracy"] = check_served(kept, pool)
+        if kept_multi:
+            line["mixed_sizes_one_launch"]["accuracy"] = check_served(
+                kept_multi, pool, "every eighth problem of the batch with n <= 4095, exact sums")
+        pool.close()
         line["cpu_baseline"] = cb
         line["rel_err_vs_exact"] = errs
+        bad = {p: e["above_1e-6"] for p, e in errs.items() if e["above_1e-6"] > 0}
+        line["accuracy"] = {"bar": ERR_BAR, "checked": {p: e["checked"] for p, e in errs.items()},
+                            "passed": not bad}
+        if bad:
+            # a throughput at the metric's bar is not valid when a checked result misses the bar
+            line["invalid"] = f"results above rel err {ERR_BAR:g}: {bad}"
     print(json.dumps(line))
 
 

@@ -5,12 +5,14 @@
 // Requests carry host factors (copied at submission, so the caller may reuse
 // its buffers at once) and host output buffers (written before the request
 // completes).  Worker lanes, one host thread and one CUDA stream each, take the
-// oldest waiting request, gather up to a plan's batch of waiting requests of
-// the same bucket (n, precision, tol, max_rank, right-hand-side rank class) in
-// arrival order, and run them as one lrp_solve_batch call; requests that arrive
-// meanwhile join the next batch of their bucket.  Plans are created on first
-// use, sized so that several fit the memory cap, and destroyed least recently
-// used when a new one would not fit.
+// oldest waiting request that can start, gather up to a plan's batch of waiting
+// requests of the same bucket (n, precision, tol, max_rank, right-hand-side
+// rank class) in arrival order, and run them as one lrp_solve_batch call (one
+// graph launch: the plans loop on the device).  A bucket may hold up to one
+// plan per lane, so requests arriving while a batch of their bucket runs start
+// on another lane instead of waiting for it.  Plans are created on first use,
+// sized so that several fit the memory cap, and destroyed least recently used
+// when a new one would not fit.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -61,11 +63,20 @@ struct BucketKey {
   }
 };
 
-// Right-hand-side rank class of a bucket: coarse, so that a stream of mixed
-// ranks shares few plans (the class only sizes the plan's r_f capacity).
-int rf_class(int r_f) { return (r_f + 63) / 64 * 64; }
+// Right-hand-side rank class of a bucket: r_f rounded up to a multiple of 16,
+// so that a stream of mixed ranks shares few plans while a plan's r_f capacity
+// (and with it its workspace) stays close to its requests' ranks.
+int rf_class(int r_f) { return (r_f + 15) / 16 * 16; }
 
-int m_cap_of(int max_rank, int rf_cap) { return std::min(2 * max_rank + rf_cap, 256); }
+// Index-set capacity of a bucket's plan.  FP64: 2 max_rank + r_f' (at most
+// 256).  Mixed precision: 64 while the right-hand side leaves room for the
+// index sets (r_f' + 16 <= 64), which keeps the refinement's recompressions in
+// double-float arithmetic on the FP32 pipe; larger r_f' take r_f' + 16.
+int m_cap_of(int max_rank, int rf_cap, int precision) {
+  const int fp64 = std::min(2 * max_rank + rf_cap, 256);
+  if (precision != LRP_MIXED) return fp64;
+  return std::min(std::max(64, rf_cap + 16), std::max(fp64, rf_cap + 2));
+}
 
 struct Request {
   uint64_t ticket = 0;
@@ -132,8 +143,8 @@ namespace {
 // Working-set estimate of one request (FP64 words): both right-hand-side
 // factors, four n x m_cap blocks (cross matrix, two orthogonalisation passes,
 // the factors) and the output factors, per side.
-size_t request_footprint(int64_t n, int r_f, int max_rank) {
-  const int m = m_cap_of(max_rank, rf_class(r_f));
+size_t request_footprint(int64_t n, int r_f, int max_rank, int precision = LRP_FP64) {
+  const int m = m_cap_of(max_rank, rf_class(r_f), precision);
   return (size_t)8 * (size_t)n * (size_t)(2 * r_f + 4 * m + 2 * max_rank);
 }
 
@@ -142,8 +153,10 @@ lrp_opts plan_opts(const BucketKey& k, int B) {
   lrp_default_opts(&o);
   o.precision = k.precision;
   o.max_rhs_rank = k.rf_cap;
-  o.m_cap = m_cap_of(k.max_rank, k.rf_cap);
+  o.m_cap = m_cap_of(k.max_rank, k.rf_cap, k.precision);
   o.batch = B;
+  // each batch is one graph launch whose iteration loops run on the device
+  o.loop_on_device = 1;
   return o;
 }
 
@@ -155,7 +168,7 @@ size_t slot_buffer_bytes(const BucketKey& k) {
 
 size_t warm_record_bytes(const BucketKey& k) {
   const size_t ld = (size_t)((k.n + 31) / 32 * 32);
-  return (size_t)2 * ld * m_cap_of(k.max_rank, k.rf_cap) * sizeof(double) + 4096;
+  return (size_t)2 * ld * m_cap_of(k.max_rank, k.rf_cap, k.precision) * sizeof(double) + 4096;
 }
 
 // Batch slots of a bucket's plan: as many as fit a quarter of the memory cap.
@@ -210,17 +223,27 @@ bool make_room(lrp_server_s* sv, size_t need, const PlanEntry* keep) {
   return true;
 }
 
-PlanEntry* find_plan(lrp_server_s* sv, const BucketKey& k) {
+// An idle plan of bucket k (nullptr if none); *count receives the bucket's plans.
+PlanEntry* find_idle_plan(lrp_server_s* sv, const BucketKey& k, int* count = nullptr) {
+  PlanEntry* idle = nullptr;
+  int c = 0;
   for (PlanEntry* e : sv->plans)
-    if (e->key == k) return e;
-  return nullptr;
+    if (e->key == k) {
+      ++c;
+      if (!e->busy && !idle) idle = e;
+    }
+  if (count) *count = c;
+  return idle;
 }
 
-// The first waiting request whose bucket has no batch running.  Lock held.
+// The first waiting request that can start now: its bucket has an idle plan,
+// or fewer plans than there are lanes (a lane may build another one, so that
+// requests arriving while a batch of their bucket runs need not wait for it).
+// Lock held.
 Request* next_runnable(lrp_server_s* sv) {
   for (Request* r : sv->queue) {
-    PlanEntry* e = find_plan(sv, r->key);
-    if (!e || !e->busy) return r;
+    int count = 0;
+    if (find_idle_plan(sv, r->key, &count) || count < sv->opts.lanes) return r;
   }
   return nullptr;
 }
@@ -356,7 +379,15 @@ void lane_main(lrp_server_s* sv) {
       continue;
     }
     const BucketKey key = head->key;
-    PlanEntry* e = find_plan(sv, key);
+    PlanEntry* e = find_idle_plan(sv, key);
+    if (head->warm_key) {
+      // prefer an idle plan of the bucket that holds the request's warm-start record
+      for (PlanEntry* c : sv->plans)
+        if (c->key == key && !c->busy && c->warm.count(head->warm_key)) {
+          e = c;
+          break;
+        }
+    }
     bool fresh = false;
     if (!e) {
       int B = 1;
@@ -552,7 +583,7 @@ extern "C" lrp_status lrp_submit(lrp_server_t sv, const lrp_request* req, uint64
     if (bytes + slot_buffer_bytes(key) > (size_t)sv->opts.memory_cap_bytes)
       return set_error(LRP_ECAPACITY, "request exceeds the server memory cap");
   }
-  const size_t fp = request_footprint(n, req->r_f, req->max_rank);
+  const size_t fp = request_footprint(n, req->r_f, req->max_rank, req->precision);
   if (fp > (size_t)sv->opts.memory_cap_bytes) return set_error(LRP_ECAPACITY, "request exceeds the server memory cap");
   Request* r = new (std::nothrow) Request();
   if (!r) return set_error(LRP_ENOMEM, "host allocation failed");

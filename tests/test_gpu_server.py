@@ -13,9 +13,12 @@ pytestmark = pytest.mark.gpu
 
 def _bucket_plan(lrp, n, r_f, tol, max_rank, precision):
     # the server's plan for this request's bucket: r_f rounded up to a multiple
-    # of 64, m_cap = min(2 max_rank + that, 256)
-    rfc = (r_f + 63) // 64 * 64
-    return lrp.Plan(n, tol, max_rank, max_rhs_rank=rfc, m_cap=min(2 * max_rank + rfc, 256), precision=precision)
+    # of 16; m_cap = min(2 max_rank + that, 256) in FP64, 64 in mixed precision
+    # while r_f' + 16 <= 64
+    rfc = (r_f + 15) // 16 * 16
+    m64 = min(2 * max_rank + rfc, 256)
+    m_cap = m64 if precision == "fp64" else min(max(64, rfc + 16), max(m64, rfc + 2))
+    return lrp.Plan(n, tol, max_rank, max_rhs_rank=rfc, m_cap=m_cap, precision=precision)
 
 
 def test_mixed_stream_equals_standalone_solves():
