@@ -97,6 +97,7 @@ def parse():
     ap.add_argument("--serve-sweep-requests", type=int, default=4000, help="requests per offered rate")
     ap.add_argument("--serve-sweep-kmax", type=int, default=18)
     ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-frac-fp64", type=float, default=0.2, help="share of FP64 requests in the stream")
     return ap.parse_args()
 
 
@@ -477,7 +478,7 @@ PEAK_SOURCE = {"fp64": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk/SM",
 # DRAM bytes (read + write) per launch from ncu captures of the mixed bench at
 # batch 128, scaled by batch / 128 (the launches' data grow with the slots);
 # a class whose kernel changed since its capture has no entry.
-TRAFFIC_B128 = {("mixed", "gram_df"): (91.1e6, "profiles/k_gram_df_mixed_n4095_batch128.md")}
+TRAFFIC_B128 = {("mixed", "gram_df"): (86.4e6, "profiles/k_gram_df_mixed_n4095_batch128.md")}
 
 
 def class_bound(prec, name, launches, ms, flops, nbytes, hbm_peak):
@@ -511,7 +512,8 @@ def roofline(res, prec, hbm_peak, peak_src, batch):
     tr = TRAFFIC_B128.get((prec, name))
     if tr is not None:
         out["traffic"] = tr[0] * batch / 128
-        out["traffic_source"] = f"{tr[1]} (dram bytes per launch at batch 128, scaled to batch {batch})"
+        out["traffic_source"] = (f"{tr[1]} (dram bytes of a launch with every problem active at batch 128, scaled to "
+                                 f"batch {batch}; the timed average launch includes later iterations with fewer active)")
     return out
 
 
@@ -553,7 +555,7 @@ def serving_stream(args, rank, rate=None, requests=None, kmax=None, lanes=2, cap
             s = dict(specs[j], repeat_of=j, warm_key=j + 1, pert=int(rng.integers(1 << 30)))
         else:
             k = int(rng.integers(8, kmax + 1))
-            mixed = rng.random() < 0.8
+            mixed = rng.random() >= args.serve_frac_fp64
             s = {"n": (1 << k) - 1, "r_f": int(rng.integers(2, 49)), "seed": int(rng.integers(1 << 30)),
                  "prec": "mixed" if mixed else "fp64", "tol": 1e-6 if mixed else 1e-10, "repeat_of": -1,
                  "warm_key": 0, "pert": 0}
@@ -614,8 +616,9 @@ def serving_stream(args, rank, rate=None, requests=None, kmax=None, lanes=2, cap
            "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,
            "status_counts": {lrp.status_string(k): v for k, v in statuses.items()},
            "status_by_class": by_class, "lanes": lanes, "memory_cap_gb": cap_gb,
-           "workload": f"n=2^k-1, k~U{{8..{kmax}}}, r_f~U{{2..48}} Gaussians, 80% mixed/1e-6, "
-                       "20% FP64/1e-10, rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
+           "workload": f"n=2^k-1, k~U{{8..{kmax}}}, r_f~U{{2..48}} Gaussians, "
+                       f"{100 * (1 - args.serve_frac_fp64):.0f}% mixed/1e-6, {100 * args.serve_frac_fp64:.0f}% FP64/1e-10, "
+                       "rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
                        "latency from arrival to completion, plans warmed per bucket beforehand"}
     return rec, kept
 
@@ -973,7 +976,7 @@ def main():
     if args.mixed_sizes <= 0:
         kept_multi = []
     if args.serve_requests > 0:
-        line["serving"], kept = serving_stream(args, rank)
+        line["serving"], kept = serving_stream(args, rank, lanes=args.serve_lanes)
     if not args.no_cpu and world == 1:
         cb, errs = cpu_baseline(rhss, replica_seeds(rank, args.batch), args.cpu_seconds, results,
                                 args.err_check, pool)

@@ -29,7 +29,10 @@
 namespace lrp {
 
 namespace {
-constexpr int CT = 256;  // threads of the core CTAs
+constexpr int CT = 256;  // threads of the Cholesky and stop CTAs
+// Threads of a k_core CTA: 16 warps = 32 half-warps, one Jacobi column pair
+// each, so that a round of up to 64 columns takes one pass; two CTAs per SM.
+constexpr int CTC = 512;
 }  // namespace
 
 // ------------------------------------------------------- work accounting
@@ -250,20 +253,25 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
 }
 
 // Small matrices of k_core live in six regions of L x L doubles: shared memory
-// when |I|, |J| <= kCoreSmemDim (L = kCoreSmemDim), else the slot's global scratch
+// when |I|, |J| <= core_smem_dim (L = that), else the slot's global scratch
 // (L = M).  Region use: R0 Q(I,:) -> compaction work; R1 Z(J,:) -> eta work;
 // R2 pinv work -> V of the core SVD -> V_k(J,:); R3 V of the pinv SVD -> U~;
 // R4 T1 -> V~; R5 core -> U_k(I,:).
-constexpr int kCoreSmemDim = 48;
+// 64 in FP32 (96 KB, two CTAs per SM: index sets of the FP32 iterations reach
+// 50-60 with leverage sampling), 48 in FP64 (110 KB).
 template <typename TC>
-constexpr size_t core_smem_bytes() {
-  return 6 * kCoreSmemDim * kCoreSmemDim * sizeof(TC);
+__host__ __device__ constexpr int core_smem_dim() {
+  return sizeof(TC) == 4 ? 64 : 48;
+}
+template <typename TC>
+__host__ __device__ constexpr size_t core_smem_bytes() {
+  return 6 * (size_t)core_smem_dim<TC>() * core_smem_dim<TC>() * sizeof(TC);
 }
 
 // The small core computes in the precision of the iteration (TC = T): FP64 for
 // the FP64 solve, FP32 for the inner solves of the mixed-precision path.
 template <typename T>
-__global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int parity) {
+__global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, int parity) {
   using TC = T;
   extern __shared__ double core_smem_d[];
   TC* core_smem = reinterpret_cast<TC*>(core_smem_d);
@@ -281,8 +289,9 @@ __global__ void __launch_bounds__(CT) k_core(CoreParams p, CoreBufs<T> b, int pa
     }
     return;
   }
-  const bool in_smem = (q <= kCoreSmemDim && pc <= kCoreSmemDim);
-  const int L = in_smem ? kCoreSmemDim : M;
+  constexpr int kDim = core_smem_dim<T>();
+  const bool in_smem = (q <= kDim && pc <= kDim);
+  const int L = in_smem ? kDim : M;
   const int64_t LL = (int64_t)L * L;
   TC* base = in_smem ? core_smem : reinterpret_cast<TC*>(b.scratch + (int64_t)slot * b.scratch_stride);
   TC* R0 = base + 0 * LL;
@@ -989,7 +998,7 @@ cudaError_t launch_chol(const CoreParams& p, const CoreBufs<T>& b, int sel, int 
 template <typename T>
 cudaError_t launch_core(const CoreParams& p, const CoreBufs<T>& b, int parity, cudaStream_t s) {
   auto kern = k_core<T>;
-  kern<<<p.g.nslots, CT, core_smem_bytes<T>(), s>>>(p, b, parity);
+  kern<<<p.g.nslots, CTC, core_smem_bytes<T>(), s>>>(p, b, parity);
   return cudaGetLastError();
 }
 

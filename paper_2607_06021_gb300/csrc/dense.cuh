@@ -81,7 +81,20 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
   const int npairs = ne / 2;
   const TC tol = (TC)((double)(mr > 1 ? mr : 1) * Eps<TC>::value);
   const TC nu = (TC)(Eps<TC>::value * Eps<TC>::value);
+  // Squared column norms: computed at the start of every sweep, then carried
+  // through its rotations (a rotation that zeroes a.b maps ||a||^2, ||b||^2 to
+  // ||a||^2 - t (a.b), ||b||^2 + t (a.b)), so that a pair needs only its dot
+  // product a.b.
+  __shared__ TC jac_nrm[kMaxM];
+  const int lane32 = tid & 31;
   for (int sweep = 0; sweep < kJacobiSweeps && ne >= 2; ++sweep) {
+    for (int j = warp; j < nc; j += nwarps) {
+      const TC* cj = A + (int64_t)j * lda;
+      TC v = 0;
+      for (int i = lane32; i < mr; i += 32) v = fma(cj[i], cj[i], v);
+      v = warp_sum(v);
+      if (lane32 == 0) jac_nrm[j] = v;
+    }
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
@@ -106,18 +119,11 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
         const bool valid = a >= 0;
         TC* ca = A + (int64_t)(valid ? a : 0) * lda;
         TC* cb = A + (int64_t)(valid ? b : 0) * lda;
-        TC alpha = 0, beta = 0, gamma = 0;
-        if (valid) {
-          for (int i = hl; i < mr; i += 16) {
-            const TC x = ca[i], y = cb[i];
-            alpha = fma(x, x, alpha);
-            beta = fma(y, y, beta);
-            gamma = fma(x, y, gamma);
-          }
-        }
-        alpha = half_warp_sum(alpha);
-        beta = half_warp_sum(beta);
+        TC gamma = 0;
+        if (valid)
+          for (int i = hl; i < mr; i += 16) gamma = fma(ca[i], cb[i], gamma);
         gamma = half_warp_sum(gamma);
+        const TC alpha = valid ? jac_nrm[a] : (TC)0, beta = valid ? jac_nrm[b] : (TC)0;
         if (!valid || gamma == (TC)0 || fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta) || fmin(alpha, beta) <= nu)
           continue;
         const TC zeta = (beta - alpha) / ((TC)2 * gamma);
@@ -138,7 +144,11 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
             vb[i] = s * x + c * y;
           }
         }
-        if (hl == 0) *flag = 1;
+        if (hl == 0) {
+          jac_nrm[a] = alpha - t * gamma;
+          jac_nrm[b] = beta + t * gamma;
+          *flag = 1;
+        }
       }
       __syncthreads();
     }

@@ -169,10 +169,28 @@ __device__ __forceinline__ void dft_small(cplx<TC>* v) {
   }
 }
 
+// Shared-memory index of complex element i: one element of padding after
+// every 128 bytes, so that the strided writes of the early Stockham stages
+// (stride R complex for Ns = 1, runs of 8 for Ns = 8) and the chunked scan
+// reads spread over all banks.
+template <typename TC>
+__device__ __forceinline__ int zpad(int i) {
+  constexpr int P = 128 / (int)sizeof(cplx<TC>);
+  return i + i / P;
+}
+
+// Scalars of one column's shared memory: the padded complex buffer (L + 1
+// elements, the extra one for zpad(L)) and the scan buffer (L + L/32).
+template <typename TC>
+__host__ __device__ constexpr int dst_half_col_scalars(int N) {
+  return 2 * ((N / 2) + (N / 2) / (128 / (int)(2 * sizeof(TC))) + 1) + (N / 2) + (N / 2) / 32;
+}
+
 // One Stockham stage of radix R on the column's L complex values in z: the
 // group's T_c = L/8 threads take butterflies j = t + q T_c (8/R each): inputs
 // z[j + r L/R], twiddles e^{-2 pi i r k / (Ns R)} (k = j mod Ns), outputs
-// z[(j - k) R + k + r Ns].  Reads complete before writes (barrier).
+// z[(j - k) R + k + r Ns] (indices padded by zpad).  Reads complete before
+// writes (barrier).
 template <typename TC, int R>
 __device__ __forceinline__ void stockham_stage(cplx<TC>* z, int L, int Ns, int N, int t, int Tc,
                                                const cplx<TC>* __restrict__ tw) {
@@ -182,7 +200,7 @@ __device__ __forceinline__ void stockham_stage(cplx<TC>* z, int L, int Ns, int N
   for (int q = 0; q < P; ++q) {
     const int j = t + q * Tc;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q][r] = z[j + r * (L / R)];
+    for (int r = 0; r < R; ++r) v[q][r] = z[zpad<TC>(j + r * (L / R))];
   }
   __syncthreads();
   const int step = 2 * N / (Ns * R);  // e^{-2 pi i r k / (Ns R)} = e^{-i pi (r k step) / N}
@@ -197,7 +215,7 @@ __device__ __forceinline__ void stockham_stage(cplx<TC>* z, int L, int Ns, int N
     dft_small<TC, R>(v[q]);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) z[base + r * Ns] = v[q][r];
+    for (int r = 0; r < R; ++r) z[zpad<TC>(base + r * Ns)] = v[q][r];
   }
   __syncthreads();
 }
@@ -271,11 +289,12 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
   const int g = threadIdx.x / Tc, t = threadIdx.x - g * Tc;
   const int slot = blockIdx.y, mat = blockIdx.z;
   const int col = blockIdx.x * cols_per_cta + g;
-  // per column: z (L complex = N scalars), R (L + L/32 scalars); per group 32 scan values
-  const int per_col = N + L + (L >> 5);
+  // per column: z (L complex, padded: N + N/P scalars), R (L + L/32 scalars);
+  // per group 32 scan values
+  const int per_col = dst_half_col_scalars<TC>(N);
   TC* colbuf = reinterpret_cast<TC*>(smem_raw) + (int64_t)g * per_col;
   cplx<TC>* z = reinterpret_cast<cplx<TC>*>(colbuf);
-  TC* Rb = colbuf + N;
+  TC* Rb = colbuf + 2 * zpad<TC>(L);
   TC* wt = reinterpret_cast<TC*>(smem_raw) + (int64_t)cols_per_cta * per_col + 32 * g;
   int ncols = job.fixed_cols;
   if (job.ncols_dev) ncols = job.ncols_dev[slot * job.ncols_stride + mat * job.ncols_mat_stride];
@@ -291,26 +310,40 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
     x += (int64_t)col * job.ld_in[mat * job.nslots + slot];
     y += (int64_t)col * job.ld_out[mat * job.nslots + slot];
   }
+  // scalar u_j / output Y[i] lives in element i/2 (.re for even i, .im for odd)
+  auto zs = [&](int i) -> TC& {
+    cplx<TC>& c = z[zpad<TC>(i >> 1)];
+    return (i & 1) ? c.im : c.re;
+  };
 
   // Pre-processing: u_j and u_{N-j} for j = 1..N/2-1 (x_j = x[j-1]); u_0 = 0,
-  // u_{N/2} = 2 x_{N/2}.  u_j goes to v_{j/2}.re (j even) or .im (j odd).
-  TC* zs = colbuf;  // z as scalars: zs[j] = u_j
+  // u_{N/2} = 2 x_{N/2}.  The thread's 16 loads are issued before any use.
   const TC half = TC(0.5);
-  for (int j = 1 + t; j < L; j += Tc) {
-    TC xa = TC(0), xb = TC(0);
-    if (live) {
-      xa = TC(x[j - 1]);
-      xb = TC(x[N - j - 1]);
+  TC xa[8], xb[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = 1 + t + q * Tc;
+    xa[q] = TC(0);
+    xb[q] = TC(0);
+    if (live && j < L) {
+      xa[q] = TC(x[j - 1]);
+      xb[q] = TC(x[N - j - 1]);
     }
-    const TC sj = TC(0) - tw_load(tw, j).im;  // sin(pi j / N)
-    const TC a = xa + xb, b = xa - xb;
-    zs[j] = sj * a + half * b;
-    zs[N - j] = sj * a - half * b;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = 1 + t + q * Tc;
+    if (j < L) {
+      const TC sj = TC(0) - tw_load(tw, j).im;  // sin(pi j / N)
+      const TC a = xa[q] + xb[q], b = xa[q] - xb[q];
+      zs(j) = sj * a + half * b;
+      zs(N - j) = sj * a - half * b;
+    }
   }
   if (t == 0) {
-    zs[0] = TC(0);
+    zs(0) = TC(0);
     const TC xm = live ? TC(x[L - 1]) : TC(0);
-    zs[L] = xm + xm;
+    zs(L) = xm + xm;
   }
   __syncthreads();
 
@@ -325,7 +358,7 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = t + e * Tc;
-    const cplx<TC> Vk = z[k], Vm = z[(L - k) & (L - 1)];
+    const cplx<TC> Vk = z[zpad<TC>(k)], Vm = z[zpad<TC>((L - k) & (L - 1))];
     const TC Er = (Vk.re + Vm.re) * half, Ei = (Vk.im - Vm.im) * half;
     const TC Or = (Vk.im + Vm.im) * half, Oi = (Vm.re - Vk.re) * half;  // (Vk - conj Vm) / (2i)
     const cplx<TC> w = tw_load(tw, 2 * k);                                // e^{-2 pi i k / N}
@@ -333,11 +366,11 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
     Ir[e] = TC(0) - (Ei + (w.re * Oi + w.im * Or));
   }
   __syncthreads();
-  TC* Y = zs;  // staged outputs: Y[k' - 1] = S_{k'}
+  // staged outputs: Y(k' - 1) = S_{k'}, in the scalar slots of z
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = t + e * Tc;
-    if (k > 0) Y[2 * k - 1] = Ir[e];
+    if (k > 0) zs(2 * k - 1) = Ir[e];
     Rb[k + (k >> 5)] = (k == 0) ? Rr[e] * half : Rr[e];
   }
   __syncthreads();
@@ -353,11 +386,11 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
   }
   const TC before = group_exclusive_scan(run, t, Tc, wt);
 #pragma unroll
-  for (int e = 0; e < 8; ++e) Y[2 * (8 * t + e)] = before + acc[e];
+  for (int e = 0; e < 8; ++e) zs(2 * (8 * t + e)) = before + acc[e];
   __syncthreads();
   if (live) {
     const TC scale = TC(sqrt(2.0 / (double)N));
-    for (int i = t; i < n; i += Tc) y[i] = (TOut)(scale * Y[i]);
+    for (int i = t; i < n; i += Tc) y[i] = (TOut)(scale * zs(i));
   }
 }
 
@@ -571,12 +604,11 @@ size_t dst_temp_bytes(int64_t n, bool fp64) {
   return dst_smem_supported(n, fp64) ? 0 : (size_t)(n + 1) * (fp64 ? 16 : 8);
 }
 
-// Shared memory of k_dst1_half: per column N + L + L/32 values, plus 32 scan
-// values per column group.
+// Shared memory of k_dst1_half: per column dst_half_col_scalars values, plus
+// 32 scan values per column group.
 template <typename TC>
 static size_t dst_half_smem(int N, int cols_per_cta) {
-  const int L = N / 2;
-  return sizeof(TC) * ((size_t)cols_per_cta * (N + L + L / 32) + 32 * (size_t)cols_per_cta);
+  return sizeof(TC) * ((size_t)cols_per_cta * dst_half_col_scalars<TC>(N) + 32 * (size_t)cols_per_cta);
 }
 
 template <typename TIn, typename TOut, typename TC>

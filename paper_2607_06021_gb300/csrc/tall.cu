@@ -113,14 +113,22 @@ __global__ void __launch_bounds__(NT) k_cross(TallGeom g, const SolveState* __re
       }
       __syncthreads();
       if (live) {
-        for (int kk = 0; kk < kn; ++kk) {
-          const T av = Fs[(int64_t)(k0 + kk) * g.ld + row];
+        // the row's values of 8 consecutive k are loaded before their FMAs
+        for (int k8 = 0; k8 < kn; k8 += 8) {
+          T av[8];
 #pragma unroll
-          for (int q = 0; q < XQ; q += 4) {
-            T b[4];
-            ld4<T>(&Bs[kk][q], b);
+          for (int u = 0; u < 8; ++u) av[u] = (k8 + u < kn) ? Fs[(int64_t)(k0 + k8 + u) * g.ld + row] : T(0);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[q + t] = fma(av, b[t], acc[q + t]);
+          for (int u = 0; u < 8; ++u) {
+            if (k8 + u >= kn) break;
+#pragma unroll
+            for (int q = 0; q < XQ; q += 4) {
+              if (q >= qn) break;  // the block's last columns (uniform across the CTA)
+              T b[4];
+              ld4<T>(&Bs[k8 + u][q], b);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) acc[q + t] = fma(av[u], b[t], acc[q + t]);
+            }
           }
         }
       }
