@@ -268,6 +268,17 @@ __host__ __device__ constexpr size_t core_smem_bytes() {
   return 6 * (size_t)core_smem_dim<TC>() * core_smem_dim<TC>() * sizeof(TC);
 }
 
+// Jacobi SVD of a core matrix: FP32 cores take the register form, whose column
+// exchange uses two free tiles (`free2`, 2 L^2 values); FP64 the shared-memory form.
+template <typename TC>
+__device__ __forceinline__ void core_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv, double* sig, int* flag,
+                                            TC* free2, int64_t free_elems) {
+  if constexpr (sizeof(TC) == 4)
+    blk_jacobi_f32(A, lda, mr, nc, V, ldv, sig, flag, free2, (int)(free_elems < (1 << 30) ? free_elems : (1 << 30)));
+  else
+    blk_jacobi<TC>(A, lda, mr, nc, V, ldv, sig, flag);
+}
+
 // The small core computes in the precision of the iteration (TC = T): FP64 for
 // the FP64 solve, FP32 for the inner solves of the mixed-precision path.
 template <typename T>
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       W1[(int64_t)j * L + i] = QI[(int64_t)j * L + i];
     }
     __syncthreads();
-    blk_jacobi(W1, L, q, pc, V1, L, sig1, &flag);
+    core_jacobi(W1, L, q, pc, V1, L, sig1, &flag, R4, 2 * LL);  // R4, R5 free
     double smax = 0.0;
     for (int j = tid; j < pc; j += nt) smax = fmax(smax, sig1[j]);
     smax = block_max(smax, red);
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       Mt[(int64_t)i * L + c] = s;
     }
     __syncthreads();
-    blk_jacobi(Mt, L, q, pc, V2, L, sig2, &flag);
+    core_jacobi(Mt, L, q, pc, V2, L, sig2, &flag, R3, 2 * LL);  // R3 (V1), R4 (T1) free
     nsv = pc;
   } else {
     // Mirror: Z(J,:) = U2 S2 V2^T (pc x q); M = R_C U2 S2^+ V2^T (pc x q), tall.
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       W1[(int64_t)j * L + i] = ZJ[(int64_t)j * L + i];
     }
     __syncthreads();
-    blk_jacobi(W1, L, pc, q, V1, L, sig1, &flag);
+    core_jacobi(W1, L, pc, q, V1, L, sig1, &flag, R4, 2 * LL);
     double smax = 0.0;
     for (int j = tid; j < q; j += nt) smax = fmax(smax, sig1[j]);
     smax = block_max(smax, red);
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       Mt[(int64_t)bb * L + i] = s;
     }
     __syncthreads();
-    blk_jacobi(Mt, L, pc, q, V2, L, sig2, &flag);
+    core_jacobi(Mt, L, pc, q, V2, L, sig2, &flag, R3, 2 * LL);
     nsv = q;
   }
   blk_sort_desc(sig2, nsv, perm);
@@ -466,60 +477,73 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
     VJ[(int64_t)t * L + a] = s;
   }
   __syncthreads();
-  TC* WK = R0;  // Q(I,:) no longer needed
-  TC* WE = R1;  // Z(J,:) no longer needed
-
   // Redundancy removal: keep I_l iff |R_R(l,l)| >= tau max|diag R_R|, J_l likewise with R_C.
   double mR = 0.0, mC = 0.0;
   for (int l = tid; l < q; l += nt) mR = fmax(mR, fabs(RR[(int64_t)l * M + l]));
   for (int l = tid; l < pc; l += nt) mC = fmax(mC, fabs(RC[(int64_t)l * M + l]));
   mR = block_max(mR, red);
   mC = block_max(mC, red);
+  __shared__ int permJ[kMaxM];
+  __shared__ int kept[2];
   for (int l = tid; l < q; l += nt) keep[l] = (mR > 0.0 && fabs(RR[(int64_t)l * M + l]) >= p.redundancy * mR) ? 1 : 0;
+  for (int l = tid; l < pc; l += nt)
+    permJ[l] = (mC > 0.0 && fabs(RC[(int64_t)l * M + l]) >= p.redundancy * mC) ? 1 : 0;
   __syncthreads();
+  // Compaction of each set in its order (perm / permJ: source row of U_k(I,:) / V_k(J,:)).
   if (tid == 0) {
     int w = 0;
     for (int l = 0; l < q; ++l) {
       if (keep[l]) {
         I[w] = I[l];
-        perm[w] = l;  // source row of U_k(I,:)
-        ++w;
-      }
-    }
-    flag = w;
-  }
-  __syncthreads();
-  const int qn = flag;
-  for (int e = tid; e < qn * r; e += nt) {
-    const int a = e % qn, t = e / qn;
-    WK[(int64_t)t * L + a] = UI[(int64_t)t * L + perm[a]];
-  }
-  __syncthreads();
-  __shared__ double vec_d[2 * kMaxM];
-  TC* vec = reinterpret_cast<TC*>(vec_d);  // 2 k values, k <= kMaxM
-  const double e1 = blk_inv_smin(WK, L, qn, r, WE, R3, L, vec, &flag);
-  for (int l = tid; l < pc; l += nt) keep[l] = (mC > 0.0 && fabs(RC[(int64_t)l * M + l]) >= p.redundancy * mC) ? 1 : 0;
-  __syncthreads();
-  if (tid == 0) {
-    int w = 0;
-    for (int l = 0; l < pc; ++l) {
-      if (keep[l]) {
-        J[w] = J[l];
         perm[w] = l;
         ++w;
       }
     }
-    flag = w;
+    kept[0] = w;
+  }
+  if (tid == (nt > 32 ? 32 : 0)) {
+    int w = 0;
+    for (int l = 0; l < pc; ++l) {
+      if (permJ[l]) {
+        J[w] = J[l];
+        permJ[w] = l;
+        ++w;
+      }
+    }
+    kept[1] = w;
   }
   __syncthreads();
-  const int pn = flag;
+  const int qn = kept[0], pn = kept[1];
+  // U_k(I,:) and V_k(J,:) on the reduced sets -> R0, R1; their Grams -> R3, R4.
+  TC* WI = R0;
+  TC* WJ = R1;
+  for (int e = tid; e < qn * r; e += nt) {
+    const int a = e % qn, t = e / qn;
+    WI[(int64_t)t * L + a] = UI[(int64_t)t * L + perm[a]];
+  }
   for (int e = tid; e < pn * r; e += nt) {
     const int a = e % pn, t = e / pn;
-    WK[(int64_t)t * L + a] = VJ[(int64_t)t * L + perm[a]];
+    WJ[(int64_t)t * L + a] = VJ[(int64_t)t * L + permJ[a]];
   }
   __syncthreads();
-  // eta_1 = ||U_k(I,:)^+||_2, eta_2 = ||V_k(J,:)^+||_2 with the reduced sets.
-  const double e2 = blk_inv_smin(WK, L, pn, r, WE, R3, L, vec, &flag);
+  const int kI = blk_gram_upper(WI, L, qn, r, R3, L);
+  const int kJ = blk_gram_upper(WJ, L, pn, r, R4, L);
+  __syncthreads();
+  // eta_1 = ||U_k(I,:)^+||_2 (warp 0) and eta_2 = ||V_k(J,:)^+||_2 (warp 1) at the
+  // same time; R5 / R2 (the gathers' sources) become the inverse factors.
+  __shared__ TC vec_w[2][2 * kMaxM];
+  __shared__ double eta_w[2];
+  const int warp = tid >> 5, nw = nt >> 5;
+  if (warp == 0) {
+    const double e = warp_inv_smin(R3, R5, L, kI, vec_w[0]);
+    if ((tid & 31) == 0) eta_w[0] = e;
+  }
+  if (warp == (nw > 1 ? 1 : 0)) {
+    const double e = warp_inv_smin(R4, R2, L, kJ, vec_w[1]);
+    if ((tid & 31) == 0) eta_w[1] = e;
+  }
+  __syncthreads();
+  const double e1 = eta_w[0], e2 = eta_w[1];
   double snorm2 = 0.0;
   for (int t = tid; t < r; t += nt) snorm2 += sig_out[t] * sig_out[t];
   snorm2 = block_sum(snorm2, red);

@@ -1,5 +1,6 @@
-// Block-cooperative small dense routines (one CTA): one-sided Jacobi SVD,
-// descending sort permutation, smallest singular value.
+// Small dense routines of the per-problem cores: one-sided Jacobi SVD and a
+// descending sort permutation (block-cooperative), the Gram of a small matrix
+// (block) and ||A^+||_2 from it (one warp).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -39,12 +40,119 @@ __device__ __forceinline__ TC half_warp_sum(TC v) {
 // (mutually orthogonal), sig[j] = ||A(:,j)|| and, if V != nullptr,
 // A_in = A_out V^T with V orthogonal.
 // A is scaled by a power of two to ||A||_F in [1/2, 1) for the sweeps (exact;
-// undone on exit), so that squared column norms cannot underflow in FP32.  A
+// undone on exit), so that squared column norms cannot underflow in FP32.  In
+// FP64 a round is split in three phases (the half-warps' dot products; one
+// lane per pair of warp 0 computing every rotation; the rotations), because the
+// FP64 pipe charges a warp instruction for all 32 lanes whatever its mask: one
+// warp then issues the rotation arithmetic of the whole round.  A
 // pair is left alone once |a_i . a_j| <= mr eps ||a_i|| ||a_j|| (rounding noise)
 // or one of its columns is below eps ||A||_F: such columns lie below every
 // cutoff applied to the singular values (the pseudoinverse's
 // max(|I|,|J|) eps sigma_1, the tail rules), and rotating them only chases
 // rounding noise.
+// Pair k of round rnd of the cyclic schedule over ne (even) columns, a < b;
+// a = b = -1 for a pair with the padding column.
+__device__ __forceinline__ void jacobi_pair(int rnd, int k, int ne, int nc, int& a, int& b) {
+  if (k == 0) {
+    a = rnd % (ne - 1);
+    b = ne - 1;
+  } else {
+    a = (rnd + k) % (ne - 1);
+    b = (rnd + ne - 1 - k) % (ne - 1);
+  }
+  if (a >= nc || b >= nc) a = b = -1;
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// One round of blk_jacobi in three phases (FP64): dot products a.b by
+// half-warps; warp 0 tests each pair (lane per pair) and computes its rotation
+// (t from zeta = (||b||^2 - ||a||^2) / (2 a.b), c = 1/sqrt(1 + t^2) by reciprocal
+// square roots) and the carried norms; the half-warps rotate.
+template <typename TC>
+__device__ inline void jacobi_round_split(TC* A, int lda, int mr, int nc, TC* V, int ldv, int rnd, int ne, TC tol, TC nu,
+                                          TC* jac_nrm, int* flag) {
+  const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int half = (tid >> 4) & 1, hl = tid & 15;
+  const int npairs = ne / 2;
+  __shared__ TC jac_g[kMaxM / 2];
+  __shared__ TC jac_c[kMaxM / 2];
+  __shared__ TC jac_s[kMaxM / 2];
+  for (int kw = warp; 2 * kw < npairs; kw += nwarps) {
+    const int k = 2 * kw + half;
+    int a = -1, b = -1;
+    if (k < npairs) jacobi_pair(rnd, k, ne, nc, a, b);
+    const bool valid = a >= 0;
+    const TC* ca = A + (int64_t)(valid ? a : 0) * lda;
+    const TC* cb = A + (int64_t)(valid ? b : 0) * lda;
+    TC gamma = 0;
+    if (valid)
+      for (int i = hl; i < mr; i += 16) gamma = fma(ca[i], cb[i], gamma);
+    gamma = half_warp_sum(gamma);
+    if (k < npairs && hl == 0) jac_g[k] = gamma;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const TC tol2 = tol * tol;
+    for (int k = tid; k < npairs; k += 32) {
+      int a = -1, b = -1;
+      jacobi_pair(rnd, k, ne, nc, a, b);
+      TC c = 1, s = 0;
+      if (a >= 0) {
+        const TC gamma = jac_g[k];
+        const TC alpha = jac_nrm[a], beta = jac_nrm[b];
+        if (!(gamma == (TC)0 || gamma * gamma <= tol2 * alpha * beta || fmin(alpha, beta) <= nu)) {
+          const TC zeta = (beta - alpha) / ((TC)2 * gamma);
+          TC t;
+          if (fabs(zeta) > (TC)1e150) {
+            t = (TC)0.5 / zeta;
+          } else {
+            const TC w = (TC)1 + zeta * zeta;
+            t = copysign((TC)1, zeta) / (fabs(zeta) + w * rsqrt(w));
+          }
+          c = rsqrt((TC)1 + t * t);
+          s = c * t;
+          jac_nrm[a] = alpha - t * gamma;
+          jac_nrm[b] = beta + t * gamma;
+          *flag = 1;
+        }
+      }
+      jac_c[k] = c;
+      jac_s[k] = s;
+    }
+  }
+  __syncthreads();
+  for (int kw = warp; 2 * kw < npairs; kw += nwarps) {
+    const int k = 2 * kw + half;
+    if (k >= npairs) continue;
+    const TC s = jac_s[k];
+    if (s == (TC)0) continue;
+    const TC c = jac_c[k];
+    int a = -1, b = -1;
+    jacobi_pair(rnd, k, ne, nc, a, b);
+    TC* ca = A + (int64_t)a * lda;
+    TC* cb = A + (int64_t)b * lda;
+    for (int i = hl; i < mr; i += 16) {
+      const TC x = ca[i], y = cb[i];
+      ca[i] = c * x - s * y;
+      cb[i] = s * x + c * y;
+    }
+    if (V) {
+      TC* va = V + (int64_t)a * ldv;
+      TC* vb = V + (int64_t)b * ldv;
+      for (int i = hl; i < nc; i += 16) {
+        const TC x = va[i], y = vb[i];
+        va[i] = c * x - s * y;
+        vb[i] = s * x + c * y;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <typename TC>
 __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv, double* sig, int* flag) {
   const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -98,6 +206,10 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
+      if constexpr (sizeof(TC) == 8) {
+        jacobi_round_split<TC>(A, lda, mr, nc, V, ldv, rnd, ne, tol, nu, jac_nrm, flag);
+        continue;
+      }
       for (int kw = warp; 2 * kw < npairs; kw += nwarps) {
         const int k = 2 * kw + half;
         int a = -1, b = -1;
@@ -172,6 +284,204 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
   __syncthreads();
 }
 
+// One-sided Jacobi SVD in FP32 with the columns in registers: the same
+// round-robin pair ordering, rotations, stopping test and Frobenius scaling as
+// blk_jacobi, one warp per column pair.  A column is its mr rows of A followed by
+// its nc rows of V (V starts as the identity), NV values per lane
+// (mr + nc <= 32 NV); a warp holds the pairs k = warp (and k = warp + nwarps with
+// NS = 2), P = ne/2 <= NS nwarps pairs.  The ordering moves each pair's first column to pair k-1
+// (pair 0's to pair 1's second place) and each second column to pair k+1 (the
+// last pair's into its own first place, pair 0's second column stays), which
+// reproduces the cyclic schedule (a, b) = ((rnd + k) mod (ne-1), (rnd - k)
+// mod (ne-1)), pair 0 = (rnd mod (ne-1), ne-1); the columns move through `buf`
+// (2P columns of 32 NV floats, twice that with `dbl`: alternate halves and one
+// barrier per round, else two barriers per round).  After each sweep (ne-1
+// rounds, the schedule's period) the columns are back in their starting pairs.
+template <int NV, int NS>
+__device__ inline void blk_jacobi_reg(float* A, int lda, int mr, int nc, float* V, int ldv, double* sig, float* buf,
+                                      bool dbl, double* jr_red, float* jr_nrm) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  const int ne = nc + (nc & 1), P = ne >> 1, R = ne - 1, rows = mr + nc;
+  constexpr int S = 32 * NV;
+  double f2 = 0.0;
+  for (int e = tid; e < mr * nc; e += blockDim.x) {
+    const double v = (double)A[(int64_t)(e / mr) * lda + (e % mr)];
+    f2 = fma(v, v, f2);
+  }
+  f2 = warp_sum(f2);
+  if (lane == 0) jr_red[warp] = f2;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < nwarps ? jr_red[tid] : 0.0;
+    v = warp_sum(v);
+    if (tid == 0) jr_red[0] = v;
+  }
+  __syncthreads();
+  const double fro2 = jr_red[0];
+  int ex = 0;
+  if (fro2 > 0.0) frexp(sqrt(fro2), &ex);
+  const float down = (float)ldexp(1.0, -ex), up = (float)ldexp(1.0, ex);
+  float x[NS][NV], y[NS][NV], al[NS], be[NS];
+  auto colval = [&](int c, int e) -> float {
+    if (c >= nc || e >= rows) return 0.f;
+    if (e < mr) return A[(int64_t)c * lda + e] * down;
+    return (e - mr == c) ? 1.f : 0.f;
+  };
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const int k = warp + j * nwarps;
+    const int ia = k, ib = (k == 0) ? ne - 1 : ne - 1 - k;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int e = lane + 32 * v;
+      x[j][v] = (k < P) ? colval(ia, e) : 0.f;
+      y[j][v] = (k < P) ? colval(ib, e) : 0.f;
+    }
+  }
+  const float tol = (float)((double)(mr > 1 ? mr : 1) * Eps<float>::value);
+  const float tol2 = tol * tol;
+  const float nu = (float)(Eps<float>::value * Eps<float>::value);
+  int par = 0;
+  for (int sweep = 0; sweep < kJacobiSweeps && ne >= 2; ++sweep) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      float sa = 0.f, sb = 0.f;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (lane + 32 * v < mr) {
+          sa = fmaf(x[j][v], x[j][v], sa);
+          sb = fmaf(y[j][v], y[j][v], sb);
+        }
+      al[j] = warp_sum(sa);
+      be[j] = warp_sum(sb);
+    }
+    int rot = 0;
+    for (int rnd = 0; rnd < R; ++rnd) {
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int k = warp + j * nwarps;
+        if (k >= P) continue;  // warp-uniform
+        float g = 0.f;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (lane + 32 * v < mr) g = fmaf(x[j][v], y[j][v], g);
+        g = warp_sum(g);
+        const float a = al[j], b = be[j];
+        if (g == 0.f || g * g <= tol2 * a * b || fminf(a, b) <= nu) continue;
+        const float zeta = (b - a) / (2.f * g);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = 1.f / sqrtf(1.f + t * t);
+        const float sn = c * t;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float xv = x[j][v], yv = y[j][v];
+          x[j][v] = c * xv - sn * yv;
+          y[j][v] = sn * xv + c * yv;
+        }
+        al[j] = a - t * g;
+        be[j] = b + t * g;
+        rot = 1;
+      }
+      if (P > 1) {
+        float* bw = buf + (dbl ? par : 0) * (2 * P * S);
+        float* nw = jr_nrm + (dbl ? par : 0) * (2 * P);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const int k = warp + j * nwarps;
+          if (k >= P) continue;
+          const int da = (k >= 1) ? 2 * (k - 1) : 3;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) bw[da * S + lane + 32 * v] = x[j][v];
+          if (lane == 0) nw[da] = al[j];
+          if (k >= 1) {
+            const int db = (k <= P - 2) ? 2 * (k + 1) + 1 : 2 * (P - 1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) bw[db * S + lane + 32 * v] = y[j][v];
+            if (lane == 0) nw[db] = be[j];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const int k = warp + j * nwarps;
+          if (k >= P) continue;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) x[j][v] = bw[2 * k * S + lane + 32 * v];
+          al[j] = nw[2 * k];
+          if (k >= 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) y[j][v] = bw[(2 * k + 1) * S + lane + 32 * v];
+            be[j] = nw[2 * k + 1];
+          }
+        }
+        if (dbl)
+          par ^= 1;
+        else
+          __syncthreads();
+      }
+    }
+    if (!__syncthreads_or(rot)) break;
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const int k = warp + j * nwarps;
+    if (k >= P) continue;
+    const int ia = k, ib = (k == 0) ? ne - 1 : ne - 1 - k;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int col = side ? ib : ia;
+      float s2 = 0.f;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int e = lane + 32 * v;
+        const float val = side ? y[j][v] : x[j][v];
+        if (e < mr) {
+          const float u = val * up;
+          s2 = fmaf(u, u, s2);
+          if (col < nc) A[(int64_t)col * lda + e] = u;
+        } else if (e < rows && col < nc) {
+          V[(int64_t)col * ldv + (e - mr)] = val;
+        }
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0 && col < nc) sig[col] = sqrt((double)s2);
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 one-sided Jacobi SVD (blk_jacobi's contract, V required): the register
+// form when the sizes fit it (mr + nc <= 128, ne/2 <= 2 warps per pair slot,
+// `buf_floats` covering one set of 2P columns), else blk_jacobi<float>.
+__device__ inline void blk_jacobi_f32(float* A, int lda, int mr, int nc, float* V, int ldv, double* sig, int* flag,
+                                      float* buf, int buf_floats) {
+  const int ne = nc + (nc & 1), P = ne >> 1, rows = mr + nc;
+  const int nv = (rows + 31) >> 5;
+  const bool fits = nc >= 1 && P <= 2 * (int)(blockDim.x >> 5) && P <= 32 && nv <= 4 && 2 * P * 32 * nv <= buf_floats;
+  if (!fits) {
+    blk_jacobi<float>(A, lda, mr, nc, V, ldv, sig, flag);
+    return;
+  }
+  const bool dbl = 2 * (2 * P * 32 * nv) <= buf_floats;
+  __shared__ double jr_red[32];     // block reduction of ||A||_F^2
+  __shared__ float jr_nrm[2 * 64];  // carried squared norms of the moving columns
+  if (P <= (int)(blockDim.x >> 5)) {
+    switch (nv) {
+      case 1: blk_jacobi_reg<1, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      case 2: blk_jacobi_reg<2, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      case 3: blk_jacobi_reg<3, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      default: blk_jacobi_reg<4, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    }
+  } else {
+    switch (nv) {
+      case 1: blk_jacobi_reg<1, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      case 2: blk_jacobi_reg<2, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      case 3: blk_jacobi_reg<3, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+      default: blk_jacobi_reg<4, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    }
+  }
+}
+
 // perm[t] = index of the t-th largest of v[0..n) (ties to the lower index).
 __device__ inline void blk_sort_desc(const double* v, int n, int* perm) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -186,45 +496,14 @@ __device__ inline void blk_sort_desc(const double* v, int n, int* perm) {
   __syncthreads();
 }
 
-// Smallest nonzero-rank singular value of the mr x nc matrix: sigma_min(A) for a
-// tall A, and the smallest of the mr singular values of a wide A, so that
-// 1/result = ||A^+||_2 for a full-rank A of either shape.
+// G = A^T A (mr >= nc) or A A^T (mr < nc), upper triangle, for the mr x nc
+// matrix A (col-major, lda); k = min(mr, nc) is returned.  Block-cooperative:
+// the caller synchronises before G is read.
 template <typename TC>
-__device__ inline double blk_smin(const TC* src, int lds, int mr, int nc, TC* work, int ldw, double* sig, int* flag) {
-  if (nc == 0 || mr == 0) return 0.0;
-  const bool wide = mr < nc;
-  const int rows = wide ? nc : mr, cols = wide ? mr : nc;
-  for (int e = threadIdx.x; e < mr * nc; e += blockDim.x) {
-    const int i = e % mr, j = e / mr;
-    const TC v = src[(int64_t)j * lds + i];
-    if (wide)
-      work[(int64_t)i * ldw + j] = v;
-    else
-      work[(int64_t)j * ldw + i] = v;
-  }
-  __syncthreads();
-  blk_jacobi<TC>(work, ldw, rows, cols, nullptr, 0, sig, flag);
-  __shared__ double red[32];
-  double mn = 1e308;
-  for (int j = threadIdx.x; j < cols; j += blockDim.x) mn = fmin(mn, sig[j]);
-  mn = -block_max(-mn, red);
-  return mn;
-}
-
-// ||A^+||_2 for the mr x nc matrix A (1 / its smallest nonzero-rank singular
-// value), from the Gram of the smaller side: G = A^T A (mr >= nc) or A A^T,
-// Cholesky G = R^T R, G^{-1} = R^{-1} R^{-T}, and power iteration on G^{-1}
-// (lambda_max(G^{-1}) = 1 / sigma_min^2).  Returns +inf when G is numerically
-// singular.  G, Ri are k x k work areas (k = min(mr, nc)), vec holds 2k values.
-template <typename TC>
-__device__ inline double blk_inv_smin(const TC* A, int lda, int mr, int nc, TC* G, TC* Ri, int ldg, TC* vec,
-                                      int* flag) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+__device__ inline int blk_gram_upper(const TC* A, int lda, int mr, int nc, TC* G, int ldg) {
   const bool tall = mr >= nc;
   const int k = tall ? nc : mr, len = tall ? mr : nc;
-  __shared__ double red_i[32];
-  if (k == 0) return INFINITY;
-  for (int e = tid; e < k * k; e += nt) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e % k, j = e / k;
     if (i > j) continue;
     TC s = 0;
@@ -235,33 +514,36 @@ __device__ inline double blk_inv_smin(const TC* A, int lda, int mr, int nc, TC* 
     }
     G[(int64_t)j * ldg + i] = s;
   }
-  if (tid == 0) *flag = 0;
-  __syncthreads();
-  // Cholesky (upper R in the upper triangle of G).
+  return k;
+}
+
+// ||A^+||_2 = 1 / sigma_min(A) from the k x k Gram G of the smaller side (upper
+// triangle filled by blk_gram_upper), by ONE warp (warp-synchronous; the other
+// warps of the block are free): Cholesky G = R^T R in place, Ri = R^{-1} by back
+// substitution, and power iteration on G^{-1} = Ri Ri^T, whose largest
+// eigenvalue is 1 / sigma_min^2, to a relative change of 1e-3 (at least 5 and at
+// most 30 steps).  Returns +inf when G is numerically singular (a pivot not > 0)
+// and for k = 0.  vec holds 2k values.
+template <typename TC>
+__device__ inline double warp_inv_smin(TC* G, TC* Ri, int ldg, int k, TC* vec) {
+  const int lane = threadIdx.x & 31;
+  if (k == 0) return INFINITY;
   for (int j = 0; j < k; ++j) {
     const TC d = G[(int64_t)j * ldg + j];
-    const bool bad = !(d > (TC)0);
-    if (bad) {
-      if (tid == 0) *flag = 1;
-      break;
-    }
+    if (!(d > (TC)0)) return INFINITY;  // every lane reads the same pivot
     const TC rjj = sqrt(d);
-    __syncthreads();
-    for (int l = j + 1 + tid; l < k; l += nt) G[(int64_t)l * ldg + j] /= rjj;
-    if (tid == 0) G[(int64_t)j * ldg + j] = rjj;
-    __syncthreads();
+    for (int l = j + 1 + lane; l < k; l += 32) G[(int64_t)l * ldg + j] /= rjj;
+    __syncwarp();
+    if (lane == 0) G[(int64_t)j * ldg + j] = rjj;
     const int t = k - j - 1;
-    for (int e = tid; e < t * t; e += nt) {
+    for (int e = lane; e < t * t; e += 32) {
       const int a = e % t, b = e / t;
       if (a > b) continue;
       G[(int64_t)(j + 1 + b) * ldg + (j + 1 + a)] -= G[(int64_t)(j + 1 + a) * ldg + j] * G[(int64_t)(j + 1 + b) * ldg + j];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  __syncthreads();
-  if (*flag) return INFINITY;
-  // Ri = R^{-1} (upper), column l by back substitution.
-  for (int l = tid; l < k; l += nt) {
+  for (int l = lane; l < k; l += 32) {
     for (int i = k - 1; i > l; --i) Ri[(int64_t)l * ldg + i] = (TC)0;
     for (int i = l; i >= 0; --i) {
       TC s = (i == l) ? (TC)1 : (TC)0;
@@ -269,38 +551,35 @@ __device__ inline double blk_inv_smin(const TC* A, int lda, int mr, int nc, TC* 
       Ri[(int64_t)l * ldg + i] = s / G[(int64_t)i * ldg + i];
     }
   }
-  __syncthreads();
-  // Power iteration on G^{-1} = Ri Ri^T: x <- Ri (Ri^T x).
   TC* x = vec;
   TC* y = vec + k;
-  for (int i = tid; i < k; i += nt) x[i] = (TC)1 / sqrt((TC)k) * (TC)(1 + (i & 1));
-  __syncthreads();
+  for (int i = lane; i < k; i += 32) x[i] = (TC)1 / sqrt((TC)k) * (TC)(1 + (i & 1));
+  __syncwarp();
   double lam = 0.0;
   for (int it = 0; it < 30; ++it) {
-    for (int i = tid; i < k; i += nt) {  // y = Ri^T x
+    for (int i = lane; i < k; i += 32) {  // y = Ri^T x
       TC s = 0;
       for (int c = 0; c <= i; ++c) s = fma(Ri[(int64_t)i * ldg + c], x[c], s);
       y[i] = s;
     }
-    __syncthreads();
-    double nrm = 0.0;
-    for (int i = tid; i < k; i += nt) {  // x_new = Ri y
+    __syncwarp();
+    double nrm = 0.0, xx = 0.0;
+    for (int i = lane; i < k; i += 32) {  // ||Ri y||^2 and ||x||^2
       TC s = 0;
       for (int c = i; c < k; ++c) s = fma(Ri[(int64_t)c * ldg + i], y[c], s);
       nrm += (double)s * (double)s;
+      xx += (double)x[i] * (double)x[i];
     }
-    nrm = block_sum(nrm, red_i);
+    nrm = warp_sum(nrm);
+    xx = warp_sum(xx);
     const double prev = lam;
-    double xx = 0.0;
-    for (int i = tid; i < k; i += nt) xx += (double)x[i] * (double)x[i];
-    xx = block_sum(xx, red_i);
     lam = sqrt(nrm / xx);  // ||G^{-1} x|| / ||x|| -> lambda_max(G^{-1})
-    for (int i = tid; i < k; i += nt) {
+    for (int i = lane; i < k; i += 32) {  // x <- Ri y / ||Ri y||
       TC s = 0;
       for (int c = i; c < k; ++c) s = fma(Ri[(int64_t)c * ldg + i], y[c], s);
       x[i] = s / (TC)sqrt(nrm);
     }
-    __syncthreads();
+    __syncwarp();
     if (it > 3 && fabs(lam - prev) <= 1e-3 * lam) break;
   }
   return sqrt(lam);

@@ -165,9 +165,10 @@ __global__ void k_assemble_residual(RefineArgs a) {
 // an FP32 solve, and FP64 keeps the final sum exact to working precision.
 constexpr int kRecSmemDim = 64;
 constexpr size_t kRecSmemBytes = 2 * kRecSmemDim * kRecSmemDim * sizeof(double);
+constexpr int kRecThreads = 512;  // 16 warps (the register Jacobi's pairs for m <= 64), 64 registers: two CTAs per SM
 
 template <typename TC>
-__global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, double rel_tol, int rcap) {
+__global__ void __launch_bounds__(kRecThreads, 2) k_recompress(RefineArgs a, int mode, double rel_tol, int rcap) {
   extern __shared__ double rec_smem[];
   const int slot = blockIdx.x;
   SolveState* st = a.st + slot;
@@ -203,7 +204,13 @@ __global__ void __launch_bounds__(RT) k_recompress(RefineArgs a, int mode, doubl
     K[(int64_t)j * L + i] = (TC)s;
   }
   __syncthreads();
-  blk_jacobi<TC>(K, L, m, m, V, L, sig, &flag);
+  if constexpr (sizeof(TC) == 4) {
+    // FP32: the register form; its column exchange takes the shared memory the
+    // two FP32 tiles leave free (none in global scratch, where m > 64 falls back)
+    blk_jacobi_f32(K, L, m, m, V, L, sig, &flag, V + (int64_t)L * L, in_smem ? 2 * L * L : 0);
+  } else {
+    blk_jacobi<TC>(K, L, m, m, V, L, sig, &flag);
+  }
   blk_sort_desc(sig, m, perm);
   int r = 0;
   if (tid == 0) {
@@ -489,9 +496,9 @@ cudaError_t launch_assemble_residual(const RefineArgs& a, int nslots, cudaStream
 }
 cudaError_t launch_recompress(const RefineArgs& a, int nslots, int mode, double rel_tol, int rcap, cudaStream_t s) {
   if (mode == 0)
-    k_recompress<float><<<nslots, RT, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
+    k_recompress<float><<<nslots, kRecThreads, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
   else
-    k_recompress<double><<<nslots, RT, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
+    k_recompress<double><<<nslots, kRecThreads, kRecSmemBytes, s>>>(a, mode, rel_tol, rcap);
   return cudaGetLastError();
 }
 cudaError_t launch_setup_correction(const RefineArgs& a, int nslots, cudaStream_t s) {
