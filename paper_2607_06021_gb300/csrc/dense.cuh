@@ -284,25 +284,46 @@ __device__ inline void blk_jacobi(TC* A, int lda, int mr, int nc, TC* V, int ldv
   __syncthreads();
 }
 
+// Rotation (c, s) of the pair with squared norms a, b and dot product g (FP32):
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g), from
+// hardware reciprocals and reciprocal square roots (t only sets how far the
+// rotation reduces a.b), c = (1 + t^2)^{-1/2} refined by one Newton step so that
+// c^2 + s^2 = 1 to working precision (the rotation stays orthogonal), s = c t.
+__device__ __forceinline__ void rot_params_f32(float a, float b, float g, float& c, float& sn, float& t) {
+  const float zeta = __fdividef(b - a, 2.f * g);
+  if (fabsf(zeta) > 1e18f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float w = fmaf(zeta, zeta, 1.f);
+    t = copysignf(__fdividef(1.f, fabsf(zeta) + w * rsqrtf(w)), zeta);
+  }
+  const float u = fmaf(t, t, 1.f);
+  const float c0 = rsqrtf(u);
+  c = c0 * fmaf(-0.5f * u * c0, c0, 1.5f);
+  sn = c * t;
+}
+
 // One-sided Jacobi SVD in FP32 with the columns in registers: the same
-// round-robin pair ordering, rotations, stopping test and Frobenius scaling as
-// blk_jacobi, one warp per column pair.  A column is its mr rows of A followed by
-// its nc rows of V (V starts as the identity), NV values per lane
-// (mr + nc <= 32 NV); a warp holds the pairs k = warp (and k = warp + nwarps with
-// NS = 2), P = ne/2 <= NS nwarps pairs.  The ordering moves each pair's first column to pair k-1
-// (pair 0's to pair 1's second place) and each second column to pair k+1 (the
-// last pair's into its own first place, pair 0's second column stays), which
-// reproduces the cyclic schedule (a, b) = ((rnd + k) mod (ne-1), (rnd - k)
-// mod (ne-1)), pair 0 = (rnd mod (ne-1), ne-1); the columns move through `buf`
-// (2P columns of 32 NV floats, twice that with `dbl`: alternate halves and one
-// barrier per round, else two barriers per round).  After each sweep (ne-1
-// rounds, the schedule's period) the columns are back in their starting pairs.
-template <int NV, int NS>
-__device__ inline void blk_jacobi_reg(float* A, int lda, int mr, int nc, float* V, int ldv, double* sig, float* buf,
-                                      bool dbl, double* jr_red, float* jr_nrm) {
+// round-robin pair ordering, stopping test and Frobenius scaling as
+// blk_jacobi, one column pair per half-warp (pair k on half-warp k, P = ne/2
+// <= 2 nwarps).  A column is its mr rows of A followed by its nc rows of V (V
+// starts as the identity), spread over the half-warp's 16 lanes, NV2 values
+// per lane (mr + nc <= 16 NV2).  The ordering moves each pair's first column to
+// pair k-1 (pair 0's to pair 1's second place) and each second column to pair
+// k+1 (the last pair's into its own first place; pair 0's second column
+// stays), which reproduces the cyclic schedule (a, b) = ((rnd + k) mod (ne-1),
+// (rnd - k) mod (ne-1)), pair 0 = (rnd mod (ne-1), ne-1).  The moving columns
+// and their carried squared norms pass through `buf` (2P columns of 16 NV2
+// floats; twice that with `dbl`: alternate halves and one barrier per round,
+// else two barriers per round).  After each sweep (ne-1 rounds, the schedule's
+// period) the columns are back in their starting pairs.
+template <int NV2>
+__device__ inline void blk_jacobi_hreg(float* A, int lda, int mr, int nc, float* V, int ldv, double* sig, float* buf,
+                                       bool dbl, double* jr_red, float* jr_nrm) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  const int hl = lane & 15, k = tid >> 4;  // this half-warp's pair
   const int ne = nc + (nc & 1), P = ne >> 1, R = ne - 1, rows = mr + nc;
-  constexpr int S = 32 * NV;
+  constexpr int S = 16 * NV2;
   double f2 = 0.0;
   for (int e = tid; e < mr * nc; e += blockDim.x) {
     const double v = (double)A[(int64_t)(e / mr) * lda + (e % mr)];
@@ -321,97 +342,89 @@ __device__ inline void blk_jacobi_reg(float* A, int lda, int mr, int nc, float* 
   int ex = 0;
   if (fro2 > 0.0) frexp(sqrt(fro2), &ex);
   const float down = (float)ldexp(1.0, -ex), up = (float)ldexp(1.0, ex);
-  float x[NS][NV], y[NS][NV], al[NS], be[NS];
-  auto colval = [&](int c, int e) -> float {
-    if (c >= nc || e >= rows) return 0.f;
-    if (e < mr) return A[(int64_t)c * lda + e] * down;
-    return (e - mr == c) ? 1.f : 0.f;
-  };
-#pragma unroll
-  for (int j = 0; j < NS; ++j) {
-    const int k = warp + j * nwarps;
+  const bool live = k < P;
+  float x[NV2], y[NV2];
+  {
     const int ia = k, ib = (k == 0) ? ne - 1 : ne - 1 - k;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int e = lane + 32 * v;
-      x[j][v] = (k < P) ? colval(ia, e) : 0.f;
-      y[j][v] = (k < P) ? colval(ib, e) : 0.f;
+    for (int v = 0; v < NV2; ++v) {
+      const int e = hl + 16 * v;
+      float xv = 0.f, yv = 0.f;
+      if (live && e < rows) {
+        if (e < mr) {
+          if (ia < nc) xv = A[(int64_t)ia * lda + e] * down;
+          if (ib < nc) yv = A[(int64_t)ib * lda + e] * down;
+        } else {
+          xv = (e - mr == ia) ? 1.f : 0.f;
+          yv = (e - mr == ib) ? 1.f : 0.f;
+        }
+      }
+      x[v] = xv;
+      y[v] = yv;
     }
   }
+  // exchange destinations of this pair's two columns (fixed for the solve)
+  const int da = (k >= 1) ? 2 * (k - 1) : 3;
+  const int db = (k == 0) ? -1 : ((k <= P - 2) ? 2 * (k + 1) + 1 : 2 * (P - 1));
   const float tol = (float)((double)(mr > 1 ? mr : 1) * Eps<float>::value);
   const float tol2 = tol * tol;
   const float nu = (float)(Eps<float>::value * Eps<float>::value);
   int par = 0;
+  float al = 0.f, be = 0.f;
   for (int sweep = 0; sweep < kJacobiSweeps && ne >= 2; ++sweep) {
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
+    {
       float sa = 0.f, sb = 0.f;
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (lane + 32 * v < mr) {
-          sa = fmaf(x[j][v], x[j][v], sa);
-          sb = fmaf(y[j][v], y[j][v], sb);
+      for (int v = 0; v < NV2; ++v)
+        if (hl + 16 * v < mr) {
+          sa = fmaf(x[v], x[v], sa);
+          sb = fmaf(y[v], y[v], sb);
         }
-      al[j] = warp_sum(sa);
-      be[j] = warp_sum(sb);
+      al = half_warp_sum(sa);
+      be = half_warp_sum(sb);
     }
     int rot = 0;
     for (int rnd = 0; rnd < R; ++rnd) {
+      float g = 0.f;
 #pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int k = warp + j * nwarps;
-        if (k >= P) continue;  // warp-uniform
-        float g = 0.f;
+      for (int v = 0; v < NV2; ++v)
+        if (hl + 16 * v < mr) g = fmaf(x[v], y[v], g);
+      g = half_warp_sum(g);
+      if (live && !(g == 0.f || g * g <= tol2 * al * be || fminf(al, be) <= nu)) {
+        float c, sn, t;
+        rot_params_f32(al, be, g, c, sn, t);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          if (lane + 32 * v < mr) g = fmaf(x[j][v], y[j][v], g);
-        g = warp_sum(g);
-        const float a = al[j], b = be[j];
-        if (g == 0.f || g * g <= tol2 * a * b || fminf(a, b) <= nu) continue;
-        const float zeta = (b - a) / (2.f * g);
-        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        const float c = 1.f / sqrtf(1.f + t * t);
-        const float sn = c * t;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const float xv = x[j][v], yv = y[j][v];
-          x[j][v] = c * xv - sn * yv;
-          y[j][v] = sn * xv + c * yv;
+        for (int v = 0; v < NV2; ++v) {
+          const float xv = x[v], yv = y[v];
+          x[v] = c * xv - sn * yv;
+          y[v] = sn * xv + c * yv;
         }
-        al[j] = a - t * g;
-        be[j] = b + t * g;
+        al = al - t * g;
+        be = be + t * g;
         rot = 1;
       }
       if (P > 1) {
         float* bw = buf + (dbl ? par : 0) * (2 * P * S);
         float* nw = jr_nrm + (dbl ? par : 0) * (2 * P);
+        if (live) {
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          const int k = warp + j * nwarps;
-          if (k >= P) continue;
-          const int da = (k >= 1) ? 2 * (k - 1) : 3;
+          for (int v = 0; v < NV2; ++v) bw[da * S + hl + 16 * v] = x[v];
+          if (hl == 0) nw[da] = al;
+          if (db >= 0) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) bw[da * S + lane + 32 * v] = x[j][v];
-          if (lane == 0) nw[da] = al[j];
-          if (k >= 1) {
-            const int db = (k <= P - 2) ? 2 * (k + 1) + 1 : 2 * (P - 1);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) bw[db * S + lane + 32 * v] = y[j][v];
-            if (lane == 0) nw[db] = be[j];
+            for (int v = 0; v < NV2; ++v) bw[db * S + hl + 16 * v] = y[v];
+            if (hl == 0) nw[db] = be;
           }
         }
         __syncthreads();
+        if (live) {
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          const int k = warp + j * nwarps;
-          if (k >= P) continue;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) x[j][v] = bw[2 * k * S + lane + 32 * v];
-          al[j] = nw[2 * k];
+          for (int v = 0; v < NV2; ++v) x[v] = bw[2 * k * S + hl + 16 * v];
+          al = nw[2 * k];
           if (k >= 1) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) y[j][v] = bw[(2 * k + 1) * S + lane + 32 * v];
-            be[j] = nw[2 * k + 1];
+            for (int v = 0; v < NV2; ++v) y[v] = bw[(2 * k + 1) * S + hl + 16 * v];
+            be = nw[2 * k + 1];
           }
         }
         if (dbl)
@@ -422,63 +435,56 @@ __device__ inline void blk_jacobi_reg(float* A, int lda, int mr, int nc, float* 
     }
     if (!__syncthreads_or(rot)) break;
   }
-#pragma unroll
-  for (int j = 0; j < NS; ++j) {
-    const int k = warp + j * nwarps;
-    if (k >= P) continue;
+  {
+    // every lane takes part in the half-warp sums; only live pairs store
     const int ia = k, ib = (k == 0) ? ne - 1 : ne - 1 - k;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int col = side ? ib : ia;
+      const bool st = live && col < nc;
       float s2 = 0.f;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const int e = lane + 32 * v;
-        const float val = side ? y[j][v] : x[j][v];
+      for (int v = 0; v < NV2; ++v) {
+        const int e = hl + 16 * v;
+        const float val = side ? y[v] : x[v];
         if (e < mr) {
           const float u = val * up;
           s2 = fmaf(u, u, s2);
-          if (col < nc) A[(int64_t)col * lda + e] = u;
-        } else if (e < rows && col < nc) {
+          if (st) A[(int64_t)col * lda + e] = u;
+        } else if (e < rows && st) {
           V[(int64_t)col * ldv + (e - mr)] = val;
         }
       }
-      s2 = warp_sum(s2);
-      if (lane == 0 && col < nc) sig[col] = sqrt((double)s2);
+      s2 = half_warp_sum(s2);
+      if (hl == 0 && st) sig[col] = sqrt((double)s2);
     }
   }
   __syncthreads();
 }
 
 // FP32 one-sided Jacobi SVD (blk_jacobi's contract, V required): the register
-// form when the sizes fit it (mr + nc <= 128, ne/2 <= 2 warps per pair slot,
+// form when the sizes fit it (mr + nc <= 96, ne/2 <= 2 nwarps and <= 32,
 // `buf_floats` covering one set of 2P columns), else blk_jacobi<float>.
 __device__ inline void blk_jacobi_f32(float* A, int lda, int mr, int nc, float* V, int ldv, double* sig, int* flag,
                                       float* buf, int buf_floats) {
   const int ne = nc + (nc & 1), P = ne >> 1, rows = mr + nc;
-  const int nv = (rows + 31) >> 5;
-  const bool fits = nc >= 1 && P <= 2 * (int)(blockDim.x >> 5) && P <= 32 && nv <= 4 && 2 * P * 32 * nv <= buf_floats;
+  const int nv2 = (rows + 15) >> 4;
+  const int need = 2 * P * 16 * nv2;
+  const bool fits = nc >= 1 && P <= 2 * (int)(blockDim.x >> 5) && P <= 32 && nv2 <= 6 && need <= buf_floats;
   if (!fits) {
     blk_jacobi<float>(A, lda, mr, nc, V, ldv, sig, flag);
     return;
   }
-  const bool dbl = 2 * (2 * P * 32 * nv) <= buf_floats;
+  const bool dbl = 2 * need <= buf_floats;
   __shared__ double jr_red[32];     // block reduction of ||A||_F^2
   __shared__ float jr_nrm[2 * 64];  // carried squared norms of the moving columns
-  if (P <= (int)(blockDim.x >> 5)) {
-    switch (nv) {
-      case 1: blk_jacobi_reg<1, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      case 2: blk_jacobi_reg<2, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      case 3: blk_jacobi_reg<3, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      default: blk_jacobi_reg<4, 1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-    }
-  } else {
-    switch (nv) {
-      case 1: blk_jacobi_reg<1, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      case 2: blk_jacobi_reg<2, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      case 3: blk_jacobi_reg<3, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-      default: blk_jacobi_reg<4, 2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
-    }
+  switch (nv2) {
+    case 1: blk_jacobi_hreg<1>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    case 2: blk_jacobi_hreg<2>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    case 3: blk_jacobi_hreg<3>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    case 4: blk_jacobi_hreg<4>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    case 5: blk_jacobi_hreg<5>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
+    default: blk_jacobi_hreg<6>(A, lda, mr, nc, V, ldv, sig, buf, dbl, jr_red, jr_nrm); break;
   }
 }
 
