@@ -25,6 +25,7 @@
 #include "core.cuh"
 #include "dense.cuh"
 #include "dst.cuh"
+#include "f64cvt.cuh"
 
 namespace lrp {
 
@@ -98,6 +99,20 @@ __device__ void acct_back(double* row, int n_, int r_out, int w_, bool df) {
 }
 
 // ------------------------------------------------------------------- kernels
+
+// FP32 <-> FP64 conversions of the small matrices on the integer pipe
+// (f64cvt.cuh: the same values as the hardware conversions, which GB300 runs
+// on its FP64 pipe).
+__device__ __forceinline__ double widen64(double x) { return x; }
+__device__ __forceinline__ double widen64(float x) { return f32_to_f64(x); }
+template <typename TC>
+__device__ __forceinline__ TC narrow_to(double x) {
+  if constexpr (sizeof(TC) == 4) {
+    return f64_to_f32_rn(x);
+  } else {
+    return x;
+  }
+}
 
 constexpr int kCholSmemDim = 64;
 constexpr size_t kCholSmemBytes = kCholSmemDim * kCholSmemDim * sizeof(double);
@@ -191,29 +206,32 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   const TC thr = (pass == 0) ? TC(0) : (TC)(p.drop_rel * mx);
   __syncthreads();
 
+  // Right-looking factorisation.  The pivot's square root and reciprocal are
+  // taken by one thread and shared (on GB300 an FP64 square root or division
+  // by every thread of the CTA would occupy the FP64 pipe for thousands of
+  // cycles per pivot); the trailing update gives warp w the columns
+  // l = j+1+w, j+1+w+nw, ... and its lanes the rows k of column l.
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
   for (int j = 0; j < m; ++j) {
-    const TC d = W[(int64_t)j * Lc + j];
-    const bool drop = !(d > thr);
-    const TC rjj = drop ? TC(0) : sqrt(d);
-    const TC ri = drop ? TC(0) : TC(1) / rjj;
+    if (tid == 0) {
+      const TC d = W[(int64_t)j * Lc + j];
+      const bool drop = !(d > thr);
+      const TC rjj = drop ? TC(0) : sqrt(d);
+      W[(int64_t)j * Lc + j] = rjj;
+      dropped[j] = drop ? 1 : 0;
+      rinv[j] = drop ? TC(0) : TC(1) / rjj;
+    }
     __syncthreads();
+    const TC ri = rinv[j];
     for (int l = j + 1 + tid; l < m; l += nt) {
       TC* wl = W + (int64_t)l * Lc + j;
       *wl = *wl * ri;
     }
-    if (tid == 0) {
-      W[(int64_t)j * Lc + j] = rjj;
-      dropped[j] = drop ? 1 : 0;
-      rinv[j] = ri;
-    }
     __syncthreads();
-    if (!drop) {
-      const int t = m - j - 1;
-      for (int e = tid; e < t * t; e += nt) {
-        const int kk = e % t, ll = e / t;
-        if (kk > ll) continue;
-        const int k = j + 1 + kk, l = j + 1 + ll;
-        W[(int64_t)l * Lc + k] -= W[(int64_t)k * Lc + j] * W[(int64_t)l * Lc + j];
+    if (!dropped[j]) {
+      for (int l = j + 1 + wid; l < m; l += nwarp) {
+        const TC wlj = W[(int64_t)l * Lc + j];
+        for (int k = j + 1 + lane; k <= l; k += 32) W[(int64_t)l * Lc + k] -= W[(int64_t)k * Lc + j] * wlj;
       }
     }
     __syncthreads();
@@ -225,30 +243,27 @@ __global__ void __launch_bounds__(CT) k_chol(CoreParams p, CoreBufs<T> b, int se
   else
     chol_inverse_cols<TC, kMaxM / 32>(W, Lc, Tm, M, m, rinv, dropped);
   __syncthreads();
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    P[(int64_t)j * M + i] = dsc[i] * (double)Tm[(int64_t)j * M + i];
-  }
+  // (warp w: columns j = w, w + nw, ...; lanes: rows i)
+  for (int j = wid; j < m; j += nwarp)
+    for (int i = lane; i < m; i += 32) P[(int64_t)j * M + i] = dsc[i] * widen64(Tm[(int64_t)j * M + i]);
   __syncthreads();
   // Racc <- R (pass 0, undoing the equilibration) or R * Racc.
   if (pass == 0) {
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? (double)W[(int64_t)j * Lc + i] / dsc[j] : 0.0;
-    }
+    for (int j = wid; j < m; j += nwarp)
+      for (int i = lane; i < m; i += 32)
+        Racc[(int64_t)j * M + i] = (i <= j && dsc[j] > 0.0) ? widen64(W[(int64_t)j * Lc + i]) / dsc[j] : 0.0;
   } else {
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e % m, l = e / m;
-      TC s = TC(0);
-      if (i <= l)
-        for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * (TC)Racc[(int64_t)l * M + k];
-      Tm[(int64_t)l * M + i] = s;
+    for (int l = wid; l < m; l += nwarp) {
+      for (int i = lane; i < m; i += 32) {
+        TC s = TC(0);
+        if (i <= l)
+          for (int k = i; k <= l; ++k) s += W[(int64_t)k * Lc + i] * narrow_to<TC>(Racc[(int64_t)l * M + k]);
+        Tm[(int64_t)l * M + i] = s;
+      }
     }
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e % m, j = e / m;
-      Racc[(int64_t)j * M + i] = (double)Tm[(int64_t)j * M + i];
-    }
+    for (int j = wid; j < m; j += nwarp)
+      for (int i = lane; i < m; i += 32) Racc[(int64_t)j * M + i] = widen64(Tm[(int64_t)j * M + i]);
   }
 }
 
@@ -335,14 +350,14 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
     const int a = e % q, c = e / q;
     const int64_t row = I[a];
     TC s = 0;
-    for (int d = 0; d <= c; ++d) s += (TC)Q20[(int64_t)d * ld + row] * (TC)P0[(int64_t)c * M + d];
+    for (int d = 0; d <= c; ++d) s += (TC)Q20[(int64_t)d * ld + row] * narrow_to<TC>(P0[(int64_t)c * M + d]);
     QI[(int64_t)c * L + a] = s;
   }
   for (int e = tid; e < pc * q; e += nt) {
     const int a = e % pc, c = e / pc;
     const int64_t row = J[a];
     TC s = 0;
-    for (int d = 0; d <= c; ++d) s += (TC)Q21[(int64_t)d * ld + row] * (TC)P1[(int64_t)c * M + d];
+    for (int d = 0; d <= c; ++d) s += (TC)Q21[(int64_t)d * ld + row] * narrow_to<TC>(P1[(int64_t)c * M + d]);
     ZJ[(int64_t)c * L + a] = s;
   }
   __syncthreads();
@@ -373,8 +388,8 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       const int a = e % pc, c = e / pc;
       TC s = 0;
       if (sig1[a] > cut) {
-        for (int d = c; d < q; ++d) s += W1[(int64_t)a * L + d] * (TC)RR[(int64_t)d * M + c];
-        s /= (TC)(sig1[a] * sig1[a]);
+        for (int d = c; d < q; ++d) s += W1[(int64_t)a * L + d] * narrow_to<TC>(RR[(int64_t)d * M + c]);
+        s /= narrow_to<TC>(sig1[a] * sig1[a]);
       }
       T1[(int64_t)c * L + a] = s;
     }
@@ -405,8 +420,8 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
       const int i = e % pc, a = e / pc;
       TC s = 0;
       if (sig1[a] > cut) {
-        for (int c = i; c < pc; ++c) s += (TC)RC[(int64_t)c * M + i] * W1[(int64_t)a * L + c];
-        s /= (TC)(sig1[a] * sig1[a]);
+        for (int c = i; c < pc; ++c) s += narrow_to<TC>(RC[(int64_t)c * M + i]) * W1[(int64_t)a * L + c];
+        s /= narrow_to<TC>(sig1[a] * sig1[a]);
       }
       T1[(int64_t)a * L + i] = s;
     }
@@ -435,13 +450,13 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
   for (int e = tid; e < pc * r; e += nt) {
     const int i = e % pc, t = e / pc;
     const int j = perm[t];
-    const TC sv = (TC)sig2[j];
+    const TC sv = narrow_to<TC>(sig2[j]);
     Ut[(int64_t)t * L + i] = (branch == 0) ? V2[(int64_t)j * L + i] : (sv > 0 ? Mt[(int64_t)j * L + i] / sv : (TC)0);
   }
   for (int e = tid; e < q * r; e += nt) {
     const int i = e % q, t = e / q;
     const int j = perm[t];
-    const TC sv = (TC)sig2[j];
+    const TC sv = narrow_to<TC>(sig2[j]);
     Vt[(int64_t)t * L + i] = (branch == 0) ? (sv > 0 ? Mt[(int64_t)j * L + i] / sv : (TC)0) : V2[(int64_t)j * L + i];
   }
   double* sig_out = b.sig + (int64_t)slot * 2 * M + (int64_t)parity * M;
@@ -455,14 +470,14 @@ __global__ void __launch_bounds__(CTC, 2) k_core(CoreParams p, CoreBufs<T> b, in
   for (int e = tid; e < pc * r; e += nt) {
     const int i = e % pc, t = e / pc;
     TC s = 0;
-    for (int d = i; d < pc; ++d) s += (TC)P0[(int64_t)d * M + i] * Ut[(int64_t)t * L + d];
-    B0[(int64_t)t * M + i] = (double)s;
+    for (int d = i; d < pc; ++d) s += narrow_to<TC>(P0[(int64_t)d * M + i]) * Ut[(int64_t)t * L + d];
+    B0[(int64_t)t * M + i] = widen64(s);
   }
   for (int e = tid; e < q * r; e += nt) {
     const int i = e % q, t = e / q;
     TC s = 0;
-    for (int d = i; d < q; ++d) s += (TC)P1[(int64_t)d * M + i] * Vt[(int64_t)t * L + d];
-    B1[(int64_t)t * M + i] = (double)s;
+    for (int d = i; d < q; ++d) s += narrow_to<TC>(P1[(int64_t)d * M + i]) * Vt[(int64_t)t * L + d];
+    B1[(int64_t)t * M + i] = widen64(s);
   }
   for (int e = tid; e < q * r; e += nt) {
     const int a = e % q, t = e / q;

@@ -10,19 +10,23 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "f64cvt.cuh"
+
 namespace lrp {
 
 struct dfloat {
   float hi, lo;
   dfloat() = default;
   __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  // The conversions to and from FP64 round exactly as the hardware ones but run
+  // on the integer pipe (f64cvt.cuh); only the FP64 add/subtract remain.
   __device__ explicit dfloat(double x) {
-    hi = __double2float_rn(x);
-    lo = __double2float_rn(x - (double)hi);
+    hi = f64_to_f32_rn(x);
+    lo = f64_to_f32_rn(x - f32_to_f64(hi));
   }
   __device__ explicit dfloat(float x) : hi(x), lo(0.f) {}
   __device__ explicit dfloat(int x) : hi((float)x), lo(0.f) {}
-  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit operator double() const { return f32_to_f64(hi) + f32_to_f64(lo); }
   __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
 };
 

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
+#include "f64cvt.cuh"
 #include "tall.cuh"
 
 namespace lrp {
@@ -50,8 +52,8 @@ __device__ __forceinline__ void dd_renorm(float& hi, float& lo) {
 
 // (hi, lo) parts of a double: hi = the nearest float, lo = the nearest float to the rest.
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
+  hi = f64_to_f32_rn(x);
+  lo = f64_to_f32_rn(x - f32_to_f64(hi));
 }
 }  // namespace
 
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(DT) k_gemm_dfx(TallGeom g, const SolveState* _
           oh.at(slot, side)[o] = h;
           if (ol.base) ol.at(slot, side)[o] = __fsub_rn(lo[i][j], __fsub_rn(h, hi[i][j]));
         } else {
-          o64.at(slot, side)[o] = (double)hi[i][j] + (double)lo[i][j];
+          o64.at(slot, side)[o] = f32_to_f64(hi[i][j]) + f32_to_f64(lo[i][j]);
         }
       }
     }
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(DT) k_gram_dd(TallGeom g, const SolveState* __
 #pragma unroll
   for (int i = 0; i < TS; ++i)
 #pragma unroll
-    for (int j = 0; j < TS; ++j) tot[i][j] = (double)hi[i][j] + (double)lo[i][j];
+    for (int j = 0; j < TS; ++j) tot[i][j] = f32_to_f64(hi[i][j]) + f32_to_f64(lo[i][j]);
   double* red = reinterpret_cast<double*>(sm);
   if (own) {
 #pragma unroll

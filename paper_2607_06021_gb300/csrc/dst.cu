@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "dfloat.cuh"
 #include "dst.cuh"
+#include "f64cvt.cuh"
 
 namespace lrp {
 
@@ -29,6 +30,30 @@ template <typename T>
 struct cplx {
   T re, im;
 };
+
+// An input element in the compute type.  FP64 data for an FP32 transform are
+// rounded on the integer pipe (f64_to_f32_rn: the same value as the hardware
+// conversion, without GB300's FP64 pipe).
+template <typename TC, typename TIn>
+__device__ __forceinline__ TC to_tc(TIn v) {
+  if constexpr (std::is_same<TIn, double>::value && std::is_same<TC, float>::value) {
+    return f64_to_f32_rn(v);
+  } else {
+    return TC(v);
+  }
+}
+
+// An output element in the output type (the integer-pipe conversions again).
+template <typename TOut, typename TC>
+__device__ __forceinline__ TOut from_tc(TC v) {
+  if constexpr (std::is_same<TOut, double>::value && std::is_same<TC, float>::value) {
+    return f32_to_f64(v);
+  } else if constexpr (std::is_same<TOut, float>::value && std::is_same<TC, double>::value) {
+    return f64_to_f32_rn(v);
+  } else {
+    return (TOut)v;
+  }
+}
 
 template <typename TC>
 __global__ void k_twiddle(cplx<TC>* tw, int N) {
@@ -283,7 +308,8 @@ constexpr int dst_max_threads() { return sizeof(TC) == 4 ? 1024 : 512; }
 template <typename TIn, typename TOut, typename TC>
 __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int logL, int cols_per_cta,
                                                                    const DstBatch<TIn, TOut> job,
-                                                                   const cplx<TC>* __restrict__ tw) {
+                                                                   const cplx<TC>* __restrict__ tw,
+                                                                   double scale64) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = n + 1, L = N >> 1, Tc = L >> 3;
   const int g = threadIdx.x / Tc, t = threadIdx.x - g * Tc;
@@ -318,17 +344,25 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
 
   // Pre-processing: u_j and u_{N-j} for j = 1..N/2-1 (x_j = x[j-1]); u_0 = 0,
   // u_{N/2} = 2 x_{N/2}.  The thread's 16 loads are issued before any use.
+  // (all 16 loads first, in the input type; the conversions, whose rare
+  // branches would otherwise hold back the later loads, follow)
   const TC half = TC(0.5);
-  TC xa[8], xb[8];
+  TIn ra[8], rb[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int j = 1 + t + q * Tc;
-    xa[q] = TC(0);
-    xb[q] = TC(0);
+    ra[q] = TIn(0);
+    rb[q] = TIn(0);
     if (live && j < L) {
-      xa[q] = TC(x[j - 1]);
-      xb[q] = TC(x[N - j - 1]);
+      ra[q] = x[j - 1];
+      rb[q] = x[N - j - 1];
     }
+  }
+  TC xa[8], xb[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    xa[q] = to_tc<TC>(ra[q]);
+    xb[q] = to_tc<TC>(rb[q]);
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -342,7 +376,7 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
   }
   if (t == 0) {
     zs(0) = TC(0);
-    const TC xm = live ? TC(x[L - 1]) : TC(0);
+    const TC xm = live ? to_tc<TC>(x[L - 1]) : TC(0);
     zs(L) = xm + xm;
   }
   __syncthreads();
@@ -389,14 +423,15 @@ __global__ void __launch_bounds__(dst_max_threads<TC>()) k_dst1_half(int n, int 
   for (int e = 0; e < 8; ++e) zs(2 * (8 * t + e)) = before + acc[e];
   __syncthreads();
   if (live) {
-    const TC scale = TC(sqrt(2.0 / (double)N));
-    for (int i = t; i < n; i += Tc) y[i] = (TOut)(scale * zs(i));
+    const TC scale = to_tc<TC>(scale64);
+    for (int i = t; i < n; i += Tc) y[i] = from_tc<TOut>(scale * zs(i));
   }
 }
 
 // Small N (< kDstMinN): one thread per output, the defining sum.
 template <typename TIn, typename TOut, typename TC>
-__global__ void k_dst1_direct(int n, const DstBatch<TIn, TOut> job, const cplx<TC>* __restrict__ tw) {
+__global__ void k_dst1_direct(int n, const DstBatch<TIn, TOut> job, const cplx<TC>* __restrict__ tw,
+                              double scale64) {
   const int N = n + 1;
   const int col = blockIdx.x, slot = blockIdx.y, mat = blockIdx.z;
   int ncols = job.fixed_cols;
@@ -408,11 +443,11 @@ __global__ void k_dst1_direct(int n, const DstBatch<TIn, TOut> job, const cplx<T
   if (x == nullptr || y == nullptr) return;
   x += (int64_t)col * job.ld_in[mat * job.nslots + slot];
   y += (int64_t)col * job.ld_out[mat * job.nslots + slot];
-  const TC scale = TC(sqrt(2.0 / (double)N));
+  const TC scale = to_tc<TC>(scale64);
   for (int k = 1 + threadIdx.x; k <= n; k += blockDim.x) {
     TC s = TC(0);
-    for (int j = 1; j <= n; ++j) s = s + TC(x[j - 1]) * (TC(0) - tw_any(tw, j * k, N).im);  // sin(pi j k / N)
-    y[k - 1] = (TOut)(scale * s);
+    for (int j = 1; j <= n; ++j) s = s + to_tc<TC>(x[j - 1]) * (TC(0) - tw_any(tw, j * k, N).im);  // sin(pi j k / N)
+    y[k - 1] = from_tc<TOut>(scale * s);
   }
 }
 
@@ -465,12 +500,12 @@ __device__ inline cplx<TC> packed(const TIn* x, int j, int N) {
   TC re, im;
   if (j < half) {
     const int e = 2 * j, o = 2 * j + 1;
-    re = (e == 0) ? (TC)0 : (TC)x[e - 1];
-    im = (TC)x[o - 1];
+    re = (e == 0) ? (TC)0 : to_tc<TC>(x[e - 1]);
+    im = to_tc<TC>(x[o - 1]);
   } else {
     const int e = 2 * N - 2 * j, o = 2 * N - 2 * j - 1;
-    re = (e == N) ? (TC)0 : -(TC)x[e - 1];
-    im = -(TC)x[o - 1];
+    re = (e == N) ? (TC)0 : -to_tc<TC>(x[e - 1]);
+    im = -to_tc<TC>(x[o - 1]);
   }
   return {re, im};
 }
@@ -516,7 +551,7 @@ __global__ void k_dst1_passA(int n, int logN1, int logN2, int G, int nmats, cons
 template <typename TIn, typename TOut, typename TC>
 __global__ void k_dst1_passB(int n, int logN1, int logN2, int nmats, const DstBatch<TIn, TOut> job,
                              const cplx<TC>* __restrict__ tw, const cplx<TC>* __restrict__ temp,
-                             int64_t temp_col_stride) {
+                             int64_t temp_col_stride, double scale64) {
   extern __shared__ unsigned char smem_raw[];
   cplx<TC>* z = reinterpret_cast<cplx<TC>*>(smem_raw);  // two rows of N1
   const int N = n + 1, N1 = 1 << logN1, N2 = 1 << logN2;
@@ -541,7 +576,7 @@ __global__ void k_dst1_passB(int n, int logN1, int logN2, int nmats, const DstBa
   if (b != a) blk_fft_bitrev<TC>(z + N1, logN1, tw, N);
   // Z[a + N2 k1] = z[k1]; Z[b + N2 k1] = z[N1 + k1] (b == a: the same row).
   const cplx<TC>* zb = (b != a) ? z + N1 : z;
-  const TC scale = (TC)sqrt(2.0 / (double)N);
+  const TC scale = to_tc<TC>(scale64);
   for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) {
     const int k = a + N2 * k1;
     if (k == 0) continue;
@@ -615,6 +650,7 @@ template <typename TIn, typename TOut, typename TC>
 cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols, int nslots, int nmats,
                         const void* tw, cudaStream_t st, void* temp, size_t temp_bytes) {
   const int N = (int)(n + 1);
+  const double scale64 = sqrt(2.0 / (double)N);  // the orthonormal scaling, once on the host
   if (!dst_smem_supported(n, sizeof(TC) == 8)) {
     // Multi-pass: N = N1 * N2 with N1 >= N2, both <= 2048 (N <= 2^22).
     const int logN = ilog2(N);
@@ -637,13 +673,14 @@ cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols,
     dim3 gB(N2 / 2 + 1, max_cols, nslots * nmats);
     const size_t smemB = 2 * (size_t)N1 * sizeof(cplx<TC>);
     k_dst1_passB<TIn, TOut, TC><<<gB, 256, smemB, st>>>((int)n, logN1, logN2, nmats, job,
-                                                         (const cplx<TC>*)tw, (const cplx<TC>*)temp, (int64_t)N);
+                                                         (const cplx<TC>*)tw, (const cplx<TC>*)temp, (int64_t)N,
+                                                         scale64);
     return cudaGetLastError();
   }
   if (max_cols <= 0 || nslots <= 0) return cudaSuccess;
   if (N < kDstMinN) {
     dim3 grid(max_cols, nslots, nmats);
-    k_dst1_direct<TIn, TOut, TC><<<grid, 64, 0, st>>>((int)n, job, (const cplx<TC>*)tw);
+    k_dst1_direct<TIn, TOut, TC><<<grid, 64, 0, st>>>((int)n, job, (const cplx<TC>*)tw, scale64);
     return cudaGetLastError();
   }
   const int L = N / 2, logL = ilog2(L);
@@ -652,7 +689,8 @@ cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols,
   const int threads = Tc * cols_per_cta;
   const size_t smem = dst_half_smem<TC>(N, cols_per_cta);
   dim3 grid((max_cols + cols_per_cta - 1) / cols_per_cta, nslots, nmats);
-  k_dst1_half<TIn, TOut, TC><<<grid, threads, smem, st>>>((int)n, logL, cols_per_cta, job, (const cplx<TC>*)tw);
+  k_dst1_half<TIn, TOut, TC><<<grid, threads, smem, st>>>((int)n, logL, cols_per_cta, job, (const cplx<TC>*)tw,
+                                                           scale64);
   return cudaGetLastError();
 }
 

@@ -137,7 +137,7 @@ __global__ void k_assemble_residual(RefineArgs a) {
     };
     for (int j = 0; j < rf; ++j) put(j, Fh[(int64_t)j * a.ld + i]);
     for (int t = 0; t < r0; ++t) {
-      const double u = U0d ? U0d[(int64_t)t * a.ld + i] : (double)U0[(int64_t)t * a.ld + i];
+      const double u = U0d ? U0d[(int64_t)t * a.ld + i] : f32_to_f64(U0[(int64_t)t * a.ld + i]);
       stash[(int64_t)t * a.ld + i] = u;
       put(rf + t, side == 0 ? lam * u : u);
       put(rf + r0 + t, side == 0 ? u : lam * u);
@@ -147,7 +147,7 @@ __global__ void k_assemble_residual(RefineArgs a) {
   double* X = a.X.at(slot, side);
   for (int j = 0; j < rf; ++j) X[(int64_t)j * a.ld + i] = Fh[(int64_t)j * a.ld + i];
   for (int t = 0; t < r0; ++t) {
-    const double u = U0d ? U0d[(int64_t)t * a.ld + i] : (double)U0[(int64_t)t * a.ld + i];
+    const double u = U0d ? U0d[(int64_t)t * a.ld + i] : f32_to_f64(U0[(int64_t)t * a.ld + i]);
     stash[(int64_t)t * a.ld + i] = u;
     const double first = (side == 0) ? lam * u : u;
     const double second = (side == 0) ? u : lam * u;
@@ -163,6 +163,19 @@ __global__ void k_assemble_residual(RefineArgs a) {
 // K is always formed in FP64 (the cancellation between the stacked blocks happens
 // there); its SVD runs in TC: FP32 suffices for the residual, whose correction is
 // an FP32 solve, and FP64 keeps the final sum exact to working precision.
+// FP32 <-> FP64 conversions on the integer pipe (f64cvt.cuh: the values of the
+// hardware conversions, which GB300 runs on its FP64 pipe).
+__device__ __forceinline__ double widen64(double x) { return x; }
+__device__ __forceinline__ double widen64(float x) { return f32_to_f64(x); }
+template <typename TC>
+__device__ __forceinline__ TC narrow_to(double x) {
+  if constexpr (sizeof(TC) == 4) {
+    return f64_to_f32_rn(x);
+  } else {
+    return x;
+  }
+}
+
 constexpr int kRecSmemDim = 64;
 constexpr size_t kRecSmemBytes = 2 * kRecSmemDim * kRecSmemDim * sizeof(double);
 constexpr int kRecThreads = 512;  // 16 warps (the register Jacobi's pairs for m <= 64), 64 registers: two CTAs per SM
@@ -196,12 +209,13 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recompress(RefineArgs a, int
   __shared__ int perm[kMaxM];
   __shared__ int flag;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // K(i, j) = sum_{l >= max(i, j)} R0(i, l) d_l R1(j, l)
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    double s = 0.0;
-    for (int l = max(i, j); l < m; ++l) s += R0[(int64_t)l * M + i] * d[l] * R1[(int64_t)l * M + j];
-    K[(int64_t)j * L + i] = (TC)s;
+  // K(i, j) = sum_{l >= max(i, j)} R0(i, l) d_l R1(j, l)   (warp: columns j; lanes: rows i)
+  for (int j = threadIdx.x >> 5; j < m; j += blockDim.x >> 5) {
+    for (int i = threadIdx.x & 31; i < m; i += 32) {
+      double s = 0.0;
+      for (int l = max(i, j); l < m; ++l) s += R0[(int64_t)l * M + i] * d[l] * R1[(int64_t)l * M + j];
+      K[(int64_t)j * L + i] = narrow_to<TC>(s);
+    }
   }
   __syncthreads();
   if constexpr (sizeof(TC) == 4) {
@@ -236,17 +250,40 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recompress(RefineArgs a, int
   __syncthreads();
   r = flag;
   // Left vectors: K(:, perm[t]) / sigma (K now holds U' Sigma); right: V(:, perm[t]).
-  for (int e = tid; e < m * r; e += nt) {
-    const int i = e % m, t = e / m;
-    const int j = perm[t];
-    double s0 = 0.0, s1 = 0.0;
-    const double sv = sig[j];
-    for (int c = i; c < m; ++c) {
-      s0 += P0[(int64_t)c * M + i] * (sv > 0.0 ? (double)K[(int64_t)j * L + c] / sv : 0.0);
-      s1 += P1[(int64_t)c * M + i] * (double)V[(int64_t)j * L + c];
+  // Each quotient K(c, j) / sigma_j is formed once (an FP64 division occupies
+  // GB300's FP64 pipe for dozens of instructions): in place for FP64 K, else
+  // in the shared memory the Jacobi exchange left free (FP64, leading
+  // dimension L).  K in global scratch (m > 64) divides inside the sums.
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
+  double* Kq = nullptr;
+  if constexpr (sizeof(TC) == 8) {
+    Kq = reinterpret_cast<double*>(K);
+  } else {
+    if (in_smem) Kq = reinterpret_cast<double*>(V + (int64_t)L * L);
+  }
+  if (Kq != nullptr) {
+    for (int t = wid; t < r; t += nwarp) {
+      const int j = perm[t];
+      const double sv = sig[j];
+      for (int c = lane; c < m; c += 32)
+        Kq[(int64_t)j * L + c] = sv > 0.0 ? widen64(K[(int64_t)j * L + c]) / sv : 0.0;
     }
-    B0[(int64_t)t * M + i] = s0;
-    B1[(int64_t)t * M + i] = s1;
+    __syncthreads();
+  }
+  for (int t = wid; t < r; t += nwarp) {
+    const int j = perm[t];
+    const double sv = sig[j];
+    for (int i = lane; i < m; i += 32) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int c = i; c < m; ++c) {
+        const double kq = Kq != nullptr ? Kq[(int64_t)j * L + c]
+                                        : (sv > 0.0 ? widen64(K[(int64_t)j * L + c]) / sv : 0.0);
+        s0 += P0[(int64_t)c * M + i] * kq;
+        s1 += P1[(int64_t)c * M + i] * widen64(V[(int64_t)j * L + c]);
+      }
+      B0[(int64_t)t * M + i] = s0;
+      B1[(int64_t)t * M + i] = s1;
+    }
   }
   for (int t = tid; t < r; t += nt) sig_out[t] = sig[perm[t]];
   if (tid == 0) {
@@ -307,7 +344,16 @@ __global__ void k_convert(int n, int64_t ld, const SolveState* st_all, Strided<c
   const int c = dim_of(st, side, sel);
   const TS* s = src.at(slot, side);
   TD* d = dst.at(slot, side);
-  for (int j = 0; j < c; ++j) d[(int64_t)j * ld + i] = (TD)s[(int64_t)j * ld + i];
+  for (int j = 0; j < c; ++j) {
+    const TS v = s[(int64_t)j * ld + i];
+    if constexpr (sizeof(TS) == 8 && sizeof(TD) == 4) {
+      d[(int64_t)j * ld + i] = f64_to_f32_rn(v);  // the hardware rounding, on the integer pipe
+    } else if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
+      d[(int64_t)j * ld + i] = f32_to_f64(v);
+    } else {
+      d[(int64_t)j * ld + i] = (TD)v;
+    }
+  }
 }
 
 // After the correction solve: d = [S0, dS], mx = r0 + rd.

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
+#include "f64cvt.cuh"
 #include "tall.cuh"
 
 namespace lrp {
@@ -59,6 +61,22 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 // 1 / x: the exact quotient in FP64; in FP32 the correctly rounded reciprocal
 // (the product then carries at most ~1.5 ulp, below the FP32 data's noise).
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// Widening to FP64 for the partial sums: exact, on the integer pipe for FP32
+// values (f64cvt.cuh; GB300 runs the hardware conversion on its FP64 pipe).
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+
+// An FP64 small-matrix entry in the data type T: for FP32 the same rounding as
+// the hardware conversion, on the integer pipe.
+template <typename T>
+__device__ __forceinline__ T from_f64(double x) {
+  if constexpr (sizeof(T) == 4) {
+    return f64_to_f32_rn(x);
+  } else {
+    return x;
+  }
+}
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 
 // Sampled columns / rows of the transformed solution (Eq. g_for_p), one thread
@@ -220,7 +238,7 @@ __device__ __forceinline__ void gemm_block(const TallGeom& g, const T* __restric
         for (int e = tid; e < kpad * TNW; e += NT) {
           const int k = e % kpad, c = e / kpad;
           const int col = c0 + c;
-          Bs[k][c] = (kb + k < kend && col < mo) ? (T)Bm[(int64_t)col * g.M + kb + k] : (T)0;
+          Bs[k][c] = (kb + k < kend && col < mo) ? from_f64<T>(Bm[(int64_t)col * g.M + kb + k]) : (T)0;
         }
       }
       for (int k0 = kb; k0 < kend; k0 += TK) {
@@ -305,7 +323,7 @@ __device__ __forceinline__ void gemm_rows(const TallGeom& g, const T* __restrict
   const int mi4 = (mi + 3) & ~3;
   for (int e = tid; e < mo * KMAX; e += NT) {
     const int k = e % KMAX, c = e / KMAX;
-    Bt[c][k] = (k < mi) ? (T)Bm[(int64_t)c * g.M + k] : (T)0;
+    Bt[c][k] = (k < mi) ? from_f64<T>(Bm[(int64_t)c * g.M + k]) : (T)0;
   }
   __syncthreads();
   for (int pass = 0; pass < kRows / (NT * R); ++pass) {
@@ -430,7 +448,7 @@ __device__ void gram_tiled(const TallGeom& g, const T* __restrict__ X, const T* 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int b = b0 + tx + 16 * j;
-          if (b < my) P[(int64_t)b * g.M + a] = (double)acc[i][j];
+          if (b < my) P[(int64_t)b * g.M + a] = to_f64(acc[i][j]);
         }
       }
     }
@@ -581,7 +599,7 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
 #pragma unroll
         for (int j = 0; j < TS; ++j) {
           const int a = TS * ia[q] + i, b = TS * ib[q] + j;
-          if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = (double)acc[q][i][j];
+          if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = to_f64(acc[q][i][j]);
         }
     }
     return;
@@ -602,7 +620,7 @@ __global__ void __launch_bounds__(NT) k_gram_small(TallGeom g, const SolveState*
     int ta, tb;
     tile_coords(tt, same, tx, ta, tb);
     const int a = TS * ta + i, b = TS * tb + j;
-    if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = (double)v;
+    if (a < mx && b < my && (!same || a <= b)) P[(int64_t)b * g.M + a] = to_f64(v);
   }
 }
 
@@ -632,10 +650,12 @@ __device__ __forceinline__ void df_add_product(float a, float b, float& hi, floa
 // k_gram_small<float, float, 4, 1>, but each entry is a double-float (hi, lo)
 // sum of exact products, renormalised by TwoSum after every chunk so that lo
 // stays within an ulp of hi: the relative error stays below ~n eps32^2 (6e-11
-// at n = 4095) in the worst case, ~1e-13 typically, and only the final sum is
-// converted to FP64 (GB300's FP64 pipe is 1/64 of its FP32 pipe).
+// at n = 4095) in the worst case, ~1e-13 typically.  Only the row groups'
+// final sums touch GB300's FP64 pipe (1/64 of its FP32 pipe): each (hi, lo)
+// pair is widened exactly on the integer pipe and the groups' values are added
+// in FP64.  At most 85 registers per thread, three CTAs per SM.
 
-__global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __restrict__ st_all,
+__global__ void __launch_bounds__(NT, 3) k_gram_df(TallGeom g, const SolveState* __restrict__ st_all,
                                                 Strided<const float> xs, int sel_x, double* __restrict__ part) {
   constexpr int KC = kSmallRows;
   constexpr int LDS = kSmallGram + 4;
@@ -714,11 +734,6 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
     }
     __syncthreads();
   }
-  double tot[TS][TS];
-#pragma unroll
-  for (int i = 0; i < TS; ++i)
-#pragma unroll
-    for (int j = 0; j < TS; ++j) tot[i][j] = (double)hi[i][j] + (double)lo[i][j];
   if (G == 1) {
     if (own) {
 #pragma unroll
@@ -726,27 +741,30 @@ __global__ void __launch_bounds__(NT) k_gram_df(TallGeom g, const SolveState* __
 #pragma unroll
         for (int j = 0; j < TS; ++j) {
           const int a = TS * ia + i, b = TS * ib + j;
-          if (a < mx && b < mx && a <= b) P[(int64_t)b * g.M + a] = tot[i][j];
+          if (a < mx && b < mx && a <= b) P[(int64_t)b * g.M + a] = f32_to_f64(hi[i][j]) + f32_to_f64(lo[i][j]);
         }
     }
     return;
   }
+  // red[grp][tile][TS * TS]: each (hi, lo) sum as the exact FP64 value hi + lo
   double* red = reinterpret_cast<double*>(gsm);
   if (own) {
 #pragma unroll
     for (int i = 0; i < TS; ++i)
 #pragma unroll
-      for (int j = 0; j < TS; ++j) red[((size_t)grp * ntile + t0) * TS * TS + i * TS + j] = tot[i][j];
+      for (int j = 0; j < TS; ++j)
+        red[((size_t)grp * ntile + t0) * TS * TS + i * TS + j] = f32_to_f64(hi[i][j]) + f32_to_f64(lo[i][j]);
   }
   __syncthreads();
   for (int e = tid; e < ntile * TS * TS; e += NT) {
     const int tt = e / (TS * TS), ij = e % (TS * TS), i = ij / TS, j = ij % TS;
-    double v = 0.0;
-    for (int q = 0; q < G; ++q) v += red[((size_t)q * ntile + tt) * TS * TS + ij];
     int ta, tb;
     tile_coords(tt, true, tx, ta, tb);
     const int a = TS * ta + i, b = TS * tb + j;
-    if (a < mx && b < mx && a <= b) P[(int64_t)b * g.M + a] = v;
+    if (a >= mx || b >= mx || a > b) continue;
+    double v = 0.0;
+    for (int q = 0; q < G; ++q) v += red[((size_t)q * ntile + tt) * TS * TS + ij];
+    P[(int64_t)b * g.M + a] = v;
   }
 }
 
