@@ -385,14 +385,16 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         lanes = args.lanes if args.lanes > 0 else (cfg[0] if cfg else 4)
         dev = bool(args.loop_on_device) if args.loop_on_device >= 0 else (cfg[1] if cfg else False)
         src = "table" if (cfg and args.lanes <= 0 and args.loop_on_device < 0) else "command line / default"
+        # launch shapes: the tuned table's (result-neutral; 0 = library default)
+        shapes = table.get_shapes(prec, N, RF, B)
         if lanes > 1:
             plan = lrp.Group(N, TOL, RMAX, lanes=lanes, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
                              refine_steps=args.refine_steps, selector=args.selector,
-                             sample_factor=args.sample_factor, loop_on_device=dev)
+                             sample_factor=args.sample_factor, loop_on_device=dev, **shapes)
         else:
             plan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
                             refine_steps=args.refine_steps, selector=args.selector, sample_factor=args.sample_factor,
-                            loop_on_device=dev)
+                            loop_on_device=dev, **shapes)
 
         def step():
             with torch.cuda.stream(stream):
@@ -421,7 +423,7 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         total_ms = max_over_ranks(sum(ms))
         res = {"ms": ms, "total_ms": total_ms, "wall_s": wall, "clocks": clk, "launches": launches,
                "value": whole_job_value(B, world, args.steps, total_ms),
-               "tuning": {"lanes": lanes, "loop_on_device": dev, "source": src}}
+               "tuning": {"lanes": lanes, "loop_on_device": dev, "source": src, **shapes}}
         # End to end through the public call with host buffers (pinned), copies inside the timed region.
         if not args.no_e2e:
             barrier()
@@ -444,7 +446,8 @@ def gpu_arm(args, rank, world, local_rank, precisions):
         # another lane's (concurrent lanes would fold their waits into each
         # launch's event interval).
         tplan = lrp.Plan(N, TOL, RMAX, precision=prec, batch=B, max_rhs_rank=RF, m_cap=M_CAP,
-                         refine_steps=args.refine_steps, selector=args.selector, sample_factor=args.sample_factor)
+                         refine_steps=args.refine_steps, selector=args.selector, sample_factor=args.sample_factor,
+                         **shapes)
         with torch.cuda.stream(stream):
             tplan.solve_batch_into(batch.inputs, batch.outputs, stream)
         tplan.set_timing(True)

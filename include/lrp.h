@@ -99,6 +99,17 @@ typedef struct lrp_opts {
                             active (bounded by max_iter), so a solve is one graph launch and the call
                             returns without waiting for it (the mixed path's second refinement step
                             is a conditional if-node of the same graph). */
+  /* Launch shapes (no counterpart in the paper).  Both are result-neutral: every
+     output is computed by the same operations in the same order whatever the
+     value, so they change only the speed (lrp_group and the autotuner in
+     tune.py pick them by timing). */
+  int32_t gemm_rows_per_thread; /* rows per thread of the narrow tall products (thread per
+                            row, at most 32 input columns): 1 or 2; 0 (default): 2 for FP32
+                            data, 1 for FP64 */
+  int32_t dst_cta_threads; /* threads per CTA of the shared-memory DST-I (n+1 <= 8192, or
+                            16384 in FP32), which then transforms threads / ((n+1)/16)
+                            columns at once: 256, 512 or 1024; 0 (default): 256.  FP64 and
+                            double-float transforms use at most 512 */
 } lrp_opts;
 
 /* Per-problem report, written by the device into caller memory. */

@@ -35,7 +35,8 @@ class lrp_opts(ctypes.Structure):
                 ("max_rhs_rank", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("m_cap", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sample_factor", ctypes.c_double),
-                ("matrix", ctypes.c_int32), ("loop_on_device", ctypes.c_int32)]
+                ("matrix", ctypes.c_int32), ("loop_on_device", ctypes.c_int32),
+                ("gemm_rows_per_thread", ctypes.c_int32), ("dst_cta_threads", ctypes.c_int32)]
 
 
 class lrp_info(ctypes.Structure):

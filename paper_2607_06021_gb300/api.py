@@ -49,7 +49,8 @@ class Plan:
     def __init__(self, n: int, tol: float, max_rank: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0,
                  check_every: int = 1, refine_steps: int = 2, selector: str = "bernoulli", sample_factor: float = 1.0,
-                 matrix: str = "poisson", loop_on_device: bool = False):
+                 matrix: str = "poisson", loop_on_device: bool = False, gemm_rows_per_thread: int = 0,
+                 dst_cta_threads: int = 0):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.batch = batch
@@ -63,6 +64,8 @@ class Plan:
         o.sample_factor = sample_factor
         o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
         o.loop_on_device = 1 if loop_on_device else 0
+        o.gemm_rows_per_thread = gemm_rows_per_thread
+        o.dst_cta_threads = dst_cta_threads
         self.n, self.tol, self.max_rank, self.batch = n, tol, max_rank, batch
         self.handle = lrp_plan(n, tol, max_rank, o)
 
@@ -282,7 +285,7 @@ class Group:
     def __init__(self, n: int, tol: float, max_rank: int, lanes: int, precision: str = "fp64", batch: int = 1,
                  max_rhs_rank: int = 64, max_iter: int = 30, m_cap: int = 0, seed: int = 0, selector: str = "bernoulli",
                  sample_factor: float = 1.0, matrix: str = "poisson", refine_steps: int = 2,
-                 loop_on_device: bool = False):
+                 loop_on_device: bool = False, gemm_rows_per_thread: int = 0, dst_cta_threads: int = 0):
         o = lrp_default_opts()
         o.precision = LRP_FP64 if precision == "fp64" else LRP_MIXED
         o.refine_steps = refine_steps
@@ -291,6 +294,8 @@ class Group:
         o.sample_factor = sample_factor
         o.matrix = {"poisson": 0, "hilbert": 1, "k": 2}[matrix]
         o.loop_on_device = 1 if loop_on_device else 0
+        o.gemm_rows_per_thread = gemm_rows_per_thread
+        o.dst_cta_threads = dst_cta_threads
         self.n, self.tol, self.max_rank, self.batch, self.lanes = n, tol, max_rank, batch, lanes
         self.handle = lrp_group_create(n, tol, max_rank, o, lanes)
         per = (batch + lanes - 1) // lanes

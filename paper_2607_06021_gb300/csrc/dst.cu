@@ -648,7 +648,7 @@ static size_t dst_half_smem(int N, int cols_per_cta) {
 
 template <typename TIn, typename TOut, typename TC>
 cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols, int nslots, int nmats,
-                        const void* tw, cudaStream_t st, void* temp, size_t temp_bytes) {
+                        const void* tw, cudaStream_t st, void* temp, size_t temp_bytes, int cta_threads) {
   const int N = (int)(n + 1);
   const double scale64 = sqrt(2.0 / (double)N);  // the orthonormal scaling, once on the host
   if (!dst_smem_supported(n, sizeof(TC) == 8)) {
@@ -685,7 +685,12 @@ cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols,
   }
   const int L = N / 2, logL = ilog2(L);
   const int Tc = L / 8;
-  const int cols_per_cta = Tc >= 256 ? 1 : 256 / Tc;
+  // columns per CTA: the requested CTA size over the Tc threads of one column,
+  // within the kernel's thread bound and the 200 KB of shared memory
+  int want = cta_threads > 0 ? cta_threads : 256;
+  if (want > dst_max_threads<TC>()) want = dst_max_threads<TC>();
+  int cols_per_cta = Tc >= want ? 1 : want / Tc;
+  while (cols_per_cta > 1 && dst_half_smem<TC>(N, cols_per_cta) > 200 * 1024) cols_per_cta >>= 1;
   const int threads = Tc * cols_per_cta;
   const size_t smem = dst_half_smem<TC>(N, cols_per_cta);
   dim3 grid((max_cols + cols_per_cta - 1) / cols_per_cta, nslots, nmats);
@@ -719,14 +724,14 @@ cudaError_t dst_configure() {
 }
 
 template cudaError_t dst1_launch<double, double, double>(int64_t, const DstBatch<double, double>&, int, int, int,
-                                                         const void*, cudaStream_t, void*, size_t);
+                                                         const void*, cudaStream_t, void*, size_t, int);
 template cudaError_t dst1_launch<double, float, float>(int64_t, const DstBatch<double, float>&, int, int, int,
-                                                       const void*, cudaStream_t, void*, size_t);
+                                                       const void*, cudaStream_t, void*, size_t, int);
 template cudaError_t dst1_launch<float, double, float>(int64_t, const DstBatch<float, double>&, int, int, int,
-                                                       const void*, cudaStream_t, void*, size_t);
+                                                       const void*, cudaStream_t, void*, size_t, int);
 template cudaError_t dst1_launch<float, float, float>(int64_t, const DstBatch<float, float>&, int, int, int,
-                                                     const void*, cudaStream_t, void*, size_t);
+                                                     const void*, cudaStream_t, void*, size_t, int);
 template cudaError_t dst1_launch<double, double, dfloat>(int64_t, const DstBatch<double, double>&, int, int, int,
-                                                         const void*, cudaStream_t, void*, size_t);
+                                                         const void*, cudaStream_t, void*, size_t, int);
 
 }  // namespace lrp

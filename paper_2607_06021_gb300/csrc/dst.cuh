@@ -37,8 +37,12 @@ bool dst_supported(int64_t n);  // n+1 <= 2^21 (shared-memory or multi-pass)
 size_t dst_temp_bytes(int64_t n, bool fp64);
 
 // temp: staging of max_cols * nslots * nmats * dst_temp_bytes(n) bytes (multi-pass only).
+// cta_threads: threads per CTA of the shared-memory kernel (256, 512 or 1024, capped
+// at 512 for FP64 and double-float; 0: 256); each column's arithmetic is the same
+// whatever the value.
 template <typename TIn, typename TOut, typename TC>
 cudaError_t dst1_launch(int64_t n, const DstBatch<TIn, TOut>& job, int max_cols, int nslots, int nmats,
-                        const void* tw, cudaStream_t st, void* temp = nullptr, size_t temp_bytes = 0);
+                        const void* tw, cudaStream_t st, void* temp = nullptr, size_t temp_bytes = 0,
+                        int cta_threads = 0);
 
 }  // namespace lrp

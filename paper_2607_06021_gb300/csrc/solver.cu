@@ -330,6 +330,8 @@ extern "C" lrp_status lrp_default_opts(lrp_opts* o) {
   o->m_cap = 0;
   o->check_every = 1;
   o->seed = 0;
+  o->gemm_rows_per_thread = 0;
+  o->dst_cta_threads = 0;
   return LRP_OK;
 }
 
@@ -357,6 +359,10 @@ static lrp_status plan_setup_host(lrp_plan_s* p, int64_t n, double tol, int32_t 
   if (o.matrix == LRP_MAT_K && n < 2) return set_error(LRP_EINVAL, "the K matrix needs n >= 2");
   if (o.check_every < 1) o.check_every = 1;
   if (o.loop_on_device != 0 && o.loop_on_device != 1) return set_error(LRP_EINVAL, "loop_on_device must be 0 or 1");
+  if (o.gemm_rows_per_thread < 0 || o.gemm_rows_per_thread > 2)
+    return set_error(LRP_EINVAL, "gemm_rows_per_thread must be 0, 1 or 2");
+  if (o.dst_cta_threads != 0 && o.dst_cta_threads != 256 && o.dst_cta_threads != 512 && o.dst_cta_threads != 1024)
+    return set_error(LRP_EINVAL, "dst_cta_threads must be 0, 256, 512 or 1024");
   const bool fp64 = (o.precision == LRP_FP64);
   if (poisson && !dst_supported(n)) return set_error(LRP_EINVAL, "n+1 must be at most 2^21");
   if (!fp64 && (o.refine_steps < 0 || o.refine_steps > 2))
@@ -585,7 +591,8 @@ extern "C" lrp_status lrp_plan_workspace_bytes(lrp_plan_t p, size_t* bytes) {
 namespace lrp {
 
 // Kernels launched by one tall GEMM / Gram call (narrow and wide variants).
-static inline int gemm_kernels(const lrp_plan_s*) { return 1; }
+// a tall product is two launches: the narrow kernel, then the general one
+static inline int gemm_kernels(const lrp_plan_s*) { return 2; }
 static inline int gram_kernels(const lrp_plan_s*) { return 1; }
 static inline int dst_kernels(const lrp_plan_s* p) { return dst_smem_supported(p->n, true) ? 1 : 2; }
 
@@ -680,6 +687,7 @@ static CoreParams make_core_params(lrp_plan_s* p, int count, double tol, double 
   const PlanDims& d = p->dims;
   CoreParams cp;
   cp.g = TallGeom{d.n, d.ld, d.M, count, d.NB, d.rows_per_block};
+  cp.g.gemm_rpt = p->opts.gemm_rows_per_thread;
   cp.st = p->st;
   cp.max_iter = p->opts.max_iter;
   cp.r_max = p->r_max;
@@ -771,13 +779,14 @@ static lrp_status phase_forward(lrp_plan_s* p, Workspace<T>& w, const CoreParams
       // FP64 data transformed in double-float arithmetic (mixed path)
       LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
                  (dst1_launch<double, double, dfloat>(d.n, job, d.RF, count, 2, p->twdf, s, p->dst_temp,
-                                                      p->dst_temp_bytes)));
+                                                      p->dst_temp_bytes, p->opts.dst_cta_threads)));
       return LRP_OK;
     }
   }
   const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
-             (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
+             (dst1_launch<double, T, T>(d.n, job, d.RF, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes,
+                                         p->opts.dst_cta_threads)));
   return LRP_OK;
 }
 
@@ -1030,13 +1039,14 @@ static lrp_status phase_finalize(lrp_plan_s* p, Workspace<T>& w, const CoreParam
     if (df && p->twdf) {
       LRP_LAUNCH(p, LRP_K_DST_DF, dst_kernels(p), s,
                  (dst1_launch<double, double, dfloat>(d.n, back, maxc, count, 2, p->twdf, s, p->dst_temp,
-                                                      p->dst_temp_bytes)));
+                                                      p->dst_temp_bytes, p->opts.dst_cta_threads)));
       return LRP_OK;
     }
   }
   const void* tw = (sizeof(T) == 8) ? p->tw64 : p->tw32;
   LRP_LAUNCH(p, LRP_K_DST, dst_kernels(p), s,
-             (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes)));
+             (dst1_launch<T, double, T>(d.n, back, maxc, count, 2, tw, s, p->dst_temp, p->dst_temp_bytes,
+                                         p->opts.dst_cta_threads)));
   return LRP_OK;
 }
 
@@ -1557,6 +1567,6 @@ extern "C" const char* lrp_status_string(lrp_status s) {
   return "LRP_UNKNOWN";
 }
 
-static_assert(sizeof(lrp_opts) == 56, "lrp_opts layout");
+static_assert(sizeof(lrp_opts) == 64, "lrp_opts layout");
 static_assert(sizeof(lrp_info) == 64, "lrp_info layout");
 static_assert(sizeof(lrp_problem) == 104, "lrp_problem layout");

@@ -19,6 +19,9 @@ struct TallGeom {
   // when null.  The Cross-DEIM iterations launch over the compacted list of
   // the slots still active, so that finished slots cost no CTAs.
   const int32_t* act = nullptr;
+  // Rows per thread of the narrow (thread-per-row) products, 1 or 2 (0: 2 for
+  // FP32 data, 1 for FP64); a launch shape only, outputs do not depend on it.
+  int gemm_rpt = 0;
 };
 
 __device__ __forceinline__ int slot_of(const TallGeom& g, int i) { return g.act ? g.act[i] : i; }

@@ -1,4 +1,5 @@
-"""Autotuning of batched solves: lane count and loop placement (lrp_group).
+"""Autotuning of batched solves: lane count, loop placement and two launch
+shapes (lrp_group, lrp_opts).
 
 A batch solved as `lanes` concurrent sub-batches returns exactly the results of
 one plan (same per-problem kernels and arithmetic), and a plan whose iteration
@@ -13,6 +14,15 @@ inputs (one untimed warm-up that also captures the graphs, then timed runs with
 CUDA events on the caller's stream) and keeps the fastest in a JSON table keyed
 by precision, n, right-hand-side rank class and batch size.  Only the timing
 runs touch the GPU; the selection and the table are host logic.
+
+The launch shapes are tuned next, one at a time at the chosen (lanes, loop
+placement), each value timed with the others at their best so far:
+`gemm_rows_per_thread` (rows per thread of the narrow tall products: 1 keeps
+more warps resident, 2 halves the shared-memory reads per multiply-add) and
+`dst_cta_threads` (columns of the shared-memory DST per CTA).  Neither changes
+an operation or its order, so every candidate must return the same bits; the
+tuner compares each candidate's outputs with the first one's and refuses a
+table entry if any differ.
 
     python -m paper_2607_06021_gb300.tune --write TABLE.json
 
@@ -31,6 +41,9 @@ DEFAULT_LANES = (1, 2, 4, 8)
 # (lanes, loop on the device)
 DEFAULT_CONFIGS = ((1, False), (2, False), (4, False), (8, False), (1, True), (2, True), (4, True))
 TIE = 0.01  # candidates within 1% of the fastest count as ties
+# result-neutral launch shapes (lrp_opts fields), values in order of preference on ties
+SHAPE_KNOBS = (("gemm_rows_per_thread", (2, 1)), ("dst_cta_threads", (256, 512, 1024)))
+DEFAULT_SHAPES = {"gemm_rows_per_thread": 0, "dst_cta_threads": 0}
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
@@ -88,6 +101,32 @@ def tune_configs(measure: Callable[[Tuple[int, bool]], List[float]], batch: int,
     return choose(times), times
 
 
+def choose_first(times: Dict, order) -> object:
+    """The fastest value by median; values within TIE of it count as ties, which
+    go to the earliest value in `order`."""
+    med = {c: statistics.median(ts) for c, ts in times.items() if ts}
+    if not med:
+        raise ValueError("no timed candidate")
+    best = min(med.values())
+    return next(c for c in order if c in med and med[c] <= best * (1.0 + TIE))
+
+
+def tune_shapes(measure: Callable[[Dict[str, int]], List[float]], knobs=SHAPE_KNOBS):
+    """Coordinate descent over the launch shapes: for each knob in turn, time
+    every value with the other knobs at their best so far (starting from the
+    first listed value of each); measure(shapes) -> timed runs (ms).  Returns the
+    chosen shapes and {knob: {value: [ms]}}."""
+    best = {name: values[0] for name, values in knobs}
+    times: Dict[str, Dict[int, List[float]]] = {}
+    for name, values in knobs:
+        t = {}
+        for v in values:
+            t[v] = list(measure(dict(best, **{name: v})))
+        best[name] = choose_first(t, values)
+        times[name] = t
+    return best, times
+
+
 class TuneTable:
     """Chosen configurations, persisted as JSON
     ({key: {"lanes": L, "loop_on_device": bool, "ms": {name: median}}})."""
@@ -102,6 +141,11 @@ class TuneTable:
     def get_config(self, precision: str, n: int, r_f: int, batch: int) -> Optional[Tuple[int, bool]]:
         e = self.entries.get(table_key(precision, n, r_f, batch))
         return (int(e["lanes"]), bool(e.get("loop_on_device", False))) if e else None
+
+    def get_shapes(self, precision: str, n: int, r_f: int, batch: int) -> Dict[str, int]:
+        """The tuned launch shapes (lrp_opts fields; 0 = the library default)."""
+        e = self.entries.get(table_key(precision, n, r_f, batch)) or {}
+        return {k: int(e.get(k, DEFAULT_SHAPES[k])) for k in DEFAULT_SHAPES}
 
     def get(self, precision: str, n: int, r_f: int, batch: int) -> Optional[int]:
         c = self.get_config(precision, n, r_f, batch)
@@ -173,6 +217,53 @@ def autotune_group(n: int, tol: float, max_rank: int, inputs, precision: str = "
     return cfg, times
 
 
+def autotune_shapes(n: int, tol: float, max_rank: int, inputs, cfg, precision: str = "mixed", reps: int = 3,
+                    stream=None, knobs=SHAPE_KNOBS, **group_kw):
+    """The launch shapes for `inputs` at the (lanes, device loop) configuration
+    `cfg`, by tune_shapes; every candidate's outputs (U, S, V, info of every
+    problem) must equal the first candidate's bit for bit, else RuntimeError.
+    Returns (shapes, {knob: {value: [ms]}})."""
+    import torch
+
+    from .api import Group, parse_info
+    batch = len(inputs)
+    r_f = max(int(U.shape[1]) for U, _, _ in inputs)
+    s = torch.cuda.current_stream() if stream is None else stream
+    lanes, dev = (cfg, False) if isinstance(cfg, int) else cfg
+    ref = []
+
+    def measure(shapes) -> List[float]:
+        g = Group(n, tol, max_rank, lanes=lanes, precision=precision, batch=batch, max_rhs_rank=r_f,
+                  loop_on_device=dev, **shapes, **group_kw)
+        try:
+            outs = [g.alloc_outputs() for _ in inputs]
+            g.solve_batch_into(inputs, outs, s)
+            torch.cuda.synchronize()
+            # the defined part of each result: rank columns of U and V, rank values
+            # of S, and the info record (columns past the rank are unspecified)
+            flat = []
+            for U, S, V, info in outs:
+                r = int(parse_info(info)["rank"])
+                flat += [U[:, :r].clone(), S[:r].clone(), V[:, :r].clone(), info.clone()]
+            if not ref:
+                ref.extend(flat)
+            elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
+                raise RuntimeError(f"launch shapes {shapes} changed the results")
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                g.solve_batch_into(inputs, outs, s)
+                e1.record(s)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return ms
+        finally:
+            g.close()
+
+    return tune_shapes(measure, knobs)
+
+
 def _main():
     import argparse
     import sys
@@ -201,10 +292,15 @@ def _main():
             t0 = time.time()
             cfg, times = autotune_group(4095, 1e-8, 64, inputs, precision=prec, table=None, m_cap=64,
                                         max_iter=30)
-            table.put(prec, 4095, 20, B, cfg, times, {"gpu": gpu, "tuned_s": round(time.time() - t0, 1)})
+            shapes, stimes = autotune_shapes(4095, 1e-8, 64, inputs, cfg, precision=prec, m_cap=64, max_iter=30)
+            extra = {"gpu": gpu, "tuned_s": round(time.time() - t0, 1), "shapes_identical": True,
+                     "shape_ms": {k: {str(v): round(statistics.median(t), 3) for v, t in tv.items()}
+                                  for k, tv in stimes.items()}}
+            extra.update(shapes)
+            table.put(prec, 4095, 20, B, cfg, times, extra)
             table.save()
             print(prec, B, config_name(cfg), {config_name(k): round(statistics.median(v), 2) for k, v in times.items()},
-                  flush=True)
+                  shapes, extra["shape_ms"], flush=True)
 
 
 if __name__ == "__main__":

@@ -82,7 +82,7 @@ def test_option_checks_need_no_gpu():
 
 def test_struct_layouts_match_header():
     pkg = pytest.importorskip("paper_2607_06021_gb300")
-    assert ctypes.sizeof(pkg.lrp_opts) == 56
+    assert ctypes.sizeof(pkg.lrp_opts) == 64
     assert ctypes.sizeof(pkg.lrp_info) == 64
     assert ctypes.sizeof(pkg.lrp_problem) == 104
     assert ctypes.sizeof(pkg.lrp_server_opts) == 24
@@ -127,3 +127,17 @@ def test_request_footprint_formula():
     assert pkg.lrp_request_footprint(262143, 48, 128) == 8 * 262143 * (96 + 4 * 256 + 256)
     assert pkg.lrp_request_footprint(1023, 2, 8) == 8 * 1023 * (4 + 4 * 32 + 16)
     assert pkg.lrp_request_footprint(255, 0, 8) == 0
+
+
+def test_launch_shape_options_are_checked():
+    import paper_2607_06021_gb300 as pkg
+    for field, bad in (("gemm_rows_per_thread", 3), ("gemm_rows_per_thread", -1), ("dst_cta_threads", 300),
+                       ("dst_cta_threads", 2048)):
+        o = pkg.lrp_default_opts()
+        setattr(o, field, bad)
+        with pytest.raises(pkg.LrpError):
+            pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o)
+    o = pkg.lrp_default_opts()
+    assert o.gemm_rows_per_thread == 0 and o.dst_cta_threads == 0
+    o.gemm_rows_per_thread, o.dst_cta_threads = 1, 1024
+    assert pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, o) == pkg.lrp_plan_estimate_bytes(4095, 1e-8, 64, None)

@@ -87,3 +87,47 @@ def test_table_round_trip_with_loop_placement(tmp_path):
                                              "gpu": "x"}
     t2 = tune.TuneTable(path)
     assert t2.get_config("mixed", 4095, 20, 256) == (2, True) and t2.get("mixed", 4095, 20, 256) == 2
+
+
+def test_shape_descent_times_each_value_with_the_best_so_far():
+    # gemm rows per thread: 1 is faster; DST threads: 512 is faster only with rpt 1
+    def cost(sh):
+        c = 100.0 if sh["gemm_rows_per_thread"] == 2 else 80.0
+        if sh["dst_cta_threads"] == 512 and sh["gemm_rows_per_thread"] == 1:
+            c -= 5.0
+        if sh["dst_cta_threads"] == 1024:
+            c += 3.0
+        return c
+
+    seen = []
+
+    def measure(sh):
+        seen.append(dict(sh))
+        return [cost(sh)] * 3
+
+    best, times = tune.tune_shapes(measure)
+    assert best == {"gemm_rows_per_thread": 1, "dst_cta_threads": 512}
+    # first knob timed at the other's first value, second at the first's best
+    assert seen[:2] == [{"gemm_rows_per_thread": 2, "dst_cta_threads": 256},
+                        {"gemm_rows_per_thread": 1, "dst_cta_threads": 256}]
+    assert all(s["gemm_rows_per_thread"] == 1 for s in seen[2:]) and len(seen) == 5
+    assert set(times) == {"gemm_rows_per_thread", "dst_cta_threads"}
+
+
+def test_shape_ties_go_to_the_first_listed_value():
+    best, _ = tune.tune_shapes(lambda sh: [100.0 + 0.5 * (sh["dst_cta_threads"] == 256)])
+    assert best == {"gemm_rows_per_thread": 2, "dst_cta_threads": 256}  # within 1%: first listed
+    assert tune.choose_first({1: [100.0], 2: [99.5]}, (2, 1)) == 2
+    assert tune.choose_first({1: [90.0], 2: [99.5]}, (2, 1)) == 1
+
+
+def test_table_keeps_the_shapes(tmp_path):
+    path = str(tmp_path / "t.json")
+    t = tune.TuneTable(path)
+    assert t.get_shapes("mixed", 4095, 20, 1024) == {"gemm_rows_per_thread": 0, "dst_cta_threads": 0}
+    t.put("mixed", 4095, 20, 1024, (8, False), {(8, False): [1.0]},
+          {"gemm_rows_per_thread": 1, "dst_cta_threads": 512})
+    t.save()
+    t2 = tune.TuneTable(path)
+    assert t2.get_shapes("mixed", 4095, 20, 1024) == {"gemm_rows_per_thread": 1, "dst_cta_threads": 512}
+    assert t2.get_config("mixed", 4095, 20, 1024) == (8, False)
