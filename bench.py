@@ -594,11 +594,15 @@ def serving_stream(args, rank, rate=None, requests=None, kmax=None, lanes=2, cap
         tickets[i] = t
         delay_us[i] = max(0.0, (time.perf_counter() - t0 - arrivals[i]) * 1e6)
     lat, warm_hits, statuses, by_class = np.zeros(R), 0, {}, {}
+    service = {}  # per class: batch start to completion (ms), and time queued (ms)
     kept = []
     for i, t in enumerate(tickets):
         res = sv.wait(t, 600.0)
         info = res[3]
         lat[i] = info["latency_us"] + delay_us[i]
+        sc = service.setdefault(f"n={specs[i]['n']},{specs[i]['prec']}", [[], []])
+        sc[0].append((info["latency_us"] - info["queue_us"]) / 1e3)
+        sc[1].append((info["queue_us"] + delay_us[i]) / 1e3)
         warm_hits += info["warm_used"]
         statuses[info["status"]] = statuses.get(info["status"], 0) + 1
         cls = f"n={specs[i]['n']},{specs[i]['prec']}"
@@ -618,7 +622,12 @@ def serving_stream(args, rank, rate=None, requests=None, kmax=None, lanes=2, cap
            "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
            "mean_ms": float(lat.mean()) / 1e3, "rejected_submits": st["rejected"], "warm_hits": warm_hits,
            "status_counts": {lrp.status_string(k): v for k, v in statuses.items()},
-           "status_by_class": by_class, "lanes": lanes, "memory_cap_gb": cap_gb,
+           "status_by_class": by_class,
+           "time_by_class_ms": {k: {"requests": len(v[0]), "service_mean": round(float(np.mean(v[0])), 2),
+                                    "service_total": round(float(np.sum(v[0])), 1),
+                                    "queue_mean": round(float(np.mean(v[1])), 2)}
+                                for k, v in sorted(service.items())},
+           "lanes": lanes, "memory_cap_gb": cap_gb,
            "workload": f"n=2^k-1, k~U{{8..{kmax}}}, r_f~U{{2..48}} Gaussians, "
                        f"{100 * (1 - args.serve_frac_fp64):.0f}% mixed/1e-6, {100 * args.serve_frac_fp64:.0f}% FP64/1e-10, "
                        "rank cap 64, 10% perturbed repeats (warm keys), Poisson arrivals; "
