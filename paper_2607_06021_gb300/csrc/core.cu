@@ -680,7 +680,8 @@ __global__ void k_select(CoreParams p, CoreBufs<T> b, int sel_c, int sort_len) {
       }
       set[cnt++] = (int32_t)g;
     }
-    if (cnt >= M) stp->flags |= kFlagCapacity;
+    // both sides' CTAs may set the bit at once: an atomic OR loses neither
+    if (cnt >= M) atomicOr(reinterpret_cast<unsigned int*>(&stp->flags), (unsigned int)kFlagCapacity);
     stp->cnt[side] = cnt;
   }
 }

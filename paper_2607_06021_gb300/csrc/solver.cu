@@ -591,8 +591,10 @@ extern "C" lrp_status lrp_plan_workspace_bytes(lrp_plan_t p, size_t* bytes) {
 namespace lrp {
 
 // Kernels launched by one tall GEMM / Gram call (narrow and wide variants).
-// a tall product is two launches: the narrow kernel, then the general one
-static inline int gemm_kernels(const lrp_plan_s*) { return 2; }
+// launches of one tall product: the thread-per-row kernel, and the register-
+// tiled one when the index capacity allows wider products
+template <typename T = float>
+static inline int gemm_kernels(const lrp_plan_s* p) { return gemm_wide_possible<T>(p->dims.M) ? 2 : 1; }
 static inline int gram_kernels(const lrp_plan_s*) { return 1; }
 static inline int dst_kernels(const lrp_plan_s* p) { return dst_smem_supported(p->n, true) ? 1 : 2; }
 
@@ -655,7 +657,7 @@ static lrp_status cholqr(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, cons
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 0, s));
   if (passes < 2) return LRP_OK;
-  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels<T>(p), s,
              launch_gemm_nn<T>(g, p->st, cs(X, side_stride, slot_stride), sel, P, sel, Strided<T>{w.Q1, nm, 2 * nm},
                                none, 0, s));
   // Later passes see a well-conditioned basis: FP32 data keep an FP32 Gram.
@@ -665,7 +667,7 @@ static lrp_status cholqr(lrp_plan_s* p, Workspace<T>& w, const TallGeom& g, cons
     return st;
   LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_chol<T>(cp, cb, sel, 1, s));
   if (passes < 3) return LRP_OK;
-  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+  LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels<T>(p), s,
              launch_gemm_nn<T>(g, p->st, cs<T>(w.Q1, nm, 2 * nm), sel, P, sel, Strided<T>{w.Q2, nm, 2 * nm}, none, 0,
                                s));
   if ((st = gram_reduce<T>(p, g, cs<T>(w.Q2, nm, 2 * nm), sel, cs<T>(w.Q2, nm, 2 * nm), sel, w.part, G, true, s,
@@ -876,7 +878,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
     lrp_status st = cholqr3<T>(p, w, g, cp, cb, w.Fh, fm, 2 * fm, kDimRF, s);
     if (st) return st;
     LRP_LAUNCH(p, LRP_K_CHOL, 1, s, launch_orth_keep<T>(cp, cb, s));
-    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels<T>(p), s,
                launch_gemm_nn<T>(g, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimRF, Strided<const double>{w.P, MM, 2 * MM},
                                  kDimC0, Strided<T>{w.U[1], nm, 2 * nm}, none, 0, s));
     // Warm-started slots replace U_{-1}, V_{-1} and the index sets with their record.
@@ -922,7 +924,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
     lrp_status st = cholqr3<T>(p, w, gi, cpi, cb, w.A, nm, 2 * nm, kDimOther, s);
     if (st) return st;
     LRP_LAUNCH(p, LRP_K_CORE, 1, s, launch_core<T>(cpi, cb, par, s));
-    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+    LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels<T>(p), s,
                launch_gemm_nn<T>(gi, p->st, cs<T>(w.Q2, nm, 2 * nm), kDimOther,
                                  Strided<const double>{w.Bf, MM, 2 * MM}, kDimR, Strided<T>{w.U[par], nm, 2 * nm},
                                  none, 0, s));
@@ -933,7 +935,7 @@ static lrp_status phase_iterate(lrp_plan_s* p, Workspace<T>& w, const CoreParams
       st = gram_reduce<T>(p, gi, cs<T>(w.U[par], nm, 2 * nm), kDimR, cs<T>(w.U[1 - par], nm, 2 * nm), kDimRPrev,
                           w.part, Gx, false, s, sizeof(T) == 8);
       if (st) return st;
-      LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels(p), s,
+      LRP_LAUNCH(p, gemm_class<T>(), gemm_kernels<T>(p), s,
                  launch_gemm_nn<T>(gi, p->st, cs<T>(w.U[par], nm, 2 * nm), kDimR,
                                    Strided<const double>{w.X, MM, 2 * MM}, kDimRPrev,
                                    Strided<T>{w.Q1, nm, 2 * nm}, cs<T>(w.U[1 - par], nm, 2 * nm), 1, s));
@@ -1207,7 +1209,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_residual(rstep, count, s));
       if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 1))) return st;
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 0, p->mixed_residual_tol, rcap_res, s));
-      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels<double>(p), s,
                  launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.A, nm, 2 * nm), kDimX,
                                         Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                         Strided<double>{p->w64.Q1, nm, 2 * nm}, none, 0, s));
@@ -1264,7 +1266,7 @@ static lrp_status run_mixed(lrp_plan_s* p, int count, cudaStream_t s) {
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_assemble_sum(ra, count, s));
       if ((st = cholqr<double>(p, p->w64, g, c64, cb64, p->w64.A, nm, 2 * nm, kDimX, s, 2))) return st;
       LRP_LAUNCH(p, LRP_K_REFINE, 1, s, launch_recompress(ra, count, 1, 0.0, d.M, s));
-      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels(p), s,
+      LRP_LAUNCH(p, LRP_K_GEMM, gemm_kernels<double>(p), s,
                  launch_gemm_nn<double>(g, p->st, cs<double>(p->w64.Q1, nm, 2 * nm), kDimX,
                                         Strided<const double>{p->w64.Bf, MM, 2 * MM}, kDimR,
                                         Strided<double>{p->w64.U[0], nm, 2 * nm}, none, 0, s));

@@ -360,31 +360,44 @@ __device__ __forceinline__ void gemm_rows(const TallGeom& g, const T* __restrict
   }
 }
 
-// The products with mi <= 32 input columns and mo <= 64 outputs, thread per row
-// with RPT rows per thread, in a kernel of their own: holding only this path's
-// registers (RPT = 1: ~50, RPT = 2: ~80) it keeps more warps resident than the
-// general kernel, whose widest path sets its register count.  Problems of other
-// widths return at once here and are served by k_gemm_nn.
+// Thread-per-row products in a kernel of their own: mi <= 32 input columns and
+// mo <= 64 outputs with RPT rows per thread (RPT = 2 halves the shared-memory
+// reads per multiply-add, RPT = 1 halves the registers of that path), and
+// (FP32) mi <= 64 with one row per thread.  Problems of other widths return at
+// once here and are served by k_gemm_nn, which is launched only when the plan's
+// index capacity allows such widths, so that the common case is one launch
+// without the register-tiled paths' registers.
+template <typename T>
+__host__ __device__ constexpr bool gemm_rows_covers(int mi, int mo) {
+  return mo <= 64 && (mi <= 32 || (sizeof(T) == 4 && mi <= 64));
+}
+
 template <typename T, int RPT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (RPT == 1 ? 4 : 3) : 2) k_gemm_narrow(TallGeom g, const SolveState* __restrict__ st_all,
-                                                    Strided<const T> in, int sel_in, Strided<const double> bm,
-                                                    int sel_out, Strided<T> out, Strided<const T> zsub, int mode) {
+__global__ void __launch_bounds__(NT, 2)
+    k_gemm_narrow(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in, int sel_in,
+                  Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode) {
   const int slot = slot_of(g, blockIdx.z >> 1), side = blockIdx.z & 1;
   if (slot < 0) return;
   const SolveState& st = st_all[slot];
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
   const int rbase = blockIdx.x * kGemmRows * kGemmTiles;
-  if (rbase >= g.n || mo < 1 || !(mo <= 64 && mi <= 32)) return;
-  __shared__ __align__(16) T Bt[64][32];
-  gemm_rows<T, 32, RPT>(g, in.at(slot, side), bm.at(slot, side), out.at(slot, side),
-                        (mode == 1) ? zsub.at(slot, side) : nullptr, mode, mi, mo, rbase, Bt);
+  if (rbase >= g.n || mo < 1 || !gemm_rows_covers<T>(mi, mo)) return;
+  __shared__ __align__(16) T Bs[64][64];
+  const T* X = in.at(slot, side);
+  const double* Bm = bm.at(slot, side);
+  T* O = out.at(slot, side);
+  const T* Z = (mode == 1) ? zsub.at(slot, side) : nullptr;
+  if (mi <= 32) {
+    gemm_rows<T, 32, RPT>(g, X, Bm, O, Z, mode, mi, mo, rbase, reinterpret_cast<T(*)[32]>(&Bs[0][0]));
+  } else if constexpr (sizeof(T) == 4) {
+    gemm_rows<T, 64, 1>(g, X, Bm, O, Z, mode, mi, mo, rbase, Bs);
+  }
 }
 
-// Every other width (the narrow products above are left to k_gemm_narrow): a
-// CTA owns kGemmTiles x kGemmRows rows.  mi <= 64 with mo <= 64 in FP32 runs
-// thread per row; wider products as register tiles, one 32-wide column block
-// when mo <= 32, else 64-wide blocks.
+// Every width the thread-per-row kernel leaves: a CTA owns kGemmTiles x
+// kGemmRows rows, register tiles, one 32-wide column block when mo <= 32,
+// else 64-wide blocks.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __restrict__ st_all, Strided<const T> in,
                                                 int sel_in, Strided<const double> bm, int sel_out, Strided<T> out,
@@ -395,7 +408,7 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   if (!st.active) return;
   const int mi = dim_of(st, side, sel_in), mo = dim_of(st, side, sel_out);
   const int rbase = blockIdx.x * kGemmRows * kGemmTiles;
-  if (rbase >= g.n || mo < 1 || (mo <= 64 && mi <= 32)) return;
+  if (rbase >= g.n || mo < 1 || gemm_rows_covers<T>(mi, mo)) return;
   __shared__ __align__(16) T As[TK][kGemmRows];
   __shared__ __align__(16) T Bs[64][64];
   const T* X = in.at(slot, side);
@@ -405,12 +418,6 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(TallGeom g, const SolveState* __
   // 4-row vectors need 16-byte aligned columns (ld is a multiple of 32)
   const bool vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(O) |
                      reinterpret_cast<uintptr_t>(Z)) & 15) == 0 && (g.ld & 3) == 0;
-  if constexpr (sizeof(T) == 4) {
-    if (mo <= 64 && mi <= 64) {
-      gemm_rows<T, 64, 1>(g, X, Bm, O, Z, mode, mi, mo, rbase, Bs);
-      return;
-    }
-  }
   if (mo <= 32) {
     gemm_block<T, 32>(g, X, Bm, O, Z, mode, mi, mo, rbase, 0, vec, As, Bs);
   } else {
@@ -935,14 +942,15 @@ template <typename T>
 cudaError_t launch_gemm_nn(const TallGeom& g, const SolveState* st, Strided<const T> in, int sel_in,
                            Strided<const double> bm, int sel_out, Strided<T> out, Strided<const T> zsub, int mode,
                            cudaStream_t s) {
-  // two launches over the same problems: the narrow products, then every other width
+  // the thread-per-row widths, then (when the index capacity allows wider
+  // products) every other width, over the same problems
   const dim3 grid(cdiv(g.n, kGemmRows * kGemmTiles), 1, g.nslots * 2);
   const int rpt = g.gemm_rpt > 0 ? g.gemm_rpt : (sizeof(T) == 4 ? 2 : 1);
   if (rpt == 2)
     k_gemm_narrow<T, 2><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
   else
     k_gemm_narrow<T, 1><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
-  k_gemm_nn<T><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
+  if (gemm_wide_possible<T>(g.M)) k_gemm_nn<T><<<grid, NT, 0, s>>>(g, st, in, sel_in, bm, sel_out, out, zsub, mode);
   return cudaGetLastError();
 }
 

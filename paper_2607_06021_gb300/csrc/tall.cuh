@@ -26,6 +26,15 @@ struct TallGeom {
 
 __device__ __forceinline__ int slot_of(const TallGeom& g, int i) { return g.act ? g.act[i] : i; }
 
+// Whether a tall product of data type T with index capacity M (every width is
+// at most M) can need the register-tiled kernel: wider than the thread-per-row
+// kernel's 32 input columns (64 for FP32) or 64 outputs.  Such products take a
+// second launch.
+template <typename T>
+inline bool gemm_wide_possible(int M) {
+  return M > (sizeof(T) == 4 ? 64 : 32);
+}
+
 template <typename T>
 struct CrossArgs {
   Strided<const T> F;          // transformed RHS factors, n x rf, ld = geom.ld
