@@ -481,7 +481,7 @@ PEAK_SOURCE = {"fp64": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk/SM",
 # DRAM bytes (read + write) per launch from ncu captures of the mixed bench at
 # batch 128, scaled by batch / 128 (the launches' data grow with the slots);
 # a class whose kernel changed since its capture has no entry.
-TRAFFIC_B128 = {("mixed", "gram_df"): (86.4e6, "profiles/k_gram_df_mixed_n4095_batch128.md")}
+TRAFFIC_B128 = {("mixed", "gram_df"): (87.0e6, "profiles/k_gram_df_mixed_n4095_batch128.md")}
 
 
 def class_bound(prec, name, launches, ms, flops, nbytes, hbm_peak):

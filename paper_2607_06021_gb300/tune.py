@@ -20,9 +20,13 @@ placement), each value timed with the others at their best so far:
 `gemm_rows_per_thread` (rows per thread of the narrow tall products: 1 keeps
 more warps resident, 2 halves the shared-memory reads per multiply-add) and
 `dst_cta_threads` (columns of the shared-memory DST per CTA).  Neither changes
-an operation or its order, so every candidate must return the same bits; the
-tuner compares each candidate's outputs with the first one's and refuses a
-table entry if any differ.
+an operation or its order: single plans return the same bits under every value
+(a GPU test).  The tuner checks this for every candidate on a single plan
+(one lane) of the first problems, bit for bit, and refuses the candidate
+otherwise; the timing runs use the chosen lanes, where the results of
+concurrent lanes have been seen to part in rare problems (the largest relative
+difference of the low-rank products between the candidates' timing runs is
+recorded).
 
     python -m paper_2607_06021_gb300.tune --write TABLE.json
 
@@ -218,37 +222,58 @@ def autotune_group(n: int, tol: float, max_rank: int, inputs, precision: str = "
 
 
 def autotune_shapes(n: int, tol: float, max_rank: int, inputs, cfg, precision: str = "mixed", reps: int = 3,
-                    stream=None, knobs=SHAPE_KNOBS, **group_kw):
+                    stream=None, knobs=SHAPE_KNOBS, check: int = 64, **group_kw):
     """The launch shapes for `inputs` at the (lanes, device loop) configuration
-    `cfg`, by tune_shapes; every candidate's outputs (U, S, V, info of every
-    problem) must equal the first candidate's bit for bit, else RuntimeError.
-    Returns (shapes, {knob: {value: [ms]}})."""
+    `cfg`, by tune_shapes.  Each candidate first solves the first `check`
+    problems on a single plan; its results must equal the first candidate's bit
+    for bit (rank columns of U, V, rank values of S, the info record), else
+    RuntimeError.  Returns (shapes, {knob: {value: [ms]}}, the largest relative
+    difference of the low-rank products between the timing runs' results)."""
     import torch
 
-    from .api import Group, parse_info
+    from .api import Group, Plan, parse_info
     batch = len(inputs)
     r_f = max(int(U.shape[1]) for U, _, _ in inputs)
     s = torch.cuda.current_stream() if stream is None else stream
     lanes, dev = (cfg, False) if isinstance(cfg, int) else cfg
-    ref = []
+    ref_plan, ref = [], []
+    worst = [0.0]
+    sub = inputs[:max(1, min(check, batch))]
+
+    def defined(outs):
+        # rank columns of U and V, rank values of S, the info record (columns
+        # past the rank are unspecified)
+        res = []
+        for U, S, V, info in outs:
+            r = int(parse_info(info)["rank"])
+            res.append((U[:, :r].clone(), S[:r].clone(), V[:, :r].clone(), info.clone()))
+        return res
 
     def measure(shapes) -> List[float]:
+        p = Plan(n, tol, max_rank, precision=precision, batch=len(sub), max_rhs_rank=r_f, **shapes, **group_kw)
+        try:
+            outs = [p.alloc_outputs() for _ in sub]
+            p.solve_batch_into(sub, outs, s)
+            torch.cuda.synchronize()
+            res = defined(outs)
+        finally:
+            p.close()
+        if not ref_plan:
+            ref_plan.extend(res)
+        elif not all(x.shape == y.shape and torch.equal(x, y) for a, b in zip(ref_plan, res) for x, y in zip(a, b)):
+            raise RuntimeError(f"launch shapes {shapes} changed a single plan's results")
         g = Group(n, tol, max_rank, lanes=lanes, precision=precision, batch=batch, max_rhs_rank=r_f,
                   loop_on_device=dev, **shapes, **group_kw)
         try:
             outs = [g.alloc_outputs() for _ in inputs]
             g.solve_batch_into(inputs, outs, s)
             torch.cuda.synchronize()
-            # the defined part of each result: rank columns of U and V, rank values
-            # of S, and the info record (columns past the rank are unspecified)
-            flat = []
-            for U, S, V, info in outs:
-                r = int(parse_info(info)["rank"])
-                flat += [U[:, :r].clone(), S[:r].clone(), V[:, :r].clone(), info.clone()]
+            res = [x[:3] for x in defined(outs)]
             if not ref:
-                ref.extend(flat)
-            elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
-                raise RuntimeError(f"launch shapes {shapes} changed the results")
+                ref.extend(res)
+            else:
+                for a, b in zip(ref, res):
+                    worst[0] = max(worst[0], lowrank_rel_diff(a, b))
             ms = []
             for _ in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -261,7 +286,22 @@ def autotune_shapes(n: int, tol: float, max_rank: int, inputs, cfg, precision: s
         finally:
             g.close()
 
-    return tune_shapes(measure, knobs)
+    shapes, times = tune_shapes(measure, knobs)
+    return shapes, times, worst[0]
+
+
+def lowrank_rel_diff(a, b) -> float:
+    """||U S V^T - U' S' V'^T||_F / ||U S V^T||_F of two results (U, S, V)
+    without forming the n x n products: Gram identity on the small factors."""
+    import torch
+    if all(x.shape == y.shape and torch.equal(x, y) for x, y in zip(a, b)):
+        return 0.0
+    U, S, V = (t.double() for t in a)
+    U2, S2, V2 = (t.double() for t in b)
+    aa = float((S * S).sum()) if S.numel() else 0.0
+    bb = float((S2 * S2).sum()) if S2.numel() else 0.0
+    ab = float(((S[:, None] * (U.T @ U2)) * ((V.T @ V2) * S2[None, :])).sum()) if S.numel() and S2.numel() else 0.0
+    return (max(aa + bb - 2.0 * ab, 0.0) ** 0.5) / max(aa ** 0.5, 1e-300)
 
 
 def _main():
@@ -292,8 +332,9 @@ def _main():
             t0 = time.time()
             cfg, times = autotune_group(4095, 1e-8, 64, inputs, precision=prec, table=None, m_cap=64,
                                         max_iter=30)
-            shapes, stimes = autotune_shapes(4095, 1e-8, 64, inputs, cfg, precision=prec, m_cap=64, max_iter=30)
-            extra = {"gpu": gpu, "tuned_s": round(time.time() - t0, 1), "shapes_identical": True,
+            shapes, stimes, worst = autotune_shapes(4095, 1e-8, 64, inputs, cfg, precision=prec, m_cap=64,
+                                                    max_iter=30)
+            extra = {"gpu": gpu, "tuned_s": round(time.time() - t0, 1), "shapes_max_rel_diff": worst,
                      "shape_ms": {k: {str(v): round(statistics.median(t), 3) for v, t in tv.items()}
                                   for k, tv in stimes.items()}}
             extra.update(shapes)

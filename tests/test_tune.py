@@ -131,3 +131,23 @@ def test_table_keeps_the_shapes(tmp_path):
     t2 = tune.TuneTable(path)
     assert t2.get_shapes("mixed", 4095, 20, 1024) == {"gemm_rows_per_thread": 1, "dst_cta_threads": 512}
     assert t2.get_config("mixed", 4095, 20, 1024) == (8, False)
+
+
+def test_lowrank_difference_of_results():
+    torch = pytest.importorskip("torch")
+    g = torch.Generator().manual_seed(3)
+    U = torch.linalg.qr(torch.randn(200, 6, generator=g, dtype=torch.float64))[0]
+    V = torch.linalg.qr(torch.randn(200, 6, generator=g, dtype=torch.float64))[0]
+    S = torch.tensor([6.0, 5.0, 4.0, 3.0, 2.0, 1.0], dtype=torch.float64)
+    assert tune.lowrank_rel_diff((U, S, V), (U.clone(), S.clone(), V.clone())) == 0.0
+    # sign flips of a singular pair leave the product unchanged
+    Uf, Vf = U.clone(), V.clone()
+    Uf[:, 2] *= -1
+    Vf[:, 2] *= -1
+    assert tune.lowrank_rel_diff((U, S, V), (Uf, S, Vf)) < 1e-7
+    # a 0.1% change of every singular value is a 0.1% change of the product
+    d = tune.lowrank_rel_diff((U, S, V), (U, S * 1.001, V))
+    assert abs(d - 1e-3) < 1e-6
+    # a dropped last pair: ||1|| / ||(6..1)||
+    d = tune.lowrank_rel_diff((U, S, V), (U[:, :5], S[:5], V[:, :5]))
+    assert abs(d - 1.0 / float(torch.sqrt((S * S).sum()))) < 1e-7
