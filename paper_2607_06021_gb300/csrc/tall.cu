@@ -4,7 +4,8 @@
 //  k_cross     C = What(:,J) and R^T = What(I,:)^T from the transformed
 //              right-hand side (Algorithm scross, "C = G(:,J), R = G(I,:)";
 //              entries by Eq. g_for_p at O(r_f) each, Sec. 2.1 / Sec. 3.2).
-//  k_gemm_nn   n x m times m x m' (the triangular applies of CholeskyQR, the
+//  k_gemm_narrow, k_gemm_nn
+//              n x m times m x m' (the triangular applies of CholeskyQR, the
 //              factor update U_k = Q U~ of Algorithm scross, and E = U' - U X):
 //              thread per row for narrow products, register tiles otherwise.
 //  k_gram_*    per-row-block partial products X^T Y (Gram matrices of
