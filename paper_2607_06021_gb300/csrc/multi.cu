@@ -171,7 +171,8 @@ extern "C" lrp_status lrp_multi_solve(lrp_multi_t m, int32_t count, const int64_
         m->launches[(size_t)b * LRP_K_COUNT + c] = p->stats.launches[c] - before[(size_t)b * LRP_K_COUNT + c];
         p->stats.launches[c] = before[(size_t)b * LRP_K_COUNT + c];
       }
-      for (int i = 0; i < 3; ++i) p->solve_key[i] = -1;  // the plan's own solve graph is not this one
+      // the plan's own solve graphs are captured anew on their next use
+      for (auto& sg : p->solve_graphs) sg.key[0] = -1;
     }
     m->key = key;
   }

@@ -566,7 +566,8 @@ static void plan_free(lrp_plan_s* p) {
   p->w64.release_graphs();
   p->w32.release_graphs();
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-  if (p->solve_exec) cudaGraphExecDestroy(p->solve_exec);
+  for (auto& g : p->solve_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (p->body_stream) cudaStreamDestroy(p->body_stream);
   if (p->if_stream) cudaStreamDestroy(p->if_stream);
   if (p->solve_done) cudaEventDestroy(p->solve_done);
@@ -1341,16 +1342,28 @@ void stage_solve(lrp_plan_s* p, int count) {
 }
 
 // One graph launch per solve: captured on first use for (count, warm records,
-// tracing), replayed on the caller's stream afterwards.
+// tracing), replayed on the caller's stream afterwards; up to kSolveGraphs such
+// graphs are kept per plan.
 static lrp_status solve_device(lrp_plan_s* p, int count, cudaStream_t s) {
   stage_solve(p, count);
   const int key[3] = {count, p->any_warm ? 1 : 0, p->trace_on ? 1 : 0};
-  if (!p->solve_exec || key[0] != p->solve_key[0] || key[1] != p->solve_key[1] || key[2] != p->solve_key[2]) {
-    if (p->solve_exec) {
-      SetupGuard guard;
-      cudaGraphExecDestroy(p->solve_exec);
-      p->solve_exec = nullptr;
+  lrp_plan_s::SolveGraph* g = nullptr;
+  lrp_plan_s::SolveGraph* victim = nullptr;  // an empty entry, else the least recently used
+  for (auto& e : p->solve_graphs) {
+    if (e.exec && e.key[0] == key[0] && e.key[1] == key[1] && e.key[2] == key[2]) {
+      g = &e;
+      break;
     }
+    if (!victim || (victim->exec && (!e.exec || e.used < victim->used))) victim = &e;
+  }
+  if (!g) {
+    g = victim;
+    if (g->exec) {
+      SetupGuard guard;
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+    }
+    for (int i = 0; i < 3; ++i) g->key[i] = -1;
     int64_t before[LRP_K_COUNT];
     for (int c = 0; c < LRP_K_COUNT; ++c) before[c] = p->stats.launches[c];
     cudaGraph_t graph = nullptr;
@@ -1365,21 +1378,22 @@ static lrp_status solve_device(lrp_plan_s* p, int count, cudaStream_t s) {
       }
       if (e != cudaSuccess) return set_error(LRP_ECUDA, std::string("solve capture: ") + cudaGetErrorString(e));
     }
-    const cudaError_t e = cudaGraphInstantiate(&p->solve_exec, graph, 0);
+    const cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      p->solve_exec = nullptr;
+      g->exec = nullptr;
       return set_error(LRP_ECUDA, std::string("solve graph instantiate: ") + cudaGetErrorString(e));
     }
     for (int c = 0; c < LRP_K_COUNT; ++c) {
-      p->solve_launches[c] = p->stats.launches[c] - before[c];
+      g->launches[c] = p->stats.launches[c] - before[c];
       p->stats.launches[c] = before[c];
     }
-    for (int i = 0; i < 3; ++i) p->solve_key[i] = key[i];
+    for (int i = 0; i < 3; ++i) g->key[i] = key[i];
   }
-  LRP_CUDA(cudaGraphLaunch(p->solve_exec, s));
+  g->used = ++p->solve_tick;
+  LRP_CUDA(cudaGraphLaunch(g->exec, s));
   LRP_CUDA(cudaEventRecord(p->solve_done, s));
-  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += p->solve_launches[c];
+  for (int c = 0; c < LRP_K_COUNT; ++c) p->stats.launches[c] += g->launches[c];
   return LRP_OK;
 }
 

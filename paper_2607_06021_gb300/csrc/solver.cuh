@@ -165,9 +165,18 @@ struct lrp_plan_s {
   cudaStream_t body_stream = nullptr;    // captures the loop bodies
   cudaStream_t if_stream = nullptr;      // captures the mixed path's second refinement step
   int32_t* loop_trips = nullptr;         // device: trips of the running device-side loop
-  cudaGraphExec_t solve_exec = nullptr;  // the captured solve
-  int solve_key[3] = {-1, -1, -1};       // (count, any_warm, trace_on) it was captured for
-  int64_t solve_launches[LRP_K_COUNT] = {};  // kernel nodes of the captured solve (loop bodies once)
+  // Captured solves, one per (count, any_warm, trace_on), the least recently
+  // used replaced: batches of varying size (a server's) each replay their own
+  // graph instead of capturing and instantiating the whole solve again.
+  struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    int key[3] = {-1, -1, -1};
+    uint64_t used = 0;
+    int64_t launches[LRP_K_COUNT] = {};  // kernel nodes of the captured solve (loop bodies once)
+  };
+  static constexpr int kSolveGraphs = 8;
+  SolveGraph solve_graphs[kSolveGraphs];
+  uint64_t solve_tick = 0;
   cudaEvent_t solve_done = nullptr;      // completion of the last enqueued solve
   std::mutex mu;
 };
