@@ -304,6 +304,10 @@ __global__ void k_setup_correction(RefineArgs a) {
   const int rR = st->r;
   const double* sR = a.sig_out + (int64_t)slot * a.sig_out_stride;
   for (int k = threadIdx.x; k < rR; k += blockDim.x) a.w32[(int64_t)slot * a.wstride + k] = (float)sR[k];
+  // Thread 0 replaces the whole state below: every thread must have read the
+  // rank first (a warp that read it after the replacement would see 0 and
+  // leave its weights, k >= 32, stale).
+  __syncthreads();
   if (threadIdx.x == 0) {
     const int total = st->total_iters;
     const int r0 = st->r0, rf0 = st->rf0;
