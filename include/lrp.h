@@ -98,7 +98,9 @@ typedef struct lrp_opts {
                             conditional while-nodes, continued by the device while any problem is
                             active (bounded by max_iter), so a solve is one graph launch and the call
                             returns without waiting for it (the mixed path's second refinement step
-                            is a conditional if-node of the same graph). */
+                            is a conditional if-node of the same graph).  The graph is captured on a
+                            batch size's first solve; a plan keeps up to eight (one per batch size,
+                            least recently used replaced). */
   /* Launch shapes (no counterpart in the paper).  Both are result-neutral: every
      output is computed by the same operations in the same order whatever the
      value, so they change only the speed (lrp_group and the autotuner in
